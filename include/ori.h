@@ -1,0 +1,215 @@
+/*
+ * ori.h - C ABI of the GB300 solver for the reduced (RED) / original (ORI)
+ * linear system of Ramm & Tran, "A fast algorithm for solving scalar wave
+ * scattering problem by billions of particles".
+ *
+ * The system (Eq. 2.19, the sum moved to the left-hand side; Eq. 2.15 is the
+ * same system with one particle per cell and N = 1):
+ *
+ *     u_q + c_S * sum_{p != q} G(x_q, x_p) h_p N_p |Delta_p| u_p = u0_q,
+ *     G(x, y) = exp(ik|x-y|) / (4 pi |x-y|)         (Eq. 2.6a, Eq. 3.3.2)
+ *     u0(x)   = exp(ik alpha . x)                    (Eq. 2.4)
+ *
+ * on the n^3 cells of a cube [o, o + side]^3; x_p is the centre of cell p
+ * and |Delta_p| = (side/n)^3.  The matrix is never stored (Section 3): the
+ * off-diagonal sum is a 3D convolution (Eq. 3.3.6-3.3.7) done with padded
+ * FFTs by the convolution theorem (Eq. 3.3.8); the kernel's spectrum is
+ * computed once per plan.  The system is solved with COCG (Section 1,
+ * Section 3) to the relative residual ||r|| / ||RHS|| (Section 4).
+ *
+ * Conventions for every entry point:
+ *  - Arrays are C-ordered [z][y][x] with x fastest; index p = (iz*n + iy)*n + ix.
+ *  - A complex array of m entries is 2*m doubles (or floats for the *32 entry
+ *    points), interleaved (re, im): the layout of C99 double complex,
+ *    std::complex<double>, numpy complex128 and torch.complex128.
+ *  - Pointers named *_dev are CUDA device pointers on the device that was
+ *    current when the plan was made; they are owned by the caller, must stay
+ *    valid until the call's work on `stream` has finished, and are only read
+ *    (const) or written as documented.  Pointers named *_host are host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it; calls return once enqueued unless
+ *    documented as synchronising.
+ *  - Every call returns an ori_status.  Nothing is thrown across the ABI.
+ *    Invalid arguments are rejected before any device work is enqueued.  A
+ *    human-readable message for the last failure on the calling thread is
+ *    available from ori_last_error().
+ *  - A plan is not safe for concurrent use from two streams or two threads.
+ */
+#ifndef ORI_H_
+#define ORI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORI_ABI_VERSION 1
+
+typedef struct ori_plan_s* ori_plan_t;
+
+typedef enum {
+  ORI_OK = 0,
+  ORI_ERR_INVALID_ARG = 1,   /* bad size, null pointer, non-finite scalar      */
+  ORI_ERR_CUDA = 2,          /* a CUDA runtime call failed                      */
+  ORI_ERR_OOM = 3,           /* device allocation failed or mem_cap exceeded    */
+  ORI_ERR_NOT_CONVERGED = 4, /* maxit reached; best iterate written             */
+  ORI_ERR_BREAKDOWN = 5,     /* COCG breakdown (p^T B p or r^T r vanished)      */
+  ORI_ERR_NONFINITE = 6,     /* NaN/Inf met in the iteration                    */
+  ORI_ERR_UNSUPPORTED = 7    /* valid request this build does not implement     */
+} ori_status;
+
+/* Arithmetic of a call. */
+enum {
+  ORI_FP64 = 0,   /* complex128 data, FP64 FFTs                                      */
+  ORI_FP32 = 1,   /* complex64 data, FP32 FFTs (FP64 spectrum rounded once)          */
+  ORI_MIXED = 2   /* solve only: FP32 COCG inside FP64 iterative refinement          */
+};
+
+/* Which operator ori_matvec applies. */
+enum {
+  ORI_FORM_A = 0, /* y = A x = x + c_S K_G (h N |Delta| x)   (Eq. 2.19, left side)   */
+  ORI_FORM_B = 1  /* y = B x = x + S c_S K_G (S x), S = diag(sqrt(h N)), principal
+                     root.  B = S A S^-1 is complex symmetric; COCG runs on it.     */
+};
+
+typedef struct {
+  double origin[3]; /* corner of the cube (x, y, z)                                 */
+  double side;      /* edge length, > 0; cell size d = side / n                     */
+} ori_domain;
+
+typedef struct {
+  double c_S;       /* surface constant |S_m| = c_S a^2 (Eq. 2.13); 0 -> 4 pi       */
+  size_t mem_cap;   /* 0 = no cap; otherwise ori_plan fails with ORI_ERR_OOM when
+                       its device memory would exceed this many bytes              */
+  int    reserved[8];
+} ori_plan_opts;
+
+typedef struct {
+  double tol;          /* target ||r||/||RHS|| of the original system, default 1e-6 */
+  int    maxit;        /* cap on COCG iterations summed over refinements, def 1000  */
+  int    precision;    /* ORI_FP64 or ORI_MIXED (default ORI_MIXED)                  */
+  double inner_tol;    /* ORI_MIXED: floor of the FP32 inner target, default 1e-5    */
+  int    max_outer;    /* ORI_MIXED: cap on refinement steps, default 8              */
+  int    check_every;  /* iterations between host reads of the convergence flag (8)  */
+  double alpha[3];     /* incidence direction when rhs_dev == NULL; (0,0,0)->(0,0,1) */
+  int    use_graph;    /* 1 (default): replay the check_every-iteration block as a
+                          captured CUDA graph; 0: plain launches                      */
+  int    reserved[7];
+} ori_solve_opts;
+
+typedef struct {
+  int    iters;         /* COCG iterations, all refinement steps together            */
+  int    outer_iters;   /* refinement steps (1 for ORI_FP64)                         */
+  int    fp64_matvecs;  /* FP64 operator applications (residuals, recovery)          */
+  double relres;        /* true ||u0 - A u|| / ||u0|| measured in FP64 on exit,
+                           evaluated on the symmetrised system S(u0 - A u)           */
+  double relres_recur;  /* last recursive residual of the inner COCG                 */
+  int    status;        /* ori_status of the solve                                   */
+  float  ms;            /* device time of the solve (CUDA events)                    */
+} ori_solve_info;
+
+/* Fill *o with the defaults named above. */
+void ori_default_solve_opts(ori_solve_opts* o);
+void ori_default_plan_opts(ori_plan_opts* o);
+
+/*
+ * ori_plan - build the operator for one grid, wave number and medium.
+ *   n        cells per axis, 2 <= n <= 1024.  The padded FFT length per axis
+ *            is L = the smallest power of two >= 2n (the paper pads to 2b-2
+ *            by mirroring, Section 3; any L >= 2n-1 gives the same crop).
+ *   k        wave number, finite and > 0 (Eq. 2.1).
+ *   dom      cube corner and side (Eq. 3.3.5 uses the unit cube at the origin).
+ *   h_dev    n^3 complex128 impedance samples h(x_p) (Eq. 2.13), device.
+ *   N_dev    n^3 float64 densities N(x_p) >= 0 (Eq. 2.17), device.
+ *   opts     may be NULL (defaults).
+ * The plan computes, on `stream`, the kernel cube c_S |Delta| G(d |j|) with
+ * the self term set to 0 (the sum excludes p = q), its spectrum by an FP64
+ * 3D FFT, stores the (L/2+1)^3 distinct entries (the cube is even along each
+ * axis) in FP64 and FP32, and copies h, N, h*N and S = sqrt(h N).  Later
+ * changes to h_dev / N_dev do not affect the plan (see ori_plan_set_medium).
+ * The call synchronises `stream` before returning.  *out receives the plan.
+ */
+ori_status ori_plan(int64_t n, double k, const ori_domain* dom,
+                    const double* h_dev, const double* N_dev,
+                    const ori_plan_opts* opts, void* stream, ori_plan_t* out);
+
+/* Replace h and N (same layout as ori_plan) without recomputing the spectrum.
+ * Synchronises `stream`. */
+ori_status ori_plan_set_medium(ori_plan_t plan, const double* h_dev,
+                               const double* N_dev, void* stream);
+
+/* Free the plan and its device memory (synchronises the device first). */
+ori_status ori_plan_destroy(ori_plan_t plan);
+
+/* Grid size, padded length, and bytes of device memory the plan holds. */
+ori_status ori_plan_info(ori_plan_t plan, int64_t* n, int64_t* L, size_t* bytes);
+
+/*
+ * ori_matvec - y = A x or y = B x (form) for n^3 complex128 vectors.
+ *   precision ORI_FP64: every pass in FP64.
+ *   precision ORI_FP32: x is rounded to complex64, the passes run in FP32
+ *                       with the FP32 spectrum, y is widened back.
+ * x_dev and y_dev may not overlap.  Asynchronous on `stream`.
+ */
+ori_status ori_matvec(ori_plan_t plan, const double* x_dev, double* y_dev,
+                      int form, int precision, void* stream);
+
+/*
+ * ori_matvec32 - the FP32 operator on complex64 device vectors (2*n^3 floats
+ * each), B or A form.  This is the matvec the mixed solver iterates with.
+ * Asynchronous on `stream`.
+ */
+ori_status ori_matvec32(ori_plan_t plan, const float* x_dev, float* y_dev,
+                        int form, void* stream);
+
+/*
+ * ori_cocg_solve - solve A u = rhs (Eq. 2.19).
+ *   rhs_dev  n^3 complex128 right-hand side, or NULL for the plane wave
+ *            u0 = exp(ik alpha . x_p) with alpha = opts->alpha (Eq. 2.4).
+ *   u_dev    n^3 complex128 output (also the best iterate on failure).
+ * COCG runs on the complex-symmetric B w = S rhs, and u = w / S; cells with
+ * S = 0 get u = rhs - K (S w) (one more FP64 operator application).
+ * ORI_FP64 runs COCG in FP64.  ORI_MIXED runs FP32 COCG with FP64 scalars on
+ * the normalised FP64 residual and refines w in FP64 until the FP64 residual
+ * meets tol.  Synchronising: returns after the solve has finished; info (may
+ * be NULL) is filled.  Returns ORI_ERR_NOT_CONVERGED / _BREAKDOWN /
+ * _NONFINITE with the best iterate in u_dev.
+ */
+ori_status ori_cocg_solve(ori_plan_t plan, const double* rhs_dev, double* u_dev,
+                          const ori_solve_opts* opts, ori_solve_info* info,
+                          void* stream);
+
+/*
+ * ori_adjoint_solve - gradient of J = sum_obs |u_o - t_o|^2 with respect to
+ * h and N, where u solves A(h, N) u = u0.  The paper has no gradient; this
+ * follows from Eq. 2.19: with psi = A^-T conj(e) (e = u - t on observation
+ * cells, 0 elsewhere) and A^T psi = conj(e):
+ *     grad_h_p = -2 conj((conj(e_p) - psi_p) u_p / h_p)   (dJ/dRe h + i dJ/dIm h)
+ *     grad_N_p = -2 Re((conj(e_p) - psi_p) u_p / N_p)
+ * Because A^T = S B S^-1, psi = S z with B z = S^-1 conj(e): one more COCG
+ * solve on the same plan.
+ *   u_dev       the converged forward solution (n^3 complex128).
+ *   econj_dev   conj(u - t) on observation cells, 0 elsewhere (n^3 complex128).
+ *   grad_h_dev  n^3 complex128 output.  grad_N_dev: n^3 float64 output.
+ * Needs h_p != 0 and N_p != 0 in every cell (else ORI_ERR_UNSUPPORTED).
+ * Synchronising, like ori_cocg_solve.
+ */
+ori_status ori_adjoint_solve(ori_plan_t plan, const double* u_dev,
+                             const double* econj_dev, double* grad_h_dev,
+                             double* grad_N_dev, const ori_solve_opts* opts,
+                             ori_solve_info* info, void* stream);
+
+/* Static description of a status code. */
+const char* ori_status_string(int status);
+/* Message of the last failure on the calling thread ("" if none). */
+const char* ori_last_error(void);
+/* ORI_ABI_VERSION of the loaded library. */
+int ori_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORI_H_ */

@@ -46,7 +46,7 @@ import numpy as np
 
 __all__ = [
     "C_S_SPHERE", "cell_size", "cell_centres", "plane_wave", "greens_function",
-    "red_weights", "red_matrix", "red_matvec_direct", "red_matvec_rows",
+    "red_weights", "red_matrix", "red_matvec_direct", "red_matvec_rows", "offdiag_sum_rows_grid",
     "symmetrised_matrix", "symmetrised_matvec_direct", "sqrt_hN",
     "pad_kernel_mirror", "pad_field_zero", "kernel_cube",
     "fft_convolution", "red_matvec_fft", "symmetrised_matvec_fft",
@@ -156,6 +156,35 @@ def red_matvec_rows(x, rows, n, k, h, N, origin=(0.0, 0.0, 0.0), side=1.0,
         off = r > 0
         G[off] = greens_function(r[off], k)
         out[s:s + chunk] = x.ravel()[q] + G @ wx
+    return out
+
+
+def offdiag_sum_rows_grid(v, rows, n, k, side=1.0, planes_per_chunk=32):
+    """sum_{p != q} G(|x_q - x_p|) v_p for the cells q in `rows`, by direct
+    summation over the grid one slab of z-planes at a time (memory O(n^2 *
+    planes_per_chunk) instead of the O(N) positions of red_matvec_rows).  Cell
+    centres differ by d times integer offsets (Eq. 3.3.5), so the distance of a
+    cell from q needs only the three 1D offset arrays."""
+    d = side / n
+    vv = np.asarray(v, dtype=np.complex128).reshape(n, n, n)
+    rows = np.asarray(rows, dtype=np.int64).ravel()
+    out = np.empty(rows.size, dtype=np.complex128)
+    idx = np.arange(n)
+    for t, q in enumerate(rows):
+        qz, rem = divmod(int(q), n * n)
+        qy, qx = divmod(rem, n)
+        dy2 = ((idx - qy) * d) ** 2
+        dx2 = ((idx - qx) * d) ** 2
+        acc = 0j
+        for z0 in range(0, n, planes_per_chunk):
+            zs = idx[z0:z0 + planes_per_chunk]
+            dz2 = ((zs - qz) * d) ** 2
+            r = np.sqrt(dz2[:, None, None] + dy2[None, :, None] + dx2[None, None, :])
+            G = np.zeros(r.shape, dtype=np.complex128)
+            nz = r > 0
+            G[nz] = greens_function(r[nz], k)
+            acc += np.sum(G * vv[z0:z0 + planes_per_chunk])
+        out[t] = acc
     return out
 
 

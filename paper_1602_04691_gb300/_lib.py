@@ -1,0 +1,116 @@
+"""ctypes declarations of the C ABI in include/ori.h (argument marshalling only).
+
+The library is loaded from the package directory, where ``build.py`` puts it.
+There is no fallback: if libori.so is missing or fails to load, every entry
+point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libori.so")
+
+ORI_OK = 0
+ORI_ERR_INVALID_ARG = 1
+ORI_ERR_CUDA = 2
+ORI_ERR_OOM = 3
+ORI_ERR_NOT_CONVERGED = 4
+ORI_ERR_BREAKDOWN = 5
+ORI_ERR_NONFINITE = 6
+ORI_ERR_UNSUPPORTED = 7
+
+ORI_FP64 = 0
+ORI_FP32 = 1
+ORI_MIXED = 2
+ORI_FORM_A = 0
+ORI_FORM_B = 1
+
+# Every symbol include/ori.h declares.
+EXPORTS = [
+    "ori_default_solve_opts", "ori_default_plan_opts", "ori_plan", "ori_plan_set_medium",
+    "ori_plan_destroy", "ori_plan_info", "ori_matvec", "ori_matvec32", "ori_cocg_solve",
+    "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
+]
+
+
+class Domain(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("side", C.c_double)]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("c_S", C.c_double), ("mem_cap", C.c_size_t), ("reserved", C.c_int * 8)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
+                ("alpha", C.c_double * 3), ("use_graph", C.c_int), ("reserved", C.c_int * 7)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("fp64_matvecs", C.c_int),
+                ("relres", C.c_double), ("relres_recur", C.c_double), ("status", C.c_int),
+                ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class OriError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libori.so (once) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    import torch  # noqa: F401  (loads the CUDA runtime first, so the library shares it)
+    lib = C.CDLL(LIB_PATH)
+    vp, d, i64, i = C.c_void_p, C.c_double, C.c_int64, C.c_int
+    lib.ori_default_solve_opts.argtypes = [C.POINTER(SolveOpts)]
+    lib.ori_default_solve_opts.restype = None
+    lib.ori_default_plan_opts.argtypes = [C.POINTER(PlanOpts)]
+    lib.ori_default_plan_opts.restype = None
+    lib.ori_plan.argtypes = [i64, d, C.POINTER(Domain), vp, vp, C.POINTER(PlanOpts), vp, C.POINTER(vp)]
+    lib.ori_plan.restype = i
+    lib.ori_plan_set_medium.argtypes = [vp, vp, vp, vp]
+    lib.ori_plan_set_medium.restype = i
+    lib.ori_plan_destroy.argtypes = [vp]
+    lib.ori_plan_destroy.restype = i
+    lib.ori_plan_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_size_t)]
+    lib.ori_plan_info.restype = i
+    lib.ori_matvec.argtypes = [vp, vp, vp, i, i, vp]
+    lib.ori_matvec.restype = i
+    lib.ori_matvec32.argtypes = [vp, vp, vp, i, vp]
+    lib.ori_matvec32.restype = i
+    lib.ori_cocg_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+    lib.ori_cocg_solve.restype = i
+    lib.ori_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
+    lib.ori_adjoint_solve.restype = i
+    lib.ori_status_string.argtypes = [i]
+    lib.ori_status_string.restype = C.c_char_p
+    lib.ori_last_error.argtypes = []
+    lib.ori_last_error.restype = C.c_char_p
+    lib.ori_abi_version.argtypes = []
+    lib.ori_abi_version.restype = i
+    _lib = lib
+    return lib
+
+
+def check(status: int, what: str = "ori call"):
+    if status != ORI_OK:
+        lib = load()
+        msg = lib.ori_last_error().decode() or lib.ori_status_string(status).decode()
+        raise OriError(status, f"{what}: {msg}")

@@ -1,0 +1,204 @@
+// common.cuh - complex arithmetic, twiddle factors and in-register DFTs for
+// the FFT passes of the convolution matvec (Section 3, Eq. 3.3.8).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ori {
+
+// ---------------------------------------------------------------------------
+// Complex numbers (interleaved re, im; 8 bytes for float, 16 for double)
+// ---------------------------------------------------------------------------
+template <class T>
+struct alignas(2 * sizeof(T)) cpx {
+  T x, y;
+};
+
+template <class T>
+__host__ __device__ __forceinline__ cpx<T> mkc(T a, T b) { return cpx<T>{a, b}; }
+template <class T>
+__device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T>
+__device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <class T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T>
+__device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <class T>
+__device__ __forceinline__ cpx<T> czero() { return {T(0), T(0)}; }
+
+template <class D, class S>
+__device__ __forceinline__ cpx<D> ccast(cpx<S> a) { return {D(a.x), D(a.y)}; }
+
+// ---------------------------------------------------------------------------
+// Twiddles.  cos/sin of 2 pi j / M are evaluated at compile time from their
+// Taylor series on [0, pi/4] after an exact reduction by octant symmetry.
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 16; ++i) {
+    t *= -x * x / double((2 * i) * (2 * i + 1));
+    s += t;
+  }
+  return s;
+}
+constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 16; ++i) {
+    t *= -x * x / double((2 * i - 1) * (2 * i));
+    s += t;
+  }
+  return s;
+}
+
+// (cos, sin) of 2 pi j / M for M divisible by 8.
+struct CosSin {
+  double c, s;
+};
+constexpr CosSin turn_cos_sin(long long j, long long M) {
+  long long jm = ((j % M) + M) % M;
+  const long long m8 = M / 8;
+  const long long oct = jm / m8, rem = jm % m8;
+  const double step = 2.0 * kPi / double(M);
+  const double phi = double(rem) * step;          // in [0, pi/4)
+  const double phr = double(m8 - rem) * step;     // in (0, pi/4]
+  const double cp = taylor_cos(phi), sp = taylor_sin(phi);
+  const double cr = taylor_cos(phr), sr = taylor_sin(phr);
+  switch (oct) {
+    case 0: return {cp, sp};
+    case 1: return {sr, cr};
+    case 2: return {-sp, cp};
+    case 3: return {-cr, sr};
+    case 4: return {-cp, -sp};
+    case 5: return {-sr, -cr};
+    case 6: return {sp, -cp};
+    default: return {cr, -sr};
+  }
+}
+
+// cos/sin of 2 pi j / 64 for the in-register DFTs (radix up to 64).
+struct Tw64 {
+  double c[64];
+  double s[64];
+  float cf[64];
+  float sf[64];
+};
+constexpr Tw64 make_tw64() {
+  Tw64 t{};
+  for (int j = 0; j < 64; ++j) {
+    CosSin v = turn_cos_sin(j, 64);
+    t.c[j] = v.c;
+    t.s[j] = v.s;
+    t.cf[j] = float(v.c);
+    t.sf[j] = float(v.s);
+  }
+  return t;
+}
+
+__constant__ Tw64 c_tw64 = make_tw64();
+
+template <class T>
+__device__ __forceinline__ T tw64c(int i);
+template <>
+__device__ __forceinline__ float tw64c<float>(int i) { return c_tw64.cf[i]; }
+template <>
+__device__ __forceinline__ double tw64c<double>(int i) { return c_tw64.c[i]; }
+template <class T>
+__device__ __forceinline__ T tw64s(int i);
+template <>
+__device__ __forceinline__ float tw64s<float>(int i) { return c_tw64.sf[i]; }
+template <>
+__device__ __forceinline__ double tw64s<double>(int i) { return c_tw64.s[i]; }
+
+// z * exp(SIGN * 2 pi i idx / 64); idx is a compile-time constant after
+// unrolling, so trivial factors cost nothing and the others read the
+// constant bank directly.
+template <int SIGN, class T>
+__device__ __forceinline__ cpx<T> tw64_mul(cpx<T> z, int idx) {
+  idx &= 63;
+  if (idx == 0) return z;
+  if (idx == 32) return {-z.x, -z.y};
+  if (idx == 16) return SIGN > 0 ? cpx<T>{-z.y, z.x} : cpx<T>{z.y, -z.x};
+  if (idx == 48) return SIGN > 0 ? cpx<T>{z.y, -z.x} : cpx<T>{-z.y, z.x};
+  const T c = tw64c<T>(idx);
+  const T s = SIGN > 0 ? tw64s<T>(idx) : -tw64s<T>(idx);
+  return {z.x * c - z.y * s, z.x * s + z.y * c};
+}
+
+// Read-only cached loads of one complex number.
+__device__ __forceinline__ cpx<float> ldgc(const cpx<float>* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+__device__ __forceinline__ cpx<double> ldgc(const cpx<double>* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
+// z * exp(SIGN * 2 pi i m / L) from a table tab[m] = (cos, sin)(2 pi m / L).
+template <int SIGN, class T>
+__device__ __forceinline__ cpx<T> twL_mul(cpx<T> z, const cpx<T>* __restrict__ tab, int m) {
+  const cpx<T> w = ldgc(tab + m);
+  const T c = w.x;
+  const T s = SIGN > 0 ? w.y : -w.y;
+  return {z.x * c - z.y * s, z.x * s + z.y * c};
+}
+
+constexpr int bitrev(int i, int R) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// In-register DFT of size R (power of two, R <= 64):
+//   a[k] <- sum_j a[j] exp(SIGN 2 pi i j k / R).
+// Radix-2 decimation in frequency, then the bit-reversal permutation (free:
+// all indices are compile-time constants).  HALF: a[j] = 0 for j >= R/2 on
+// input (the zero padding of Section 3), which removes the first stage's adds.
+template <int R, int SIGN, bool HALF, class T>
+__device__ __forceinline__ void dft(cpx<T> (&a)[R]) {
+  if constexpr (R > 1) {
+#pragma unroll
+    for (int s = R / 2; s >= 1; s >>= 1) {
+#pragma unroll
+      for (int b = 0; b < R; b += 2 * s) {
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+          const int idx = j * (64 / (2 * s));
+          const cpx<T> u = a[b + j];
+          if (HALF && s == R / 2) {
+            a[b + j + s] = tw64_mul<SIGN>(u, idx);
+          } else {
+            const cpx<T> v = a[b + j + s];
+            a[b + j] = u + v;
+            a[b + j + s] = tw64_mul<SIGN>(u - v, idx);
+          }
+        }
+      }
+    }
+    cpx<T> t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) t[i] = a[bitrev(i, R)];
+#pragma unroll
+    for (int i = 0; i < R; ++i) a[i] = t[i];
+  }
+}
+
+// Split of the padded length L = L1 * L2 into two in-register stages.
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+template <int L>
+struct Split {
+  static constexpr int lg = ilog2(L);
+  static constexpr int L1 = 1 << ((lg + 1) / 2);
+  static constexpr int L2 = L / L1;
+};
+
+}  // namespace ori

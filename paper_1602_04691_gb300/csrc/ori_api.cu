@@ -1,0 +1,776 @@
+// ori_api.cu - the C ABI declared in include/ori.h: plan, matvec, COCG solve
+// (FP64 and mixed FP32/FP64 refinement) and the adjoint gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/ori.h"
+#include "common.cuh"
+#include "passes.cuh"
+#include "scalars.cuh"
+#include "vector_kernels.cuh"
+
+namespace ori {
+template <class T> cudaError_t run_xfwd(int, bool, const XArgs&, cudaStream_t, bool);
+template <class T> cudaError_t run_xinv(int, const XArgs&, Scalars*, int, cudaStream_t, bool, unsigned*);
+template <class T> cudaError_t run_strided(int, int, bool, const SArgs&, cudaStream_t, bool);
+}  // namespace ori
+
+using namespace ori;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static ori_status fail(ori_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define ORI_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? ORI_ERR_OOM : ORI_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+#define ORI_TRY(expr)                 \
+  do {                                \
+    ori_status s_ = (expr);           \
+    if (s_ != ORI_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+struct ori_plan_s {
+  int device = 0;
+  int n = 0, L = 0, H = 0;
+  long long n3 = 0;
+  double k = 0, d = 0, c_S = 0, side = 0, origin[3] = {0, 0, 0};
+  size_t bytes = 0, mem_cap = 0;
+  int sm_count = 0;
+  unsigned long long zero_S = 0;
+  // medium
+  cpx<double>* h = nullptr;
+  double* N = nullptr;
+  cpx<double>* w64 = nullptr;
+  cpx<double>* S64 = nullptr;
+  cpx<float>* w32 = nullptr;
+  cpx<float>* S32 = nullptr;
+  // spectrum and twiddles
+  cpx<double>* ghat64 = nullptr;
+  cpx<float>* ghat32 = nullptr;
+  cpx<double>* tw64 = nullptr;
+  cpx<float>* tw32 = nullptr;
+  // pass scratch
+  cpx<float>* T1f = nullptr;
+  cpx<float>* T2f = nullptr;
+  cpx<double>* T1d = nullptr;
+  cpx<double>* T2d = nullptr;
+  // solver state
+  Scalars* sc = nullptr;
+  Scalars* h_sc = nullptr;   // pinned mirror
+  double2* partials = nullptr;
+  size_t npartials = 0;
+  unsigned long long* d_count = nullptr;
+  cpx<double>* b64 = nullptr;
+  cpx<double>* w = nullptr;
+  cpx<double>* r64 = nullptr;
+  cpx<double>* u0 = nullptr;
+  cpx<double>* p64 = nullptr;
+  cpx<double>* q64 = nullptr;
+  cpx<float>* x32 = nullptr;
+  cpx<float>* r32 = nullptr;
+  cpx<float>* p32 = nullptr;
+  cpx<float>* q32 = nullptr;
+  cudaStream_t ps = nullptr;   // private stream (capturable)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evj = nullptr;
+  cudaGraphExec_t graph_f = nullptr, graph_d = nullptr;
+  int graph_f_len = 0, graph_d_len = 0;
+  int vec_grid = 0;
+};
+
+static ori_status plan_alloc(ori_plan_s* p, void** ptr, size_t bytes) {
+  if (p->mem_cap && p->bytes + bytes > p->mem_cap)
+    return fail(ORI_ERR_OOM, "plan memory would exceed opts->mem_cap");
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(ORI_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  p->bytes += bytes;
+  return ORI_OK;
+}
+
+template <class P>
+static ori_status alloc_n(ori_plan_s* p, P** ptr, size_t count) {
+  return plan_alloc(p, reinterpret_cast<void**>(ptr), count * sizeof(P));
+}
+
+static void plan_free(ori_plan_s* p) {
+  if (!p) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
+                  p->T1f, p->T2f, p->T1d, p->T2d, p->sc, p->partials, p->d_count, p->b64, p->w,
+                  p->r64, p->u0, p->p64, p->q64, p->x32, p->r32, p->p32, p->q32};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->h_sc) cudaFreeHost(p->h_sc);
+  if (p->graph_f) cudaGraphExecDestroy(p->graph_f);
+  if (p->graph_d) cudaGraphExecDestroy(p->graph_d);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  if (p->evj) cudaEventDestroy(p->evj);
+  if (p->ps) cudaStreamDestroy(p->ps);
+  cudaSetDevice(prev);
+  delete p;
+}
+
+// Host twiddle table tab[m] = (cos, sin)(2 pi m / L), from the compile-time
+// evaluable series in common.cuh on a fine circle (2^20 points).
+template <class T>
+static void host_twiddles(int L, cpx<T>* out) {
+  const long long M = 1LL << 20;
+  for (int m = 0; m < L; ++m) {
+    CosSin v = turn_cos_sin((long long)m * (M / L), M);
+    out[m] = cpx<T>{T(v.c), T(v.s)};
+  }
+}
+
+// Stream handoff: the plan's private stream waits for the caller's stream.
+static ori_status enter(ori_plan_s* p, cudaStream_t user) {
+  ORI_CUDA(cudaEventRecord(p->evj, user));
+  ORI_CUDA(cudaStreamWaitEvent(p->ps, p->evj, 0));
+  return ORI_OK;
+}
+static ori_status leave(ori_plan_s* p, cudaStream_t user) {
+  ORI_CUDA(cudaEventRecord(p->evj, p->ps));
+  ORI_CUDA(cudaStreamWaitEvent(user, p->evj, 0));
+  return ORI_OK;
+}
+
+// One application of the convolution operator: X fwd (prologue), Y fwd, Z
+// conv, Y inv, X inv (epilogue).  `pro` and `epi` carry the mode and vectors.
+template <class T>
+static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s,
+                           const int* done) {
+  const bool f32 = sizeof(T) == 4;
+  cpx<T>* T1 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T1f : (void*)p->T1d);
+  cpx<T>* T2 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T2f : (void*)p->T2d);
+  const void* tw = f32 ? (const void*)p->tw32 : (const void*)p->tw64;
+  const int n = p->n, L = p->L;
+  pro.n = n; pro.nlines = n * n; pro.n_in = n; pro.line_len_in = n; pro.line_len_out = L;
+  pro.fft_out = T1; pro.twL = tw; pro.done = done;
+  ORI_CUDA(run_xfwd<T>(L, true, pro, s, false));
+
+  SArgs y{};
+  y.in = T1; y.out = T2;
+  y.in_outer = (long long)n * L; y.out_outer = (long long)L * L;
+  y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = n; y.n_out = L; y.nouter = n;
+  y.twL = tw; y.done = done;
+  ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
+
+  SArgs z{};
+  z.in = T2; z.out = T2;
+  z.in_outer = L; z.out_outer = L;
+  z.in_pt = (long long)L * L; z.out_pt = (long long)L * L;
+  z.ncols = L; z.n_in = n; z.n_out = n; z.nouter = L;
+  z.twL = tw; z.ghat = f32 ? (const void*)p->ghat32 : (const void*)p->ghat64; z.H = p->H;
+  z.done = done;
+  ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
+
+  SArgs yi{};
+  yi.in = T2; yi.out = T1;
+  yi.in_outer = (long long)L * L; yi.out_outer = (long long)n * L;
+  yi.in_pt = L; yi.out_pt = L; yi.ncols = L; yi.n_in = L; yi.n_out = n; yi.nouter = n;
+  yi.twL = tw; yi.done = done;
+  ORI_CUDA(run_strided<T>(L, SMODE_INV, false, yi, s, false));
+
+  epi.n = n; epi.nlines = n * n; epi.line_len_in = L; epi.line_len_out = n;
+  epi.in = T1; epi.twL = tw; epi.done = done; epi.partials = p->partials;
+  ORI_CUDA(run_xinv<T>(L, epi, p->sc, fin, s, false, nullptr));
+  return ORI_OK;
+}
+
+template <class T>
+static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n) {
+  XArgs a{};
+  a.nlines = n * n;
+  ORI_CUDA(run_xfwd<T>(L, true, a, nullptr, true));
+  ORI_CUDA(run_xfwd<T>(L, false, a, nullptr, true));
+  ORI_CUDA(run_xinv<T>(L, a, nullptr, FIN_NONE, nullptr, true, xinv_blocks));
+  SArgs s{};
+  ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, s, nullptr, true));
+  ORI_CUDA(run_strided<T>(L, SMODE_FWD, false, s, nullptr, true));
+  ORI_CUDA(run_strided<T>(L, SMODE_INV, false, s, nullptr, true));
+  ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, s, nullptr, true));
+  return ORI_OK;
+}
+
+static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N_dev) {
+  const size_t n3 = size_t(p->n3);
+  ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
+  ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
+  ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
+  k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->n3, p->d_count);
+  ORI_CUDA(cudaGetLastError());
+  ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  return ORI_OK;
+}
+
+static ori_status build_spectrum(ori_plan_s* p) {
+  const int L = p->L, n = p->n;
+  const long long L3 = (long long)L * L * L;
+  cpx<double>* cube = nullptr;
+  {
+    cudaError_t e = cudaMalloc(&cube, size_t(L3) * sizeof(cpx<double>));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ORI_ERR_OOM, std::string("cudaMalloc (kernel cube): ") + cudaGetErrorString(e));
+    }
+  }
+  ori_status st = ORI_OK;
+  do {
+    XArgs a{};
+    a.mode = PRO_KERNEL;
+    a.d = p->d;
+    a.k = p->k;
+    a.n = n;
+    a.nlines = L * L;
+    a.n_in = L;
+    a.line_len_in = L;
+    a.line_len_out = L;
+    a.lines_per_plane = L;
+    a.fft_out = cube;
+    a.twL = p->tw64;
+    cudaError_t e = run_xfwd<double>(L, false, a, p->ps, false);
+    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan X pass: ") + cudaGetErrorString(e)); break; }
+    SArgs y{};
+    y.in = cube; y.out = cube;
+    y.in_outer = (long long)L * L; y.out_outer = (long long)L * L;
+    y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = L; y.n_out = L; y.nouter = L;
+    y.twL = p->tw64;
+    e = run_strided<double>(L, SMODE_FWD, false, y, p->ps, false);
+    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Y pass: ") + cudaGetErrorString(e)); break; }
+    SArgs z{};
+    z.in = cube; z.out = cube;
+    z.in_outer = L; z.out_outer = L;
+    z.in_pt = (long long)L * L; z.out_pt = (long long)L * L;
+    z.ncols = L; z.n_in = L; z.n_out = L; z.nouter = L;
+    z.twL = p->tw64;
+    e = run_strided<double>(L, SMODE_FWD, false, z, p->ps, false);
+    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z pass: ") + cudaGetErrorString(e)); break; }
+    const double scale = p->c_S * p->d * p->d * p->d / double(L3);
+    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64, p->ghat32, L, p->H, scale);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan extract: ") + cudaGetErrorString(e)); break; }
+    e = cudaStreamSynchronize(p->ps);
+    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan spectrum: ") + cudaGetErrorString(e)); break; }
+  } while (0);
+  cudaFree(cube);
+  return st;
+}
+
+static bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+extern "C" {
+
+void ori_default_plan_opts(ori_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->c_S = 4.0 * kPi;
+}
+
+void ori_default_solve_opts(ori_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->maxit = 1000;
+  o->precision = ORI_MIXED;
+  o->inner_tol = 1e-5;
+  o->max_outer = 8;
+  o->check_every = 8;
+  o->alpha[2] = 1.0;
+  o->use_graph = 1;
+}
+
+int ori_abi_version(void) { return ORI_ABI_VERSION; }
+
+const char* ori_last_error(void) { return g_last_error.c_str(); }
+
+const char* ori_status_string(int s) {
+  switch (s) {
+    case ORI_OK: return "ok";
+    case ORI_ERR_INVALID_ARG: return "invalid argument";
+    case ORI_ERR_CUDA: return "CUDA error";
+    case ORI_ERR_OOM: return "out of device memory";
+    case ORI_ERR_NOT_CONVERGED: return "not converged";
+    case ORI_ERR_BREAKDOWN: return "COCG breakdown";
+    case ORI_ERR_NONFINITE: return "non-finite value";
+    case ORI_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_dev,
+                    const double* N_dev, const ori_plan_opts* opts, void* stream, ori_plan_t* out) {
+  g_last_error.clear();
+  if (!out) return fail(ORI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 2 || n > 512) return fail(ORI_ERR_INVALID_ARG, "n must be in [2, 512]");
+  if (!std::isfinite(k) || k <= 0) return fail(ORI_ERR_INVALID_ARG, "k must be finite and > 0");
+  if (!dom) return fail(ORI_ERR_INVALID_ARG, "dom is NULL");
+  if (!std::isfinite(dom->side) || dom->side <= 0 || !finite3(dom->origin))
+    return fail(ORI_ERR_INVALID_ARG, "domain side must be finite and > 0, origin finite");
+  if (!h_dev || !N_dev) return fail(ORI_ERR_INVALID_ARG, "h_dev and N_dev must be non-NULL");
+  ori_plan_opts o;
+  ori_default_plan_opts(&o);
+  if (opts) {
+    o = *opts;
+    if (o.c_S == 0.0) o.c_S = 4.0 * kPi;
+  }
+  if (!std::isfinite(o.c_S)) return fail(ORI_ERR_INVALID_ARG, "c_S must be finite");
+
+  ori_plan_s* p = new (std::nothrow) ori_plan_s();
+  if (!p) return fail(ORI_ERR_OOM, "host allocation failed");
+  ori_status st = ORI_OK;
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  do {
+    if (cudaGetDevice(&p->device) != cudaSuccess) { st = fail(ORI_ERR_CUDA, "cudaGetDevice failed"); break; }
+    p->n = int(n);
+    p->L = 4;
+    while (p->L < 2 * p->n) p->L *= 2;
+    p->H = p->L / 2 + 1;
+    p->n3 = (long long)n * n * n;
+    p->k = k;
+    p->side = dom->side;
+    p->d = dom->side / double(n);
+    for (int i = 0; i < 3; ++i) p->origin[i] = dom->origin[i];
+    p->c_S = o.c_S;
+    p->mem_cap = o.mem_cap;
+    cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    p->vec_grid = std::max(1, p->sm_count) * 8;
+    if (cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->evj, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
+      st = fail(ORI_ERR_CUDA, "stream/event creation failed");
+      break;
+    }
+    const size_t n3 = size_t(p->n3);
+    const size_t H3 = size_t(p->H) * p->H * p->H;
+    const size_t t1 = size_t(p->n) * p->n * p->L, t2 = size_t(p->n) * p->L * p->L;
+    if ((st = alloc_n(p, &p->h, n3)) || (st = alloc_n(p, &p->N, n3)) || (st = alloc_n(p, &p->w64, n3)) ||
+        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
+        (st = alloc_n(p, &p->ghat64, H3)) || (st = alloc_n(p, &p->ghat32, H3)) ||
+        (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
+        (st = alloc_n(p, &p->T1f, t1)) || (st = alloc_n(p, &p->T2f, t2)) ||
+        (st = alloc_n(p, &p->T1d, t1)) || (st = alloc_n(p, &p->T2d, t2)) ||
+        (st = alloc_n(p, &p->sc, 1)) || (st = alloc_n(p, &p->d_count, 1)))
+      break;
+    unsigned bx32 = 0, bx64 = 0;
+    if ((st = setup_kernels<float>(p->L, &bx32, p->n)) || (st = setup_kernels<double>(p->L, &bx64, p->n))) break;
+    p->npartials = std::max<size_t>({size_t(bx32), size_t(bx64), size_t(2 * p->vec_grid)}) + 16;
+    if ((st = alloc_n(p, &p->partials, p->npartials))) break;
+    if (cudaMallocHost(&p->h_sc, sizeof(Scalars)) != cudaSuccess) { st = fail(ORI_ERR_OOM, "cudaMallocHost failed"); break; }
+    if ((st = enter(p, user))) break;
+    ORI_CUDA(cudaMemsetAsync(p->sc, 0, sizeof(Scalars), p->ps));
+    {
+      cpx<double>* twd = new cpx<double>[p->L];
+      cpx<float>* twf = new cpx<float>[p->L];
+      host_twiddles<double>(p->L, twd);
+      host_twiddles<float>(p->L, twf);
+      cudaError_t e1 = cudaMemcpy(p->tw64, twd, sizeof(cpx<double>) * p->L, cudaMemcpyHostToDevice);
+      cudaError_t e2 = cudaMemcpy(p->tw32, twf, sizeof(cpx<float>) * p->L, cudaMemcpyHostToDevice);
+      delete[] twd;
+      delete[] twf;
+      if (e1 != cudaSuccess || e2 != cudaSuccess) { st = fail(ORI_ERR_CUDA, "twiddle upload failed"); break; }
+    }
+    if ((st = set_medium(p, h_dev, N_dev))) break;
+    if ((st = build_spectrum(p))) break;
+    if ((st = leave(p, user))) break;
+  } while (0);
+  if (st != ORI_OK) {
+    plan_free(p);
+    return st;
+  }
+  *out = p;
+  return ORI_OK;
+}
+
+ori_status ori_plan_set_medium(ori_plan_t p, const double* h_dev, const double* N_dev, void* stream) {
+  g_last_error.clear();
+  if (!p || !h_dev || !N_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(enter(p, user));
+  ORI_TRY(set_medium(p, h_dev, N_dev));
+  return leave(p, user);
+}
+
+ori_status ori_plan_destroy(ori_plan_t p) {
+  plan_free(p);
+  return ORI_OK;
+}
+
+ori_status ori_plan_info(ori_plan_t p, int64_t* n, int64_t* L, size_t* bytes) {
+  if (!p) return fail(ORI_ERR_INVALID_ARG, "plan is NULL");
+  if (n) *n = p->n;
+  if (L) *L = p->L;
+  if (bytes) *bytes = p->bytes;
+  return ORI_OK;
+}
+
+ori_status ori_matvec(ori_plan_t p, const double* x_dev, double* y_dev, int form, int precision,
+                      void* stream) {
+  g_last_error.clear();
+  if (!p || !x_dev || !y_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (form != ORI_FORM_A && form != ORI_FORM_B) return fail(ORI_ERR_INVALID_ARG, "form must be ORI_FORM_A or ORI_FORM_B");
+  if (precision != ORI_FP64 && precision != ORI_FP32) return fail(ORI_ERR_INVALID_ARG, "precision must be ORI_FP64 or ORI_FP32");
+  if (x_dev == y_dev) return fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(enter(p, user));
+  XArgs pro{}, epi{};
+  pro.x = x_dev;
+  epi.xin = x_dev;
+  epi.out = y_dev;
+  if (precision == ORI_FP64) {
+    pro.mode = PRO_SCALE;
+    pro.scale = form == ORI_FORM_A ? (const void*)p->w64 : (const void*)p->S64;
+    epi.mode = form == ORI_FORM_A ? EPI_PLUS : EPI_PLUS_S;
+    epi.scale = p->S64;
+    ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+  } else {
+    pro.mode = PRO_SCALE_D;
+    pro.scale = form == ORI_FORM_A ? (const void*)p->w32 : (const void*)p->S32;
+    epi.mode = form == ORI_FORM_A ? EPI_PLUS_D : EPI_PLUS_S_D;
+    epi.scale = p->S32;
+    ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+  }
+  return leave(p, user);
+}
+
+ori_status ori_matvec32(ori_plan_t p, const float* x_dev, float* y_dev, int form, void* stream) {
+  g_last_error.clear();
+  if (!p || !x_dev || !y_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (form != ORI_FORM_A && form != ORI_FORM_B) return fail(ORI_ERR_INVALID_ARG, "form must be ORI_FORM_A or ORI_FORM_B");
+  if (x_dev == y_dev) return fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(enter(p, user));
+  XArgs pro{}, epi{};
+  pro.x = x_dev;
+  pro.mode = PRO_SCALE;
+  pro.scale = form == ORI_FORM_A ? (const void*)p->w32 : (const void*)p->S32;
+  epi.xin = x_dev;
+  epi.out = y_dev;
+  epi.mode = form == ORI_FORM_A ? EPI_PLUS : EPI_PLUS_S;
+  epi.scale = p->S32;
+  ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+  return leave(p, user);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solver
+// ---------------------------------------------------------------------------
+
+static ori_status alloc_solver(ori_plan_s* p) {
+  if (p->b64) return ORI_OK;
+  const size_t n3 = size_t(p->n3);
+  ORI_TRY(alloc_n(p, &p->b64, n3));
+  ORI_TRY(alloc_n(p, &p->w, n3));
+  ORI_TRY(alloc_n(p, &p->r64, n3));
+  ORI_TRY(alloc_n(p, &p->u0, n3));
+  ORI_TRY(alloc_n(p, &p->p64, n3));
+  ORI_TRY(alloc_n(p, &p->q64, n3));
+  ORI_TRY(alloc_n(p, &p->x32, n3));
+  ORI_TRY(alloc_n(p, &p->r32, n3));
+  ORI_TRY(alloc_n(p, &p->p32, n3));
+  ORI_TRY(alloc_n(p, &p->q32, n3));
+  return ORI_OK;
+}
+
+template <class T>
+static ori_status cocg_iteration(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cpx<T>* q,
+                                 const cpx<T>* S, bool first) {
+  XArgs pro{}, epi{};
+  pro.mode = first ? PRO_COCG_FIRST : PRO_COCG;
+  pro.x = r;
+  pro.p = pp;
+  pro.scale = S;
+  pro.beta = &p->sc->beta;
+  epi.mode = EPI_COCG;
+  epi.xin = pp;
+  epi.out = q;
+  epi.scale = S;
+  ORI_TRY(run_conv<T>(p, pro, epi, FIN_ALPHA, p->ps, &p->sc->done));
+  k_cocg_update<T><<<p->vec_grid, 256, 0, p->ps>>>(x, pp, r, q, p->n3, p->sc, p->partials);
+  ORI_CUDA(cudaGetLastError());
+  return ORI_OK;
+}
+
+struct InnerResult {
+  int iters = 0;
+  int done = 0;
+  double relres_recur = 0;
+};
+
+// COCG on B x = r (r holds the right-hand side on entry, the residual on exit;
+// x starts at 0).  Stops when ||r|| <= tol ||r_0|| or after maxit iterations.
+template <class T>
+static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cpx<T>* q,
+                             const cpx<T>* S, double tol, int maxit, int check_every, bool use_graph,
+                             InnerResult* res) {
+  k_cocg_init<T><<<p->vec_grid, 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, tol, maxit);
+  ORI_CUDA(cudaGetLastError());
+  ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->h_sc->done == DONE_RUNNING && maxit > 0) {
+    ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, true));
+    cudaGraphExec_t& gexec = sizeof(T) == 4 ? p->graph_f : p->graph_d;
+    int& glen = sizeof(T) == 4 ? p->graph_f_len : p->graph_d_len;
+    if (use_graph && (gexec == nullptr || glen != check_every)) {
+      if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+      cudaGraph_t g = nullptr;
+      ORI_CUDA(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal));
+      ori_status cs = ORI_OK;
+      for (int i = 0; i < check_every && cs == ORI_OK; ++i) cs = cocg_iteration<T>(p, x, r, pp, q, S, false);
+      cudaError_t ee = cudaStreamEndCapture(p->ps, &g);
+      if (cs != ORI_OK) { if (g) cudaGraphDestroy(g); return cs; }
+      if (ee != cudaSuccess) return fail(ORI_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+      ee = cudaGraphInstantiate(&gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ee != cudaSuccess) { gexec = nullptr; return fail(ORI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee)); }
+      glen = check_every;
+    }
+    int launched = 1;
+    for (;;) {
+      ORI_CUDA(cudaMemcpyAsync(&p->h_sc->done, &p->sc->done, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->ps));
+      ORI_CUDA(cudaStreamSynchronize(p->ps));
+      if (p->h_sc->done != DONE_RUNNING || launched >= maxit) break;
+      if (use_graph) {
+        ORI_CUDA(cudaGraphLaunch(gexec, p->ps));
+      } else {
+        for (int i = 0; i < check_every; ++i) ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, false));
+      }
+      launched += check_every;
+    }
+  }
+  ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  res->iters = p->h_sc->iter;
+  res->done = p->h_sc->done;
+  res->relres_recur = p->h_sc->rnorm2_0 > 0 ? std::sqrt(p->h_sc->rnorm2 / p->h_sc->rnorm2_0) : 0.0;
+  return ORI_OK;
+}
+
+// r64 = b64 - B w in FP64; returns ||r64||.
+static ori_status fp64_residual(ori_plan_s* p, double* rnorm) {
+  XArgs pro{}, epi{};
+  pro.mode = PRO_SCALE;
+  pro.x = p->w;
+  pro.scale = p->S64;
+  epi.mode = EPI_RESID;
+  epi.xin = p->w;
+  epi.bvec = p->b64;
+  epi.out = p->r64;
+  epi.scale = p->S64;
+  ORI_TRY(run_conv<double>(p, pro, epi, FIN_SUM, p->ps, nullptr));
+  ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  *rnorm = std::sqrt(p->h_sc->sum.x);
+  return ORI_OK;
+}
+
+static ori_status status_of(int done) {
+  switch (done) {
+    case DONE_CONVERGED: return ORI_OK;
+    case DONE_BREAKDOWN: return ORI_ERR_BREAKDOWN;
+    case DONE_NONFINITE: return ORI_ERR_NONFINITE;
+    default: return ORI_ERR_NOT_CONVERGED;
+  }
+}
+
+// Solve B w = b64 (b64 and ||b64|| ready on the device / in bnorm); w -> p->w.
+static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, ori_solve_info* info) {
+  info->iters = 0;
+  info->outer_iters = 0;
+  info->fp64_matvecs = 0;
+  const long long n3 = p->n3;
+  const size_t bytes64 = size_t(n3) * sizeof(cpx<double>);
+  if (bnorm == 0.0) {
+    ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
+    info->relres = 0.0;
+    info->relres_recur = 0.0;
+    info->status = ORI_OK;
+    return ORI_OK;
+  }
+  const bool graph = o.use_graph != 0;
+  if (o.precision == ORI_FP64) {
+    ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+    InnerResult ir;
+    ORI_TRY(cocg_inner<double>(p, p->w, p->r64, p->p64, p->q64, p->S64, o.tol, o.maxit, o.check_every, graph, &ir));
+    info->iters = ir.iters;
+    info->outer_iters = 1;
+    info->relres_recur = ir.relres_recur;
+    double rn = 0;
+    ORI_TRY(fp64_residual(p, &rn));
+    info->fp64_matvecs = 1;
+    info->relres = rn / bnorm;
+    info->status = ir.done == DONE_CONVERGED ? (info->relres <= 10 * o.tol ? ORI_OK : ORI_ERR_NOT_CONVERGED)
+                                             : status_of(ir.done);
+    return ORI_OK;
+  }
+  // mixed: FP32 COCG on the normalised FP64 residual, FP64 refinement
+  ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
+  ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+  double rn = bnorm;
+  int total = 0;
+  int last_done = DONE_CONVERGED;
+  double last_recur = 0;
+  int outer = 0;
+  while (rn > o.tol * bnorm && outer < o.max_outer && total < o.maxit) {
+    k_normalise_to_f32<<<p->vec_grid, 256, 0, p->ps>>>(p->r64, p->r32, n3, 1.0 / rn);
+    ORI_CUDA(cudaGetLastError());
+    const double want = 0.5 * o.tol * bnorm / rn;
+    const double tin = std::min(0.5, std::max(o.inner_tol, want));
+    InnerResult ir;
+    ORI_TRY(cocg_inner<float>(p, p->x32, p->r32, p->p32, p->q32, p->S32, tin, o.maxit - total, o.check_every, graph, &ir));
+    total += ir.iters;
+    last_done = ir.done;
+    last_recur = ir.relres_recur;
+    ++outer;
+    if (ir.done == DONE_NONFINITE) break;
+    k_accumulate<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->x32, n3, rn);
+    ORI_CUDA(cudaGetLastError());
+    double rn_new = 0;
+    ORI_TRY(fp64_residual(p, &rn_new));
+    info->fp64_matvecs += 1;
+    const bool stalled = rn_new > 0.9 * rn;
+    rn = rn_new;
+    if (stalled && ir.done != DONE_CONVERGED) break;
+  }
+  info->iters = total;
+  info->outer_iters = outer;
+  info->relres = rn / bnorm;
+  info->relres_recur = last_recur;
+  if (info->relres <= o.tol) info->status = ORI_OK;
+  else if (last_done == DONE_NONFINITE) info->status = ORI_ERR_NONFINITE;
+  else if (last_done == DONE_BREAKDOWN) info->status = ORI_ERR_BREAKDOWN;
+  else info->status = ORI_ERR_NOT_CONVERGED;
+  return ORI_OK;
+}
+
+static ori_status check_solve_opts(const ori_solve_opts* in, ori_solve_opts* o) {
+  ori_default_solve_opts(o);
+  if (in) *o = *in;
+  if (!std::isfinite(o->tol) || o->tol <= 0) return fail(ORI_ERR_INVALID_ARG, "tol must be finite and > 0");
+  if (o->maxit < 0) return fail(ORI_ERR_INVALID_ARG, "maxit must be >= 0");
+  if (o->precision != ORI_FP64 && o->precision != ORI_MIXED)
+    return fail(ORI_ERR_INVALID_ARG, "precision must be ORI_FP64 or ORI_MIXED");
+  if (!std::isfinite(o->inner_tol) || o->inner_tol <= 0 || o->inner_tol >= 1)
+    return fail(ORI_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+  if (o->max_outer < 1) return fail(ORI_ERR_INVALID_ARG, "max_outer must be >= 1");
+  if (o->check_every < 1 || o->check_every > 1024) return fail(ORI_ERR_INVALID_ARG, "check_every must be in [1, 1024]");
+  if (!finite3(o->alpha)) return fail(ORI_ERR_INVALID_ARG, "alpha must be finite");
+  return ORI_OK;
+}
+
+extern "C" {
+
+ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, const ori_solve_opts* opts,
+                          ori_solve_info* info_out, void* stream) {
+  g_last_error.clear();
+  if (!p || !u_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  ori_solve_opts o;
+  ORI_TRY(check_solve_opts(opts, &o));
+  double an = std::sqrt(o.alpha[0] * o.alpha[0] + o.alpha[1] * o.alpha[1] + o.alpha[2] * o.alpha[2]);
+  double al[3] = {0.0, 0.0, 1.0};
+  if (an > 0) for (int i = 0; i < 3; ++i) al[i] = o.alpha[i] / an;
+  ori_solve_info info{};
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(alloc_solver(p));
+  ORI_TRY(enter(p, user));
+  ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
+  k_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0, p->b64,
+                                          p->n, p->d, p->origin[0], p->origin[1], p->origin[2], p->k,
+                                          al[0], al[1], al[2], p->sc, p->partials);
+  ORI_CUDA(cudaGetLastError());
+  ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  const double bnorm = std::sqrt(p->h_sc->sum.x);
+  ORI_TRY(solve_B(p, bnorm, o, &info));
+  // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
+  if (p->zero_S == 0) {
+    k_recover<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->S64, reinterpret_cast<cpx<double>*>(u_dev), p->n3);
+    ORI_CUDA(cudaGetLastError());
+  } else {
+    XArgs pro{}, epi{};
+    pro.mode = PRO_SCALE;
+    pro.x = p->w;
+    pro.scale = p->S64;
+    epi.mode = EPI_RECOVER;
+    epi.xin = p->w;
+    epi.bvec = p->u0;
+    epi.out = u_dev;
+    epi.scale = p->S64;
+    ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+    info.fp64_matvecs += 1;
+  }
+  ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
+  ORI_CUDA(cudaEventSynchronize(p->ev1));
+  cudaEventElapsedTime(&info.ms, p->ev0, p->ev1);
+  ORI_TRY(leave(p, user));
+  if (info_out) *info_out = info;
+  if (info.status != ORI_OK)
+    return fail(ori_status(info.status), std::string("solve ended with status ") + ori_status_string(info.status));
+  return ORI_OK;
+}
+
+ori_status ori_adjoint_solve(ori_plan_t p, const double* u_dev, const double* econj_dev, double* grad_h_dev,
+                             double* grad_N_dev, const ori_solve_opts* opts, ori_solve_info* info_out,
+                             void* stream) {
+  g_last_error.clear();
+  if (!p || !u_dev || !econj_dev || !grad_h_dev || !grad_N_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (p->zero_S != 0) return fail(ORI_ERR_UNSUPPORTED, "the adjoint needs h N != 0 in every cell");
+  ori_solve_opts o;
+  ORI_TRY(check_solve_opts(opts, &o));
+  ori_solve_info info{};
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(alloc_solver(p));
+  ORI_TRY(enter(p, user));
+  ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
+  k_adj_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->S64, p->b64,
+                                              p->n3, p->sc, p->partials);
+  ORI_CUDA(cudaGetLastError());
+  ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  const double bnorm = std::sqrt(p->h_sc->sum.x);
+  ORI_TRY(solve_B(p, bnorm, o, &info));
+  k_gradient<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->w,
+                                               reinterpret_cast<const cpx<double>*>(u_dev), p->S64, p->h, p->N,
+                                               reinterpret_cast<cpx<double>*>(grad_h_dev), grad_N_dev, p->n3);
+  ORI_CUDA(cudaGetLastError());
+  ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
+  ORI_CUDA(cudaEventSynchronize(p->ev1));
+  cudaEventElapsedTime(&info.ms, p->ev0, p->ev1);
+  ORI_TRY(leave(p, user));
+  if (info_out) *info_out = info;
+  if (info.status != ORI_OK)
+    return fail(ori_status(info.status), std::string("adjoint solve ended with status ") + ori_status_string(info.status));
+  return ORI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,425 @@
+// passes_impl.cuh - kernels of the five FFT passes and their launchers.
+// Included by one translation unit per precision (passes_f32.cu, passes_f64.cu).
+#pragma once
+
+#include "passes.cuh"
+#include "scalars.cuh"
+
+namespace ori {
+
+// ---------------------------------------------------------------------------
+// Prologue of the X forward pass: the value of the (zero-padded) field that
+// enters the transform at cell (line, j) with j < n.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ int signed_offset(int j, int L) { return j <= L / 2 ? j : j - L; }
+
+template <class T>
+__device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int j, int L) {
+  const long long i = line * a.n + j;
+  switch (a.mode) {
+    case PRO_SCALE: {
+      const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+      const cpx<T> v = reinterpret_cast<const cpx<T>*>(a.x)[i];
+      return cmul(s, v);
+    }
+    case PRO_SCALE_D: {
+      const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+      const cpx<double> v = reinterpret_cast<const cpx<double>*>(a.x)[i];
+      return cmul(s, ccast<T>(v));
+    }
+    case PRO_COCG_FIRST: {
+      const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+      const cpx<T> r = reinterpret_cast<const cpx<T>*>(a.x)[i];
+      reinterpret_cast<cpx<T>*>(a.p)[i] = r;
+      return cmul(s, r);
+    }
+    case PRO_COCG: {
+      const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+      const cpx<T> r = reinterpret_cast<const cpx<T>*>(a.x)[i];
+      cpx<T>* pp = reinterpret_cast<cpx<T>*>(a.p) + i;
+      const double2 bd = *reinterpret_cast<const double2*>(a.beta);
+      const cpx<T> b = {T(bd.x), T(bd.y)};
+      const cpx<T> p = r + cmul(b, *pp);
+      *pp = p;
+      return cmul(s, p);
+    }
+    default: {  // PRO_KERNEL: kernel cube entry at signed offsets (FP64)
+      const int l3 = int(line / a.lines_per_plane), l2 = int(line % a.lines_per_plane);
+      const int s1 = signed_offset<T>(j, L), s2 = signed_offset<T>(l2, L), s3 = signed_offset<T>(l3, L);
+      if (abs(s1) >= a.n || abs(s2) >= a.n || abs(s3) >= a.n) return czero<T>();
+      const long long r2 = (long long)s1 * s1 + (long long)s2 * s2 + (long long)s3 * s3;
+      if (r2 == 0) return czero<T>();           // p = q is excluded from the sum
+      const double r = a.d * sqrt(double(r2));
+      double sn, cs;
+      sincos(a.k * r, &sn, &cs);
+      const double g = 1.0 / (4.0 * kPi * r);   // G = exp(ikr) / (4 pi r)
+      return {T(cs * g), T(sn * g)};
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// X forward pass (contiguous lines): x[line][0..n) -> T1[line][0..L)
+// ---------------------------------------------------------------------------
+template <class T, int L, int C, bool HALF>
+__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xfwd(XArgs a) {
+  using TL = Tile<L, C, T>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
+  constexpr int PK = TL::PK, PC = TL::PC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const int tid = threadIdx.x;
+
+  int c, j2;
+  map_t<LAYOUT_CONTIG, C, L2>(tid, c, j2);
+  const long long line = (long long)blockIdx.x * C + c;
+  const bool ok = line < a.nlines;
+  cpx<T> r[L1];
+#pragma unroll
+  for (int j1 = 0; j1 < L1; ++j1) {
+    r[j1] = czero<T>();
+    if (!HALF || j1 < L1 / 2) {
+      const int j = j1 * L2 + j2;
+      if (ok && j < a.n_in) r[j1] = x_prologue<T>(a, line, j, L);
+    }
+  }
+  dft<L1, -1, HALF>(r);
+#pragma unroll
+  for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
+#pragma unroll
+  for (int k1 = 0; k1 < L1; ++k1) sm[c * PC + k1 * PK + j2] = r[k1];
+  __syncthreads();
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.fft_out);
+#pragma unroll
+  for (int it = 0; it < L1 / L2; ++it) {
+    int c2, k1;
+    map_s<LAYOUT_CONTIG, C, L1>(tid + it * NT, c2, k1);
+    cpx<T> b[L2];
+#pragma unroll
+    for (int j = 0; j < L2; ++j) b[j] = sm[c2 * PC + k1 * PK + j];
+    dft<L2, -1, false>(b);
+    const long long l2 = (long long)blockIdx.x * C + c2;
+    if (l2 < a.nlines) {
+      cpx<T>* o = out + l2 * a.line_len_out;
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) o[k1 + L1 * k2] = b[k2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// X inverse pass + operator epilogue: T1[line][0..L) -> y[line][0..n)
+// ---------------------------------------------------------------------------
+template <class T, int L, int C>
+__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc, int fin) {
+  using TL = Tile<L, C, T>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
+  constexpr int PKI = TL::PKI, PCI = TL::PCI;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+  __shared__ double2 red[32];
+  __shared__ int s_last;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in);
+  const int tid = threadIdx.x;
+
+  // stage A: DFT over k2 of X[k1 + L1 k2], twiddle, exchange
+#pragma unroll
+  for (int it = 0; it < L1 / L2; ++it) {
+    int c2, k1;
+    map_s<LAYOUT_CONTIG, C, L1>(tid + it * NT, c2, k1);
+    const long long l2 = (long long)blockIdx.x * C + c2;
+    cpx<T> b[L2];
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2)
+      b[k2] = l2 < a.nlines ? in[l2 * a.line_len_in + k1 + L1 * k2] : czero<T>();
+    dft<L2, +1, false>(b);
+#pragma unroll
+    for (int ja = 1; ja < L2; ++ja) b[ja] = twL_mul<+1>(b[ja], tw, (ja * k1) & (L - 1));
+#pragma unroll
+    for (int ja = 0; ja < L2; ++ja) sm[c2 * PCI + ja * PKI + k1] = b[ja];
+  }
+  __syncthreads();
+  // stage B: DFT over k1 -> x[ja + L2 jb]
+  int c, ja;
+  map_t<LAYOUT_CONTIG, C, L2>(tid, c, ja);
+  const long long line = (long long)blockIdx.x * C + c;
+  cpx<T> r[L1];
+#pragma unroll
+  for (int k1 = 0; k1 < L1; ++k1) r[k1] = sm[c * PCI + ja * PKI + k1];
+  dft<L1, +1, false>(r);
+
+  double2 acc = make_double2(0.0, 0.0);
+  if (line < a.nlines) {
+    cpx<T> accT = czero<T>();
+#pragma unroll
+    for (int jb = 0; jb < L1 / 2; ++jb) {
+      const int x = ja + L2 * jb;
+      if (x < a.n) {
+        const long long i = line * a.n + x;
+        const cpx<T> v = r[jb];
+        switch (a.mode) {
+          case EPI_PLUS: {
+            const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+            reinterpret_cast<cpx<T>*>(a.out)[i] = xi + v;
+          } break;
+          case EPI_PLUS_S: {
+            const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+            reinterpret_cast<cpx<T>*>(a.out)[i] = xi + cmul(s, v);
+          } break;
+          case EPI_PLUS_D: {
+            const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+            const cpx<double> vd = ccast<double>(v);
+            reinterpret_cast<cpx<double>*>(a.out)[i] = xi + vd;
+          } break;
+          case EPI_PLUS_S_D: {
+            const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+            reinterpret_cast<cpx<double>*>(a.out)[i] = xi + ccast<double>(cmul(s, v));
+          } break;
+          case EPI_COCG: {
+            const cpx<T> p = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+            const cpx<T> q = p + cmul(s, v);
+            reinterpret_cast<cpx<T>*>(a.out)[i] = q;
+            accT = accT + cmul(p, q);                 // p^T q, no conjugate
+          } break;
+          case EPI_RESID: {
+            const cpx<T> w = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+            const cpx<T> b = reinterpret_cast<const cpx<T>*>(a.bvec)[i];
+            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+            const cpx<T> rr = b - (w + cmul(s, v));
+            reinterpret_cast<cpx<T>*>(a.out)[i] = rr;
+            acc.x += double(rr.x) * double(rr.x) + double(rr.y) * double(rr.y);
+          } break;
+          default: {  // EPI_RECOVER: u = w / s where s != 0, else b - v
+            const cpx<T> w = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+            cpx<T> u;
+            if (s.x != T(0) || s.y != T(0)) {
+              const T den = s.x * s.x + s.y * s.y;
+              u = {(w.x * s.x + w.y * s.y) / den, (w.y * s.x - w.x * s.y) / den};
+            } else {
+              const cpx<T> b = reinterpret_cast<const cpx<T>*>(a.bvec)[i];
+              u = b - v;
+            }
+            reinterpret_cast<cpx<T>*>(a.out)[i] = u;
+          } break;
+        }
+      }
+    }
+    acc.x += double(accT.x);
+    acc.y += double(accT.y);
+  }
+  if (fin == FIN_NONE) return;
+  block_partial(acc, red, a.partials);
+  if (last_block_arrives(sc, s_last)) finalize(sc, a.partials, gridDim.x, fin, red);
+}
+
+// ---------------------------------------------------------------------------
+// Strided passes (Y forward, Z convolution, Y inverse, and the plan's full
+// forward transforms): a tile of C consecutive columns of L points.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int mirror_index(int k, int L) { return k <= L / 2 ? k : L - k; }
+
+template <class T, int L, int C, int SMODE, bool HALF>
+__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a) {
+  using TL = Tile<L, C, T>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
+  constexpr int PK = TL::PK, PC = TL::PC, PKI = TL::PKI, PCI = TL::PCI;
+  constexpr int NI = L1 / L2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const int tid = threadIdx.x;
+  const int outer = blockIdx.x / a.col_blocks;
+  const int cb = blockIdx.x - outer * a.col_blocks;
+  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + outer * a.in_outer + (long long)cb * C;
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + outer * a.out_outer + (long long)cb * C;
+  const int colmax = a.ncols - cb * C;
+
+  cpx<T> b[NI][L2];
+  if (SMODE != SMODE_INV) {
+    int c, j2;
+    map_t<LAYOUT_STRIDED, C, L2>(tid, c, j2);
+    cpx<T> r[L1];
+#pragma unroll
+    for (int j1 = 0; j1 < L1; ++j1) {
+      r[j1] = czero<T>();
+      if (!HALF || j1 < L1 / 2) {
+        const int j = j1 * L2 + j2;
+        if (c < colmax && j < a.n_in) r[j1] = in[(long long)j * a.in_pt + c];
+      }
+    }
+    dft<L1, -1, HALF>(r);
+#pragma unroll
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) sm[c * PC + k1 * PK + j2] = r[k1];
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+#pragma unroll
+      for (int j = 0; j < L2; ++j) b[it][j] = sm[c2 * PC + k1 * PK + j];
+      dft<L2, -1, false>(b[it]);
+    }
+    if (SMODE == SMODE_FWD) {
+#pragma unroll
+      for (int it = 0; it < NI; ++it) {
+        int c2, k1;
+        map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+        if (c2 < colmax) {
+#pragma unroll
+          for (int k2 = 0; k2 < L2; ++k2) {
+            const int k = k1 + L1 * k2;
+            if (k < a.n_out) out[(long long)k * a.out_pt + c2] = b[it][k2];
+          }
+        }
+      }
+      return;
+    }
+    // Z convolution: multiply by the spectrum entry of (kx, ky, kz)
+    const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
+    const int my = mirror_index(outer, L);
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+      const int mx = mirror_index(min(cb * C + c2, L - 1), L);
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) {
+        const int mz = mirror_index(k1 + L1 * k2, L);
+        const cpx<T> g = ldgc(gh + ((long long)mz * a.H + my) * a.H + mx);
+        b[it][k2] = cmul(b[it][k2], g);
+      }
+    }
+    __syncthreads();   // every read of the forward exchange is done
+  } else {
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2)
+        b[it][k2] = c2 < colmax ? in[(long long)(k1 + L1 * k2) * a.in_pt + c2] : czero<T>();
+    }
+  }
+  // inverse stage A: DFT over k2, twiddle, exchange
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    int c2, k1;
+    map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+    dft<L2, +1, false>(b[it]);
+#pragma unroll
+    for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
+#pragma unroll
+    for (int ja = 0; ja < L2; ++ja) sm[c2 * PCI + ja * PKI + k1] = b[it][ja];
+  }
+  __syncthreads();
+  // inverse stage B
+  int c, ja;
+  map_t<LAYOUT_STRIDED, C, L2>(tid, c, ja);
+  cpx<T> r[L1];
+#pragma unroll
+  for (int k1 = 0; k1 < L1; ++k1) r[k1] = sm[c * PCI + ja * PKI + k1];
+  dft<L1, +1, false>(r);
+  if (c < colmax) {
+#pragma unroll
+    for (int jb = 0; jb < L1; ++jb) {
+      const int j = ja + L2 * jb;
+      if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (dispatch on the padded length)
+// ---------------------------------------------------------------------------
+template <class T> constexpr int cols_strided() { return sizeof(T) == 4 ? 8 : 4; }
+template <class T, int L> constexpr int lines_contig() {
+  constexpr int want = (sizeof(T) == 4 ? 256 : 128) / Split<L>::L2;
+  return want < 1 ? 1 : want;
+}
+
+template <class T, int L, bool HALF>
+cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
+  constexpr int C = lines_contig<T, L>();
+  using TL = Tile<L, C, T>;
+  auto kfn = k_xfwd<T, L, C, HALF>;
+  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
+  const unsigned grid = unsigned((a.nlines + C - 1) / C);
+  kfn<<<grid, TL::NT, TL::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T, int L>
+cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
+  constexpr int C = lines_contig<T, L>();
+  using TL = Tile<L, C, T>;
+  auto kfn = k_xinv<T, L, C>;
+  const unsigned grid = unsigned((a.nlines + C - 1) / C);
+  if (nblocks) *nblocks = grid;
+  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
+  kfn<<<grid, TL::NT, TL::SMEM_BYTES, s>>>(a, sc, fin);
+  return cudaGetLastError();
+}
+
+template <class T, int L, int SMODE, bool HALF>
+cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
+  constexpr int C = cols_strided<T>();
+  using TL = Tile<L, C, T>;
+  auto kfn = k_strided<T, L, C, SMODE, HALF>;
+  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
+  a.col_blocks = (a.ncols + C - 1) / C;
+  const unsigned grid = unsigned(a.nouter) * unsigned(a.col_blocks);
+  kfn<<<grid, TL::NT, TL::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+#define ORI_FOR_EACH_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+template <class T>
+cudaError_t run_xfwd(int L, bool half, const XArgs& a, cudaStream_t s, bool setup) {
+  switch (L) {
+#define ORI_CASE(LL) \
+    case LL: return half ? launch_xfwd_L<T, LL, true>(a, s, setup) : launch_xfwd_L<T, LL, false>(a, s, setup);
+    ORI_FOR_EACH_L(ORI_CASE)
+#undef ORI_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T>
+cudaError_t run_xinv(int L, const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
+  switch (L) {
+#define ORI_CASE(LL) case LL: return launch_xinv_L<T, LL>(a, sc, fin, s, setup, nblocks);
+    ORI_FOR_EACH_L(ORI_CASE)
+#undef ORI_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T>
+cudaError_t run_strided(int L, int smode, bool half, const SArgs& a, cudaStream_t s, bool setup) {
+  switch (L) {
+#define ORI_CASE(LL)                                                                        \
+    case LL:                                                                                \
+      if (smode == SMODE_FWD) return half ? launch_strided_L<T, LL, SMODE_FWD, true>(a, s, setup) \
+                                          : launch_strided_L<T, LL, SMODE_FWD, false>(a, s, setup); \
+      if (smode == SMODE_INV) return launch_strided_L<T, LL, SMODE_INV, false>(a, s, setup); \
+      return launch_strided_L<T, LL, SMODE_ZCONV, true>(a, s, setup);
+    ORI_FOR_EACH_L(ORI_CASE)
+#undef ORI_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ori

@@ -1,0 +1,252 @@
+// vector_kernels.cuh - elementwise and reduction kernels of the solver:
+// medium set-up (S = sqrt(h N)), the spectrum extraction of the plan, the
+// right-hand side u0 = exp(ik alpha . x) (Eq. 2.4), the COCG vector update,
+// the mixed-precision refinement steps and the adjoint gradient.
+#pragma once
+
+#include "common.cuh"
+#include "passes.cuh"
+#include "scalars.cuh"
+
+namespace ori {
+
+// Principal square root of a + ib (Re >= 0), from |z| by the half-angle formulas.
+__device__ __forceinline__ cpx<double> csqrt_principal(cpx<double> z) {
+  if (z.x == 0.0 && z.y == 0.0) return {0.0, 0.0};
+  const double m = hypot(z.x, z.y);
+  const double t = sqrt(0.5 * (m + fabs(z.x)));
+  if (z.x >= 0.0) return {t, z.y / (2.0 * t)};
+  return {fabs(z.y) / (2.0 * t), copysign(t, z.y)};
+}
+
+__device__ __forceinline__ cpx<double> cdivd(cpx<double> a, cpx<double> b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den};
+}
+
+// w = h N (A form scale), S = sqrt(h N) (B form scale), both precisions;
+// counts cells with S == 0 and cells with h == 0 or N == 0.
+__global__ void k_medium(const cpx<double>* __restrict__ h, const double* __restrict__ N,
+                         cpx<double>* w64, cpx<double>* S64, cpx<float>* w32, cpx<float>* S32,
+                         long long n3, unsigned long long* zero_count) {
+  unsigned long long zs = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<double> hv = h[i];
+    const double nv = N[i];
+    const cpx<double> w = {hv.x * nv, hv.y * nv};
+    const cpx<double> s = csqrt_principal(w);
+    w64[i] = w;
+    S64[i] = s;
+    w32[i] = ccast<float>(w);
+    S32[i] = ccast<float>(s);
+    if (w.x == 0.0 && w.y == 0.0) ++zs;
+  }
+  if (zs) atomicAdd(zero_count, zs);
+}
+
+// Spectrum of the kernel cube: keep the (L/2+1)^3 distinct entries of the
+// even cube and fold in c_S |Delta| / L^3.
+__global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>* g64,
+                               cpx<float>* g32, int L, int H, double scale) {
+  const long long total = (long long)H * H * H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m1 = int(i % H), m2 = int((i / H) % H), m3 = int(i / ((long long)H * H));
+    const cpx<double> v = cube[((long long)m3 * L + m2) * L + m1];
+    const cpx<double> s = {v.x * scale, v.y * scale};
+    g64[i] = s;
+    g32[i] = ccast<float>(s);
+  }
+}
+
+// Reduction helper for the vector kernels: two double2 partials per block.
+__device__ __forceinline__ void block_partial2(double2 a, double2 b, double2* red,
+                                               double2* partials) {
+  a = warp_sum2(a);
+  b = warp_sum2(b);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) { red[w] = a; red[32 + w] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 sa = make_double2(0.0, 0.0), sb = make_double2(0.0, 0.0);
+    for (int i = 0; i < nw; ++i) {
+      sa.x += red[i].x; sa.y += red[i].y;
+      sb.x += red[32 + i].x; sb.y += red[32 + i].y;
+    }
+    partials[2 * blockIdx.x] = sa;
+    partials[2 * blockIdx.x + 1] = sb;
+  }
+}
+
+// Right-hand side of the symmetrised system: u0 = rhs or exp(ik alpha . x_p)
+// (Eq. 2.4, cell centres), b = S u0; sum |b|^2 -> sc->sum.x.
+__global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __restrict__ S,
+                      cpx<double>* u0, cpx<double>* b, int n, double d, double ox, double oy,
+                      double oz, double k, double ax, double ay, double az, Scalars* sc,
+                      double2* partials) {
+  __shared__ double2 red[64];
+  __shared__ int s_last;
+  const long long n3 = (long long)n * n * n;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    cpx<double> u;
+    if (rhs != nullptr) {
+      u = rhs[i];
+    } else {
+      const int ix = int(i % n), iy = int((i / n) % n), iz = int(i / ((long long)n * n));
+      const double x = ox + (ix + 0.5) * d, y = oy + (iy + 0.5) * d, z = oz + (iz + 0.5) * d;
+      double sn, cs;
+      sincos(k * (ax * x + ay * y + az * z), &sn, &cs);
+      u = {cs, sn};
+    }
+    u0[i] = u;
+    const cpx<double> bv = cmul(S[i], u);
+    b[i] = bv;
+    acc += bv.x * bv.x + bv.y * bv.y;
+  }
+  block_partial(make_double2(acc, 0.0), red, partials);
+  if (last_block_arrives(sc, s_last)) finalize(sc, partials, gridDim.x, FIN_SUM, red);
+}
+
+// Adjoint right-hand side b = S^-1 conj(e); sum |b|^2 -> sc->sum.x.
+__global__ void k_adj_rhs(const cpx<double>* __restrict__ ec, const cpx<double>* __restrict__ S,
+                          cpx<double>* b, long long n3, Scalars* sc, double2* partials) {
+  __shared__ double2 red[64];
+  __shared__ int s_last;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<double> bv = cdivd(ec[i], S[i]);
+    b[i] = bv;
+    acc += bv.x * bv.x + bv.y * bv.y;
+  }
+  block_partial(make_double2(acc, 0.0), red, partials);
+  if (last_block_arrives(sc, s_last)) finalize(sc, partials, gridDim.x, FIN_SUM, red);
+}
+
+// COCG start: x = 0, rho = r^T r, ||r||^2; sets tol/maxit and the flags.
+template <class T>
+__global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n3, Scalars* sc,
+                            double2* partials, double tol, int maxit) {
+  __shared__ double2 red[64];
+  __shared__ int s_last;
+  double2 rho = make_double2(0.0, 0.0);
+  double nn = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<T> rv = r[i];
+    x[i] = czero<T>();
+    const double a = double(rv.x), b = double(rv.y);
+    rho.x += a * a - b * b;
+    rho.y += 2.0 * a * b;
+    nn += a * a + b * b;
+  }
+  block_partial2(rho, make_double2(nn, 0.0), red, partials);
+  if (last_block_arrives(sc, s_last)) {
+    if (threadIdx.x == 0) {
+      sc->tol = tol;
+      sc->maxit = maxit;
+    }
+    finalize(sc, partials, gridDim.x, FIN_INIT, red);
+  }
+}
+
+// COCG update: x += alpha p, r -= alpha q; rho' = r^T r and ||r||^2 of the new
+// residual (sums in T over 8 elements per thread, then in FP64).
+template <class T>
+__global__ void k_cocg_update(cpx<T>* __restrict__ x, const cpx<T>* __restrict__ p,
+                              cpx<T>* __restrict__ r, const cpx<T>* __restrict__ q, long long n3,
+                              Scalars* sc, double2* partials) {
+  __shared__ double2 red[64];
+  __shared__ int s_last;
+  if (sc->done != 0) return;
+  const double2 ad = sc->alpha;
+  const cpx<T> al = {T(ad.x), T(ad.y)};
+  double2 rho = make_double2(0.0, 0.0);
+  double nn = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x; base < n3;
+       base += 8 * stride) {
+    cpx<T> rs = czero<T>();
+    T ns = T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long i = base + u * stride;
+      if (i < n3) {
+        const cpx<T> pv = p[i], qv = q[i];
+        cpx<T> xv = x[i], rv = r[i];
+        xv = xv + cmul(al, pv);
+        rv = rv - cmul(al, qv);
+        x[i] = xv;
+        r[i] = rv;
+        rs = rs + cmul(rv, rv);
+        ns += rv.x * rv.x + rv.y * rv.y;
+      }
+    }
+    rho.x += double(rs.x);
+    rho.y += double(rs.y);
+    nn += double(ns);
+  }
+  block_partial2(rho, make_double2(nn, 0.0), red, partials);
+  if (last_block_arrives(sc, s_last)) finalize(sc, partials, gridDim.x, FIN_UPDATE, red);
+}
+
+// Mixed refinement: r32 = r64 / ||r64||.
+__global__ void k_normalise_to_f32(const cpx<double>* __restrict__ r64, cpx<float>* r32,
+                                   long long n3, double inv) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<double> v = r64[i];
+    r32[i] = {float(v.x * inv), float(v.y * inv)};
+  }
+}
+
+// Mixed refinement: w += scale * d32.
+__global__ void k_accumulate(cpx<double>* w, const cpx<float>* __restrict__ d32, long long n3,
+                             double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<float> dv = d32[i];
+    cpx<double> wv = w[i];
+    wv.x += scale * double(dv.x);
+    wv.y += scale * double(dv.y);
+    w[i] = wv;
+  }
+}
+
+// u = w / S (every S != 0).
+__global__ void k_recover(const cpx<double>* __restrict__ w, const cpx<double>* __restrict__ S,
+                          cpx<double>* u, long long n3) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x)
+    u[i] = cdivd(w[i], S[i]);
+}
+
+// Adjoint gradient: psi = S z, t = (conj(e) - psi) u,
+// grad_h = -2 conj(t / h), grad_N = -2 Re(t / N).
+__global__ void k_gradient(const cpx<double>* __restrict__ ec, const cpx<double>* __restrict__ z,
+                           const cpx<double>* __restrict__ u, const cpx<double>* __restrict__ S,
+                           const cpx<double>* __restrict__ h, const double* __restrict__ N,
+                           cpx<double>* gh, double* gN, long long n3) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<double> psi = cmul(S[i], z[i]);
+    const cpx<double> t = cmul(ec[i] - psi, u[i]);
+    const cpx<double> th = cdivd(t, h[i]);
+    gh[i] = {-2.0 * th.x, 2.0 * th.y};
+    gN[i] = -2.0 * t.x / N[i];
+  }
+}
+
+// Widen a complex64 vector to complex128 / narrow complex128 to complex64.
+__global__ void k_widen(const cpx<float>* __restrict__ a, cpx<double>* b, long long n3) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = ccast<double>(a[i]);
+}
+
+}  // namespace ori

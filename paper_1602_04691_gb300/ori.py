@@ -1,0 +1,207 @@
+"""Python face of the C ABI: a Plan object over torch CUDA tensors.
+
+Every operation runs in libori.so on the GPU; this module only checks tensor
+types and passes pointers and the current CUDA stream.  The system is Eq. 2.19
+of the paper (RED; ORI when each cell holds one particle and N = 1):
+    u_q + c_S sum_{p != q} G(x_q, x_p) h_p N_p |Delta_p| u_p = u0_q.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import torch
+
+from . import _lib
+from ._lib import ORI_FORM_A, ORI_FORM_B, ORI_FP32, ORI_FP64, ORI_MIXED, OriError  # noqa: F401
+
+_FORMS = {"A": ORI_FORM_A, "B": ORI_FORM_B}
+_PREC = {"fp64": ORI_FP64, "fp32": ORI_FP32, "mixed": ORI_MIXED}
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return t.contiguous()
+
+
+def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_outer=8,
+               check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True) -> _lib.SolveOpts:
+    lib = _lib.load()
+    o = _lib.SolveOpts()
+    lib.ori_default_solve_opts(C.byref(o))
+    o.tol = float(tol)
+    o.precision = _PREC[precision]
+    o.maxit = int(maxit)
+    o.inner_tol = float(inner_tol)
+    o.max_outer = int(max_outer)
+    o.check_every = int(check_every)
+    for i in range(3):
+        o.alpha[i] = float(alpha[i])
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+class Plan:
+    """Operator for one grid (n^3 cells of a cube), wave number k and medium (h, N).
+
+    h: complex128 CUDA tensor of n^3 impedances, N: float64 CUDA tensor of n^3
+    densities, both C-ordered [z][y][x].  c_S defaults to 4 pi (spheres)."""
+
+    def __init__(self, n: int, k: float, h: torch.Tensor, N: torch.Tensor, side: float = 1.0,
+                 origin=(0.0, 0.0, 0.0), c_S: float | None = None, mem_cap: int = 0, stream=None):
+        lib = _lib.load()
+        self.n = int(n)
+        self.k = float(k)
+        self.side = float(side)
+        self.origin = tuple(float(v) for v in origin)
+        self.c_S = 4.0 * math.pi if c_S is None else float(c_S)
+        m = self.n ** 3
+        h = _need(h, torch.complex128, m, "h")
+        N = _need(N, torch.float64, m, "N")
+        self.device = h.device
+        dom = _lib.Domain()
+        for i in range(3):
+            dom.origin[i] = self.origin[i]
+        dom.side = self.side
+        po = _lib.PlanOpts()
+        lib.ori_default_plan_opts(C.byref(po))
+        po.c_S = self.c_S
+        po.mem_cap = int(mem_cap)
+        handle = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = lib.ori_plan(self.n, self.k, C.byref(dom), h.data_ptr(), N.data_ptr(), C.byref(po),
+                              _stream_ptr(stream), C.byref(handle))
+        _lib.check(st, "ori_plan")
+        self._h = handle
+        nn, LL, by = C.c_int64(), C.c_int64(), C.c_size_t()
+        lib.ori_plan_info(self._h, C.byref(nn), C.byref(LL), C.byref(by))
+        self.L = int(LL.value)
+        self.bytes = int(by.value)
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().ori_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    # -- medium ----------------------------------------------------------------
+    def set_medium(self, h: torch.Tensor, N: torch.Tensor, stream=None):
+        m = self.n ** 3
+        h = _need(h, torch.complex128, m, "h")
+        N = _need(N, torch.float64, m, "N")
+        _lib.check(_lib.load().ori_plan_set_medium(self.handle, h.data_ptr(), N.data_ptr(),
+                                                   _stream_ptr(stream)), "ori_plan_set_medium")
+
+    # -- operator ----------------------------------------------------------------
+    def matvec(self, x: torch.Tensor, form: str = "A", precision: str = "fp64", stream=None):
+        """y = A x (form "A", Eq. 2.19) or B x = x + S K (S x) (form "B")."""
+        x = _need(x, torch.complex128, self.n ** 3, "x")
+        y = torch.empty_like(x)
+        _lib.check(_lib.load().ori_matvec(self.handle, x.data_ptr(), y.data_ptr(), _FORMS[form],
+                                          _PREC[precision], _stream_ptr(stream)), "ori_matvec")
+        return y
+
+    def matvec32(self, x: torch.Tensor, form: str = "B", out: torch.Tensor | None = None, stream=None):
+        """The FP32 operator on complex64 vectors (what the mixed solver iterates with)."""
+        x = _need(x, torch.complex64, self.n ** 3, "x")
+        y = torch.empty_like(x) if out is None else out
+        _lib.check(_lib.load().ori_matvec32(self.handle, x.data_ptr(), y.data_ptr(), _FORMS[form],
+                                            _stream_ptr(stream)), "ori_matvec32")
+        return y
+
+    # -- solves ------------------------------------------------------------------
+    def solve(self, rhs: torch.Tensor | None = None, out: torch.Tensor | None = None,
+              raise_on_failure: bool = True, stream=None, **kw):
+        """Solve A u = rhs (rhs None: plane wave exp(ik alpha . x)); returns (u, info dict)."""
+        m = self.n ** 3
+        if rhs is not None:
+            rhs = _need(rhs, torch.complex128, m, "rhs")
+        u = torch.empty(m, dtype=torch.complex128, device=self.device) if out is None else out
+        o = solve_opts(**kw)
+        info = _lib.SolveInfo()
+        st = _lib.load().ori_cocg_solve(self.handle, rhs.data_ptr() if rhs is not None else None,
+                                        u.data_ptr(), C.byref(o), C.byref(info), _stream_ptr(stream))
+        if raise_on_failure:
+            _lib.check(st, "ori_cocg_solve")
+        d = info.as_dict()
+        d["returned"] = st
+        return u, d
+
+    def adjoint(self, u: torch.Tensor, econj: torch.Tensor, raise_on_failure: bool = True,
+                stream=None, **kw):
+        """Gradient of J = sum_obs |u_o - t_o|^2 w.r.t. h and N; econj = conj(u - t) on the
+        observation cells and 0 elsewhere.  Returns (grad_h, grad_N, info)."""
+        m = self.n ** 3
+        u = _need(u, torch.complex128, m, "u")
+        econj = _need(econj, torch.complex128, m, "econj")
+        gh = torch.empty(m, dtype=torch.complex128, device=self.device)
+        gN = torch.empty(m, dtype=torch.float64, device=self.device)
+        o = solve_opts(**kw)
+        info = _lib.SolveInfo()
+        st = _lib.load().ori_adjoint_solve(self.handle, u.data_ptr(), econj.data_ptr(), gh.data_ptr(),
+                                           gN.data_ptr(), C.byref(o), C.byref(info), _stream_ptr(stream))
+        if raise_on_failure:
+            _lib.check(st, "ori_adjoint_solve")
+        d = info.as_dict()
+        d["returned"] = st
+        return gh, gN, d
+
+
+class OriSolve(torch.autograd.Function):
+    """u = A(h, N)^-1 rhs with a hand-written adjoint backward.
+
+    The forward solution is kept for the backward (one checkpoint, no
+    per-iteration storage); the backward is one more COCG solve on the same
+    plan (A^T = S B S^-1) plus elementwise products."""
+
+    @staticmethod
+    def forward(ctx, h, N, plan: Plan, rhs, kw):
+        plan.set_medium(h.detach(), N.detach())
+        u, info = plan.solve(rhs, **kw)
+        ctx.plan = plan
+        ctx.kw = kw
+        ctx.info = info
+        ctx.save_for_backward(u)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        # grad_u = dL/dRe u + i dL/dIm u; dL = Re(conj(grad_u) du) = 2 Re(conj(e) du), e = grad_u / 2
+        econj = torch.conj(grad_u).contiguous() * 0.5
+        gh, gN, _ = ctx.plan.adjoint(u, econj.to(torch.complex128), **ctx.kw)
+        return gh, gN, None, None, None
+
+
+def solve_autograd(plan: Plan, h: torch.Tensor, N: torch.Tensor, rhs=None, **kw):
+    """Differentiable solve: gradients flow to h (complex) and N (real)."""
+    return OriSolve.apply(h, N, plan, rhs, kw)

@@ -1,0 +1,78 @@
+"""The C ABI library loads and exports every function include/ori.h declares
+(no compute calls: these run without a GPU)."""
+
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ori.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ori_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1602_04691_gb300 import build as b
+    if not os.path.exists(b.LIB) and shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no nvcc to build libori.so")
+    return b.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("ori_plan", "ori_matvec", "ori_cocg_solve", "ori_adjoint_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_declares_every_export(libpath):
+    from paper_1602_04691_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == _declared()
+    lib = _lib.load()
+    assert lib.ori_abi_version() == 1
+    assert lib.ori_status_string(0) == b"ok"
+    assert lib.ori_status_string(5) == b"COCG breakdown"
+
+
+def test_default_options_host_only(libpath):
+    from paper_1602_04691_gb300 import _lib
+    lib = _lib.load()
+    o = _lib.SolveOpts()
+    lib.ori_default_solve_opts(ctypes.byref(o))
+    assert o.tol == 1e-6 and o.precision == _lib.ORI_MIXED and o.check_every == 8
+    assert tuple(o.alpha) == (0.0, 0.0, 1.0)
+
+
+def test_invalid_arguments_rejected_before_device_work(libpath):
+    """Argument checks run on the host and return a status (no GPU needed)."""
+    from paper_1602_04691_gb300 import _lib
+    lib = _lib.load()
+    dom = _lib.Domain()
+    dom.side = 1.0
+    h = ctypes.c_void_p()
+    st = lib.ori_plan(1, 1.0, ctypes.byref(dom), 1, 1, None, None, ctypes.byref(h))
+    assert st == _lib.ORI_ERR_INVALID_ARG and b"n must be" in lib.ori_last_error()
+    st = lib.ori_plan(8, -1.0, ctypes.byref(dom), 1, 1, None, None, ctypes.byref(h))
+    assert st == _lib.ORI_ERR_INVALID_ARG
+    st = lib.ori_plan(8, float("nan"), ctypes.byref(dom), 1, 1, None, None, ctypes.byref(h))
+    assert st == _lib.ORI_ERR_INVALID_ARG
+    st = lib.ori_plan(8, 1.0, ctypes.byref(dom), None, 1, None, None, ctypes.byref(h))
+    assert st == _lib.ORI_ERR_INVALID_ARG
+    dom.side = 0.0
+    st = lib.ori_plan(8, 1.0, ctypes.byref(dom), 1, 1, None, None, ctypes.byref(h))
+    assert st == _lib.ORI_ERR_INVALID_ARG
+    assert lib.ori_matvec(None, 1, 2, 0, 0, None) == _lib.ORI_ERR_INVALID_ARG
+    assert lib.ori_cocg_solve(None, None, 1, None, None, None) == _lib.ORI_ERR_INVALID_ARG

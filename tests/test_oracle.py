@@ -182,6 +182,18 @@ def test_direct_sum_rows_equal_dense_matrix():
     assert rel(O.red_matvec_rows(x, rows, n, k, h, N), (A @ x)[rows]) < 1e-14
 
 
+def test_grid_row_sums_equal_dense_rows():
+    """The memory-light row sums used at large n agree with the dense matrix."""
+    n, k, side = 6, 2.7, 1.4
+    h, N = inputs.random_h_N(n, 5)
+    x = inputs.random_complex(n ** 3, 6)
+    w = O.red_weights(h, N, side / n)
+    rows = np.array([0, 17, 100, 215])
+    A = O.red_matrix(n, k, h, N, side=side)
+    got = x[rows] + O.offdiag_sum_rows_grid(w * x, rows, n, k, side, planes_per_chunk=4)
+    assert rel(got, (A @ x)[rows]) < 1e-14
+
+
 def test_brute_force_tiny_grid():
     """n = 2 (8 cells) summed pair by pair in plain Python."""
     n, k, side = 2, 3.1, 0.7
