@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: the mixed-precision COCG solve of Eq. 2.19.
+
+Workload (one step = one solve): n = 512 cells per axis (P = 134,217,728 cells,
+1024^3 padded FFTs), unit cube, k = 5, plane wave alpha = (0, 0, 1), seeded
+h, N ~ U[0.5, 1.5] (inputs.random_h_N, seed 3), FP32 COCG with FP64 scalars
+inside FP64 iterative refinement, to relative residual 1e-6.  The plan (the
+kernel spectrum) is built once, outside the timed region, and reported apart.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+paper's algorithm restated in numpy) on a bounded sample instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Solve time to rel-res 1e-6 + FFT-matvec HBM GB/s at n=512, mixed vs FP64"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--k", type=float, default=5.0)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--matvec-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    except Exception:
+        return dict(PEAKS_FALLBACK, source="fallback")
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes per launch of each pass (complex element = 8 B in FP32,
+# 16 B in FP64; N = n^3 cells; H = L/2 + 1).  COCG-mode prologue/epilogue.
+# ---------------------------------------------------------------------------
+def alg_bytes(kind: str, n: int, L: int, cb: int) -> float:
+    N = n ** 3
+    T1 = n * n * L
+    T2 = n * L * L
+    H3 = (L // 2 + 1) ** 3
+    table = {}
+    # exact per-kind counts (the zero halves of the padded cubes are never read):
+    table["xfwd"] = (3 * N + N + T1) * cb        # read r, p, S; write p, T1 = [n][n][L]
+    table["yfwd"] = (T1 + T2) * cb               # read T1 = [n][n][L]; write T2 = [n][L][L]
+    table["zconv"] = (T2 + T2 + H3) * cb         # read and write T2 in place; spectrum once
+    table["yinv"] = (T2 + T1) * cb               # read T2; write T1
+    table["xinv"] = (T1 + 3 * N) * cb            # read T1, p, S; write q
+    table["update"] = 6 * N * cb                 # read x, p, r, q; write x, r
+    return float(table[kind])
+
+
+def matvec_alg_bytes(n: int, L: int, cb: int) -> float:
+    """Bytes of one standalone B-form matvec (y = x + S K(S x)): X fwd reads x, S and
+    writes T1; Y fwd; Z conv; Y inv; X inv reads T1, x, S and writes y."""
+    N, T1, T2, H3 = n ** 3, n * n * L, n * L * L, (L // 2 + 1) ** 3
+    return float(((2 * N + T1) + (T1 + T2) + (2 * T2 + H3) + (T2 + T1) + (T1 + 3 * N)) * cb)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1602_04691_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary, only if the kernel
+    sources are unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent:
+        return None
+    scale = (n / ent["n"]) ** 3 if ent.get("n") else 1.0
+    return ent["dram_bytes_per_launch"] * scale
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    rows.append({"sm": float(parts[1]), "max": float(parts[2]), "util": float(parts[4]),
+                                 "hw": parts[6], "hwt": parts[7], "swt": parts[8], "pcap": parts[9]})
+                except ValueError:
+                    continue
+        if not rows:
+            return None
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = set()
+        for r in load:
+            if r["hw"].lower() == "active":
+                reasons.add("hw_slowdown")
+            if r["hwt"].lower() == "active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"].lower() == "active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"].lower() == "active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(n_target: int, k: float, seed: int, tol: float, budget_s: float = 12.0):
+    """The oracle as it stands: the paper's algorithm in numpy (FFT matvec with
+    the mirror padding of size 2n-2, COCG) on the host.  Sample: its COCG
+    iteration count at n = 32 (same recipe, same k, tol), and the time of its
+    FFT matvec at n = 64, repeated for about `budget_s` seconds; the solve time
+    at n_target is (iterations + 1) * matvec time * (N log N of the padded
+    cubes at n_target) / (same at 64)."""
+    import numpy as np
+    import oracle as O
+    from paper_1602_04691_gb300 import inputs
+    t0 = time.perf_counter()
+    h32, N32 = inputs.random_h_N(32, seed)
+    _, iters, _ = O.solve_red_cocg_fft(32, k, h32, N32, tol=tol)
+    t_iters = time.perf_counter() - t0
+    ns = 64
+    h, N = inputs.random_h_N(ns, seed)
+    x = inputs.random_complex(ns ** 3, seed + 1)
+    c = O.kernel_cube(ns, k, 1.0 / ns)
+    reps, t1 = 0, time.perf_counter()
+    while True:
+        O.symmetrised_matvec_fft(x, ns, k, h, N, _c=c)
+        reps += 1
+        if time.perf_counter() - t1 > budget_s and reps >= 2:
+            break
+    t_mv = (time.perf_counter() - t1) / reps
+    Ls, Lt = 2 * ns - 2, 2 * n_target - 2
+    scale = (Lt ** 3 * math.log(Lt ** 3)) / (Ls ** 3 * math.log(Ls ** 3))
+    est = (iters + 1) * t_mv * scale
+    return {
+        "value": est, "unit": "s", "cores": 1, "kind": "oracle",
+        "sample": (f"oracle COCG iterations at n=32 ({iters}, tol {tol:g}, {t_iters:.1f} s) x oracle FFT "
+                   f"matvec time at n=64 ({t_mv * 1e3:.1f} ms, mean of {reps}) scaled to n={n_target} by padded "
+                   f"N log N ({scale:.0f}x); numpy FFT single-threaded; extrapolated"),
+    }
+
+
+# ---------------------------------------------------------------------------
+# Arms
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args.n, args.k, args.seed, args.tol, budget_s=1.0)
+    vals = []
+    last = None
+    for _ in range(max(1, args.steps)):
+        last = oracle_sample(args.n, args.k, args.seed, args.tol, budget_s=4.0)
+        vals.append(last["value"])
+    v = statistics.median(vals)
+    cpu = dict(last)
+    cpu["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args), "cpu_baseline": cpu,
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def workload_config(args):
+    n = args.n
+    L = 4
+    while L < 2 * n:
+        L *= 2
+    return {"workload": (f"mixed-precision COCG solve of Eq. 2.19 to relres {args.tol:g}, n={n} "
+                         f"(P={n ** 3:,} cells), {L}^3 padded FFTs, k={args.k:g}, unit cube, alpha=(0,0,1), "
+                         f"h,N ~ U[0.5,1.5] seed {args.seed}"),
+            "n": n, "L": L, "k": args.k, "tol": args.tol, "precision": "mixed FP32/FP64",
+            "l2": "inputs larger than L2 (each complex64 vector is n^3*8 B)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def ours_arm(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1602_04691_gb300 import Plan, inputs
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n, k = args.n, args.k
+    h_np, N_np = inputs.random_h_N(n, args.seed)
+    h_host = torch.from_numpy(h_np).pin_memory()
+    N_host = torch.from_numpy(N_np).pin_memory()
+    del h_np, N_np
+    h_dev = h_host.to(dev, non_blocking=True)
+    N_dev = N_host.to(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = Plan(n, k, h_dev, N_dev)
+    plan_s = time.perf_counter() - t0
+    L = plan.L
+    kw = dict(tol=args.tol, precision="mixed")
+    u = torch.empty(n ** 3, dtype=torch.complex128, device=dev)
+
+    for _ in range(args.warmup):
+        plan.solve(out=u, **kw)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, inputs resident ---------------------------
+    plan.reset_stats()
+    plan.set_timing(True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        _, info = plan.solve(out=u, **kw)
+        infos.append(info)
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    stats = plan.stats()
+    plan.set_timing(False)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    value = ms_total / 1e3 / (args.steps * world)
+
+    # ---- roofline of the dominant kernel (FP32 pass with the largest time) --
+    pk = peaks()
+    fp32_kinds = ["xfwd", "yfwd", "zconv", "yinv", "xinv", "update"]
+    pm, pc = stats["pass_ms"], stats["pass_count"]
+    dom = max(fp32_kinds, key=lambda kk: pm.get(kk + "_f32", 0.0))
+    dom_ms = pm[dom + "_f32"] / max(1, pc[dom + "_f32"])
+    ab = alg_bytes(dom, n, L, 8)
+    achieved = ab / (dom_ms * 1e-3) / 1e9
+    kernel_names = {"xfwd": "k_xfwd", "yfwd": "k_strided(FWD)", "zconv": "k_strided(ZCONV)",
+                    "yinv": "k_strided(INV)", "xinv": "k_xinv", "update": "k_cocg_update"}
+    roof = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+            "traffic": traffic_from_profiles(dom, n), "alg_bytes_per_launch": ab,
+            "ms_per_launch": dom_ms, "peak_source": pk["source"] + " (burst copy)"}
+    passes = {}
+    for kk in fp32_kinds:
+        key = kk + "_f32"
+        if pc.get(key):
+            per = pm[key] / pc[key]
+            b = alg_bytes(kk, n, L, 8)
+            passes[kk] = {"launches": pc[key], "ms_total": pm[key], "ms_per_launch": per,
+                          "alg_GBps": b / (per * 1e-3) / 1e9}
+    for kk, v in pm.items():
+        if kk.endswith("_f64") or kk.startswith("vector"):
+            passes[kk] = {"launches": pc[kk], "ms_total": v, "ms_per_launch": v / max(1, pc[kk])}
+
+    # ---- standalone FP32 matvec (the operator the inner COCG applies) -------
+    x32 = torch.randn(n ** 3, dtype=torch.complex64, device=dev)
+    y32 = torch.empty_like(x32)
+    for _ in range(3):
+        plan.matvec32(x32, "B", out=y32)
+    torch.cuda.synchronize()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record()
+    for _ in range(args.matvec_reps):
+        plan.matvec32(x32, "B", out=y32)
+    m1.record()
+    torch.cuda.synchronize()
+    mv_ms = m0.elapsed_time(m1) / args.matvec_reps
+    mv_bytes = matvec_alg_bytes(n, L, 8)
+    matvec = {"fp32_ms": mv_ms, "alg_bytes": mv_bytes, "alg_GBps": mv_bytes / (mv_ms * 1e-3) / 1e9,
+              "frac_of_hbm": mv_bytes / (mv_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+    del x32, y32
+
+    # ---- plain FP64 GPU solve (comparator), once -------------------------------
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        u64 = torch.empty_like(u)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        _, i64 = plan.solve(out=u64, tol=args.tol, precision="fp64", maxit=2000)
+        f1.record()
+        torch.cuda.synchronize()
+        diff = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+        fp64 = {"s": f0.elapsed_time(f1) / 1e3, "iters": i64["iters"], "relres": i64["relres"],
+                "mixed_vs_fp64_rel_l2": diff, "speedup_mixed": f0.elapsed_time(f1) / ms_per_step}
+        del u64
+
+    # ---- end to end through the public API with host buffers -------------------
+    e2e = None
+    if not args.no_e2e:
+        u_host = torch.empty(n ** 3, dtype=torch.complex128).pin_memory()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        steps_e2e = max(1, min(args.steps, 3))
+        for _ in range(steps_e2e):
+            h_dev.copy_(h_host, non_blocking=True)
+            N_dev.copy_(N_host, non_blocking=True)
+            plan.set_medium(h_dev, N_dev)
+            plan.solve(out=u, **kw)
+            u_host.copy_(u, non_blocking=True)
+        g1.record()
+        torch.cuda.synchronize()
+        e2e_s = g0.elapsed_time(g1) / 1e3 / steps_e2e
+        e2e = {"value": e2e_s / world, "unit": "s",
+               "h2d_bytes_per_step": h_host.numel() * 16 + N_host.numel() * 8,
+               "d2h_bytes_per_step": u_host.numel() * 16}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = oracle_sample(n, k, args.seed, args.tol)
+
+    last = infos[-1]
+    out = {
+        "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": workload_config(args),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(stats["kernel_launches"]) * world,
+        "clocks": ck,
+        "solve": {"iters": last["iters"], "outer_iters": last["outer_iters"], "relres": last["relres"],
+                  "fp64_matvecs": last["fp64_matvecs"], "status": last["status"]},
+        "plan_s": plan_s, "fp64_solve": fp64, "matvec": matvec, "passes": passes,
+        "fp32_matvecs_per_step": stats["fp32_matvecs"] / args.steps,
+        "fp64_matvecs_per_step": stats["fp64_matvecs"] / args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        ours_arm(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

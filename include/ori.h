@@ -87,7 +87,7 @@ typedef struct {
 } ori_plan_opts;
 
 typedef struct {
-  double tol;          /* target ||r||/||RHS|| of the original system, default 1e-6 */
+  double tol;          /* target ||r||/||RHS|| of the symmetrised system, def 1e-6  */
   int    maxit;        /* cap on COCG iterations summed over refinements, def 1000  */
   int    precision;    /* ORI_FP64 or ORI_MIXED (default ORI_MIXED)                  */
   double inner_tol;    /* ORI_MIXED: floor of the FP32 inner target, default 1e-5    */
@@ -103,8 +103,8 @@ typedef struct {
   int    iters;         /* COCG iterations, all refinement steps together            */
   int    outer_iters;   /* refinement steps (1 for ORI_FP64)                         */
   int    fp64_matvecs;  /* FP64 operator applications (residuals, recovery)          */
-  double relres;        /* true ||u0 - A u|| / ||u0|| measured in FP64 on exit,
-                           evaluated on the symmetrised system S(u0 - A u)           */
+  double relres;        /* true residual of the symmetrised system COCG solves,
+                           ||S rhs - B w|| / ||S rhs|| with u = w / S, in FP64      */
   double relres_recur;  /* last recursive residual of the inner COCG                 */
   int    status;        /* ori_status of the solve                                   */
   float  ms;            /* device time of the solve (CUDA events)                    */
@@ -116,7 +116,7 @@ void ori_default_plan_opts(ori_plan_opts* o);
 
 /*
  * ori_plan - build the operator for one grid, wave number and medium.
- *   n        cells per axis, 2 <= n <= 1024.  The padded FFT length per axis
+ *   n        cells per axis, 2 <= n <= 512.  The padded FFT length per axis
  *            is L = the smallest power of two >= 2n (the paper pads to 2b-2
  *            by mirroring, Section 3; any L >= 2n-1 gives the same crop).
  *   k        wave number, finite and > 0 (Eq. 2.1).
@@ -200,6 +200,40 @@ ori_status ori_adjoint_solve(ori_plan_t plan, const double* u_dev,
                              const double* econj_dev, double* grad_h_dev,
                              double* grad_N_dev, const ori_solve_opts* opts,
                              ori_solve_info* info, void* stream);
+
+/* Device-time accounting of a plan's kernels (for profiling and benchmarks). */
+enum {
+  ORI_PASS_XFWD = 0,   /* X forward FFT pass with its prologue                  */
+  ORI_PASS_YFWD = 1,   /* Y forward FFT pass                                    */
+  ORI_PASS_ZCONV = 2,  /* Z forward FFT, spectrum multiply, Z inverse FFT       */
+  ORI_PASS_YINV = 3,   /* Y inverse FFT pass                                    */
+  ORI_PASS_XINV = 4,   /* X inverse FFT pass with its epilogue and reduction    */
+  ORI_PASS_UPDATE = 5, /* COCG vector update and reductions                     */
+  ORI_PASS_VECTOR = 6, /* other elementwise / reduction kernels of a solve      */
+  ORI_PASS_FP64 = 8,   /* added to the kind for launches in FP64 arithmetic     */
+  ORI_PASS_KINDS = 16
+};
+
+typedef struct {
+  uint64_t kernel_launches;        /* kernels this plan launched (graph nodes
+                                      counted at each replay) since the reset */
+  double   pass_ms[ORI_PASS_KINDS];   /* summed device time per kind (FP32 kinds
+                                         0..6, FP64 kinds 8..14), timing on     */
+  uint64_t pass_count[ORI_PASS_KINDS];/* launches timed per kind               */
+  uint64_t fp32_matvecs;           /* FP32 operator applications            */
+  uint64_t fp64_matvecs;           /* FP64 operator applications            */
+} ori_plan_stats;
+
+/* Turn per-kernel CUDA-event timing on (1) or off (0).  With timing on, every
+ * launch of the plan is bracketed by events on the plan's stream (inside
+ * captured graphs too); times are summed into ori_plan_stats.pass_ms at the
+ * solver's synchronisation points, and at ori_plan_get_stats.  Timing adds
+ * an event record between kernels; leave it off outside measurements. */
+ori_status ori_plan_set_timing(ori_plan_t plan, int on);
+/* Copy the counters (synchronises the plan's stream). */
+ori_status ori_plan_get_stats(ori_plan_t plan, ori_plan_stats* out);
+/* Zero the counters. */
+ori_status ori_plan_reset_stats(ori_plan_t plan);
 
 /* Static description of a status code. */
 const char* ori_status_string(int status);

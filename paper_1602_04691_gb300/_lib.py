@@ -33,7 +33,11 @@ EXPORTS = [
     "ori_default_solve_opts", "ori_default_plan_opts", "ori_plan", "ori_plan_set_medium",
     "ori_plan_destroy", "ori_plan_info", "ori_matvec", "ori_matvec32", "ori_cocg_solve",
     "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
+    "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats",
 ]
+
+PASS_NAMES = ["xfwd", "yfwd", "zconv", "yinv", "xinv", "update", "vector", "unused"]
+PASS_NAMES = [k + "_f32" for k in PASS_NAMES] + [k + "_f64" for k in PASS_NAMES]
 
 
 class Domain(C.Structure):
@@ -57,6 +61,21 @@ class SolveInfo(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PlanStats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("pass_ms", C.c_double * 16),
+                ("pass_count", C.c_uint64 * 16), ("fp32_matvecs", C.c_uint64),
+                ("fp64_matvecs", C.c_uint64)]
+
+    def as_dict(self):
+        return {
+            "kernel_launches": int(self.kernel_launches),
+            "pass_ms": {PASS_NAMES[i]: float(self.pass_ms[i]) for i in range(16) if self.pass_count[i]},
+            "pass_count": {PASS_NAMES[i]: int(self.pass_count[i]) for i in range(16) if self.pass_count[i]},
+            "fp32_matvecs": int(self.fp32_matvecs),
+            "fp64_matvecs": int(self.fp64_matvecs),
+        }
 
 
 class OriError(RuntimeError):
@@ -99,6 +118,12 @@ def load():
     lib.ori_cocg_solve.restype = i
     lib.ori_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.ori_adjoint_solve.restype = i
+    lib.ori_plan_set_timing.argtypes = [vp, i]
+    lib.ori_plan_set_timing.restype = i
+    lib.ori_plan_get_stats.argtypes = [vp, C.POINTER(PlanStats)]
+    lib.ori_plan_get_stats.restype = i
+    lib.ori_plan_reset_stats.argtypes = [vp]
+    lib.ori_plan_reset_stats.restype = i
     lib.ori_status_string.argtypes = [i]
     lib.ori_status_string.restype = C.c_char_p
     lib.ori_last_error.argtypes = []

@@ -95,8 +95,81 @@ struct ori_plan_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evj = nullptr;
   cudaGraphExec_t graph_f = nullptr, graph_d = nullptr;
   int graph_f_len = 0, graph_d_len = 0;
+  bool graph_f_timed = false, graph_d_timed = false;
   int vec_grid = 0;
+  // accounting (ori_plan_stats) and optional per-kernel event timing
+  ori_plan_stats stats{};
+  bool capturing = false;
+  unsigned long long cap_launches = 0, graph_f_kernels = 0, graph_d_kernels = 0;
+  bool timing = false;
+  struct Pend { int kind, e0, e1; };
+  cudaEvent_t* tev = nullptr;      // immediate pool
+  int tev_n = 0, tev_used = 0;
+  Pend* pend = nullptr;
+  int npend = 0;
+  cudaEvent_t* gev = nullptr;      // pool owned by the captured graphs
+  int gev_n = 0, gev_used = 0;
+  Pend* gpend_f = nullptr;
+  Pend* gpend_d = nullptr;
+  int ngpend_f = 0, ngpend_d = 0;
+  Pend* gpend_cur = nullptr;
+  int* ngpend_cur = nullptr;
 };
+
+static constexpr int kEvPool = 4096;
+
+// Count one kernel launch (graph nodes are counted at each replay instead).
+static inline void launched(ori_plan_s* p) {
+  if (p->capturing) ++p->cap_launches;
+  else ++p->stats.kernel_launches;
+}
+
+// Record a timing event on s; returns its pool index, or -1 (timing off/full).
+static int t_rec(ori_plan_s* p, cudaStream_t s) {
+  if (!p->timing) return -1;
+  if (p->capturing) {
+    if (p->gev_used >= p->gev_n) return -1;
+    cudaEventRecord(p->gev[p->gev_used], s);
+    return p->gev_used++;
+  }
+  if (p->tev_used >= p->tev_n) return -1;
+  cudaEventRecord(p->tev[p->tev_used], s);
+  return p->tev_used++;
+}
+
+static void t_pair(ori_plan_s* p, int kind, int e0, int e1) {
+  if (e0 < 0 || e1 < 0) return;
+  if (p->capturing) {
+    if (p->gpend_cur && *p->ngpend_cur < kEvPool) p->gpend_cur[(*p->ngpend_cur)++] = {kind, e0, e1};
+  } else if (p->npend < kEvPool) {
+    p->pend[p->npend++] = {kind, e0, e1};
+  }
+}
+
+// Add the elapsed times of recorded pairs (the stream must be synchronised).
+static void t_harvest(ori_plan_s* p) {
+  for (int i = 0; i < p->npend; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->tev[p->pend[i].e0], p->tev[p->pend[i].e1]) == cudaSuccess) {
+      p->stats.pass_ms[p->pend[i].kind] += ms;
+      p->stats.pass_count[p->pend[i].kind] += 1;
+    }
+  }
+  cudaGetLastError();
+  p->npend = 0;
+  p->tev_used = 0;
+}
+
+static void t_harvest_graph(ori_plan_s* p, const ori_plan_s::Pend* g, int ng) {
+  for (int i = 0; i < ng; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->gev[g[i].e0], p->gev[g[i].e1]) == cudaSuccess) {
+      p->stats.pass_ms[g[i].kind] += ms;
+      p->stats.pass_count[g[i].kind] += 1;
+    }
+  }
+  cudaGetLastError();
+}
 
 static ori_status plan_alloc(ori_plan_s* p, void** ptr, size_t bytes) {
   if (p->mem_cap && p->bytes + bytes > p->mem_cap)
@@ -133,6 +206,11 @@ static void plan_free(ori_plan_s* p) {
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->evj) cudaEventDestroy(p->evj);
+  if (p->tev) { for (int i = 0; i < p->tev_n; ++i) cudaEventDestroy(p->tev[i]); delete[] p->tev; }
+  if (p->gev) { for (int i = 0; i < p->gev_n; ++i) cudaEventDestroy(p->gev[i]); delete[] p->gev; }
+  delete[] p->pend;
+  delete[] p->gpend_f;
+  delete[] p->gpend_d;
   if (p->ps) cudaStreamDestroy(p->ps);
   cudaSetDevice(prev);
   delete p;
@@ -171,9 +249,12 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   cpx<T>* T2 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T2f : (void*)p->T2d);
   const void* tw = f32 ? (const void*)p->tw32 : (const void*)p->tw64;
   const int n = p->n, L = p->L;
+  int e0 = t_rec(p, s), e1;
   pro.n = n; pro.nlines = n * n; pro.n_in = n; pro.line_len_in = n; pro.line_len_out = L;
   pro.fft_out = T1; pro.twL = tw; pro.done = done;
   ORI_CUDA(run_xfwd<T>(L, true, pro, s, false));
+  launched(p);
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_XFWD + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
 
   SArgs y{};
   y.in = T1; y.out = T2;
@@ -181,6 +262,8 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = n; y.n_out = L; y.nouter = n;
   y.twL = tw; y.done = done;
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
+  launched(p);
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
 
   SArgs z{};
   z.in = T2; z.out = T2;
@@ -190,6 +273,8 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.twL = tw; z.ghat = f32 ? (const void*)p->ghat32 : (const void*)p->ghat64; z.H = p->H;
   z.done = done;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
+  launched(p);
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
 
   SArgs yi{};
   yi.in = T2; yi.out = T1;
@@ -197,12 +282,31 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   yi.in_pt = L; yi.out_pt = L; yi.ncols = L; yi.n_in = L; yi.n_out = n; yi.nouter = n;
   yi.twL = tw; yi.done = done;
   ORI_CUDA(run_strided<T>(L, SMODE_INV, false, yi, s, false));
+  launched(p);
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
 
   epi.n = n; epi.nlines = n * n; epi.line_len_in = L; epi.line_len_out = n;
   epi.in = T1; epi.twL = tw; epi.done = done; epi.partials = p->partials;
   ORI_CUDA(run_xinv<T>(L, epi, p->sc, fin, s, false, nullptr));
+  launched(p);
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_XINV + (f32 ? 0 : ORI_PASS_FP64), e0, e1);
+  if (!p->capturing) {
+    if (f32) ++p->stats.fp32_matvecs;
+    else ++p->stats.fp64_matvecs;
+  }
   return ORI_OK;
 }
+
+// Launch a vector kernel with accounting: ORI_VEC(p, kind, kernel<<<...>>>(...)).
+#define ORI_VEC(p, kind, launch_expr)                     \
+  do {                                                    \
+    int ve0_ = t_rec((p), (p)->ps);                       \
+    launch_expr;                                          \
+    ORI_CUDA(cudaGetLastError());                         \
+    launched(p);                                          \
+    int ve1_ = t_rec((p), (p)->ps);                       \
+    t_pair((p), (kind), ve0_, ve1_);                      \
+  } while (0)
 
 template <class T>
 static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n) {
@@ -224,8 +328,7 @@ static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N
   ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
-  k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->n3, p->d_count);
-  ORI_CUDA(cudaGetLastError());
+  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->n3, p->d_count)));
   ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   return ORI_OK;
@@ -419,6 +522,39 @@ ori_status ori_plan_set_medium(ori_plan_t p, const double* h_dev, const double* 
   return leave(p, user);
 }
 
+ori_status ori_plan_set_timing(ori_plan_t p, int on) {
+  if (!p) return fail(ORI_ERR_INVALID_ARG, "plan is NULL");
+  if (on && !p->tev) {
+    p->tev = new (std::nothrow) cudaEvent_t[kEvPool];
+    p->gev = new (std::nothrow) cudaEvent_t[2 * kEvPool];
+    p->pend = new (std::nothrow) ori_plan_s::Pend[kEvPool];
+    if (!p->tev || !p->gev || !p->pend) return fail(ORI_ERR_OOM, "host allocation failed");
+    for (int i = 0; i < kEvPool; ++i) ORI_CUDA(cudaEventCreate(&p->tev[i]));
+    for (int i = 0; i < 2 * kEvPool; ++i) ORI_CUDA(cudaEventCreate(&p->gev[i]));
+    p->tev_n = kEvPool;
+  }
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
+  p->timing = on != 0;
+  return ORI_OK;
+}
+
+ori_status ori_plan_get_stats(ori_plan_t p, ori_plan_stats* out) {
+  if (!p || !out) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
+  *out = p->stats;
+  return ORI_OK;
+}
+
+ori_status ori_plan_reset_stats(ori_plan_t p) {
+  if (!p) return fail(ORI_ERR_INVALID_ARG, "plan is NULL");
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
+  std::memset(&p->stats, 0, sizeof(p->stats));
+  return ORI_OK;
+}
+
 ori_status ori_plan_destroy(ori_plan_t p) {
   plan_free(p);
   return ORI_OK;
@@ -516,8 +652,7 @@ static ori_status cocg_iteration(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp
   epi.out = q;
   epi.scale = S;
   ORI_TRY(run_conv<T>(p, pro, epi, FIN_ALPHA, p->ps, &p->sc->done));
-  k_cocg_update<T><<<p->vec_grid, 256, 0, p->ps>>>(x, pp, r, q, p->n3, p->sc, p->partials);
-  ORI_CUDA(cudaGetLastError());
+  ORI_VEC(p, ORI_PASS_UPDATE + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64), (k_cocg_update<T><<<p->vec_grid, 256, 0, p->ps>>>(x, pp, r, q, p->n3, p->sc, p->partials)));
   return ORI_OK;
 }
 
@@ -533,20 +668,34 @@ template <class T>
 static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cpx<T>* q,
                              const cpx<T>* S, double tol, int maxit, int check_every, bool use_graph,
                              InnerResult* res) {
-  k_cocg_init<T><<<p->vec_grid, 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, tol, maxit);
-  ORI_CUDA(cudaGetLastError());
+  ORI_VEC(p, ORI_PASS_VECTOR + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64), (k_cocg_init<T><<<p->vec_grid, 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, tol, maxit)));
   ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
   if (p->h_sc->done == DONE_RUNNING && maxit > 0) {
     ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, true));
-    cudaGraphExec_t& gexec = sizeof(T) == 4 ? p->graph_f : p->graph_d;
-    int& glen = sizeof(T) == 4 ? p->graph_f_len : p->graph_d_len;
-    if (use_graph && (gexec == nullptr || glen != check_every)) {
+    const bool f32 = sizeof(T) == 4;
+    cudaGraphExec_t& gexec = f32 ? p->graph_f : p->graph_d;
+    int& glen = f32 ? p->graph_f_len : p->graph_d_len;
+    bool& gtimed = f32 ? p->graph_f_timed : p->graph_d_timed;
+    unsigned long long& gkern = f32 ? p->graph_f_kernels : p->graph_d_kernels;
+    ori_plan_s::Pend*& gpend = f32 ? p->gpend_f : p->gpend_d;
+    int& ngpend = f32 ? p->ngpend_f : p->ngpend_d;
+    if (use_graph && (gexec == nullptr || glen != check_every || gtimed != p->timing)) {
       if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+      if (!gpend) gpend = new ori_plan_s::Pend[kEvPool];
+      ngpend = 0;
+      p->gpend_cur = gpend;
+      p->ngpend_cur = &ngpend;
+      p->gev_used = f32 ? 0 : kEvPool;
+      p->gev_n = p->gev ? (f32 ? kEvPool : 2 * kEvPool) : 0;
+      p->cap_launches = 0;
       cudaGraph_t g = nullptr;
       ORI_CUDA(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal));
+      p->capturing = true;
       ori_status cs = ORI_OK;
       for (int i = 0; i < check_every && cs == ORI_OK; ++i) cs = cocg_iteration<T>(p, x, r, pp, q, S, false);
+      p->capturing = false;
       cudaError_t ee = cudaStreamEndCapture(p->ps, &g);
       if (cs != ORI_OK) { if (g) cudaGraphDestroy(g); return cs; }
       if (ee != cudaSuccess) return fail(ORI_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
@@ -554,18 +703,30 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
       cudaGraphDestroy(g);
       if (ee != cudaSuccess) { gexec = nullptr; return fail(ORI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee)); }
       glen = check_every;
+      gtimed = p->timing;
+      gkern = p->cap_launches;
     }
-    int launched = 1;
+    int launched_iters = 1;
+    bool graph_pending = false;
     for (;;) {
       ORI_CUDA(cudaMemcpyAsync(&p->h_sc->done, &p->sc->done, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->ps));
       ORI_CUDA(cudaStreamSynchronize(p->ps));
-      if (p->h_sc->done != DONE_RUNNING || launched >= maxit) break;
+      if (p->timing) {
+        t_harvest(p);
+        if (graph_pending) t_harvest_graph(p, gpend, ngpend);
+      }
+      graph_pending = false;
+      if (p->h_sc->done != DONE_RUNNING || launched_iters >= maxit) break;
       if (use_graph) {
         ORI_CUDA(cudaGraphLaunch(gexec, p->ps));
+        p->stats.kernel_launches += gkern;
+        if (f32) p->stats.fp32_matvecs += check_every;
+        else p->stats.fp64_matvecs += check_every;
+        graph_pending = true;
       } else {
         for (int i = 0; i < check_every; ++i) ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, false));
       }
-      launched += check_every;
+      launched_iters += check_every;
     }
   }
   ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
@@ -590,6 +751,7 @@ static ori_status fp64_residual(ori_plan_s* p, double* rnorm) {
   ORI_TRY(run_conv<double>(p, pro, epi, FIN_SUM, p->ps, nullptr));
   ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
   *rnorm = std::sqrt(p->h_sc->sum.x);
   return ORI_OK;
 }
@@ -642,8 +804,7 @@ static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, 
   double last_recur = 0;
   int outer = 0;
   while (rn > o.tol * bnorm && outer < o.max_outer && total < o.maxit) {
-    k_normalise_to_f32<<<p->vec_grid, 256, 0, p->ps>>>(p->r64, p->r32, n3, 1.0 / rn);
-    ORI_CUDA(cudaGetLastError());
+    ORI_VEC(p, ORI_PASS_VECTOR, (k_normalise_to_f32<<<p->vec_grid, 256, 0, p->ps>>>(p->r64, p->r32, n3, 1.0 / rn)));
     const double want = 0.5 * o.tol * bnorm / rn;
     const double tin = std::min(0.5, std::max(o.inner_tol, want));
     InnerResult ir;
@@ -653,8 +814,7 @@ static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, 
     last_recur = ir.relres_recur;
     ++outer;
     if (ir.done == DONE_NONFINITE) break;
-    k_accumulate<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->x32, n3, rn);
-    ORI_CUDA(cudaGetLastError());
+    ORI_VEC(p, ORI_PASS_VECTOR, (k_accumulate<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->x32, n3, rn)));
     double rn_new = 0;
     ORI_TRY(fp64_residual(p, &rn_new));
     info->fp64_matvecs += 1;
@@ -704,18 +864,19 @@ ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, co
   ORI_TRY(alloc_solver(p));
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
-  k_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0, p->b64,
-                                          p->n, p->d, p->origin[0], p->origin[1], p->origin[2], p->k,
-                                          al[0], al[1], al[2], p->sc, p->partials);
-  ORI_CUDA(cudaGetLastError());
+  ORI_VEC(p, ORI_PASS_VECTOR,
+          (k_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0,
+                                                  p->b64, p->n, p->d, p->origin[0], p->origin[1], p->origin[2],
+                                                  p->k, al[0], al[1], al[2], p->sc, p->partials)));
   ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
   const double bnorm = std::sqrt(p->h_sc->sum.x);
   ORI_TRY(solve_B(p, bnorm, o, &info));
   // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
   if (p->zero_S == 0) {
-    k_recover<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->S64, reinterpret_cast<cpx<double>*>(u_dev), p->n3);
-    ORI_CUDA(cudaGetLastError());
+    ORI_VEC(p, ORI_PASS_VECTOR,
+            (k_recover<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->S64, reinterpret_cast<cpx<double>*>(u_dev), p->n3)));
   } else {
     XArgs pro{}, epi{};
     pro.mode = PRO_SCALE;
@@ -732,6 +893,7 @@ ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, co
   ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
   ORI_CUDA(cudaEventSynchronize(p->ev1));
   cudaEventElapsedTime(&info.ms, p->ev0, p->ev1);
+  if (p->timing) t_harvest(p);
   ORI_TRY(leave(p, user));
   if (info_out) *info_out = info;
   if (info.status != ORI_OK)
@@ -752,20 +914,23 @@ ori_status ori_adjoint_solve(ori_plan_t p, const double* u_dev, const double* ec
   ORI_TRY(alloc_solver(p));
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
-  k_adj_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->S64, p->b64,
-                                              p->n3, p->sc, p->partials);
-  ORI_CUDA(cudaGetLastError());
+  ORI_VEC(p, ORI_PASS_VECTOR,
+          (k_adj_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->S64, p->b64,
+                                                      p->n3, p->sc, p->partials)));
   ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
   const double bnorm = std::sqrt(p->h_sc->sum.x);
   ORI_TRY(solve_B(p, bnorm, o, &info));
-  k_gradient<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->w,
-                                               reinterpret_cast<const cpx<double>*>(u_dev), p->S64, p->h, p->N,
-                                               reinterpret_cast<cpx<double>*>(grad_h_dev), grad_N_dev, p->n3);
-  ORI_CUDA(cudaGetLastError());
+  ORI_VEC(p, ORI_PASS_VECTOR,
+          (k_gradient<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->w,
+                                                       reinterpret_cast<const cpx<double>*>(u_dev), p->S64, p->h,
+                                                       p->N, reinterpret_cast<cpx<double>*>(grad_h_dev), grad_N_dev,
+                                                       p->n3)));
   ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
   ORI_CUDA(cudaEventSynchronize(p->ev1));
   cudaEventElapsedTime(&info.ms, p->ev0, p->ev1);
+  if (p->timing) t_harvest(p);
   ORI_TRY(leave(p, user));
   if (info_out) *info_out = info;
   if (info.status != ORI_OK)

@@ -113,6 +113,19 @@ class Plan:
             raise RuntimeError("plan is closed")
         return self._h
 
+    # -- accounting ------------------------------------------------------------
+    def set_timing(self, on: bool = True):
+        """Bracket every kernel of this plan with CUDA events (summed per pass kind)."""
+        _lib.check(_lib.load().ori_plan_set_timing(self.handle, 1 if on else 0), "ori_plan_set_timing")
+
+    def stats(self) -> dict:
+        st = _lib.PlanStats()
+        _lib.check(_lib.load().ori_plan_get_stats(self.handle, C.byref(st)), "ori_plan_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        _lib.check(_lib.load().ori_plan_reset_stats(self.handle), "ori_plan_reset_stats")
+
     # -- medium ----------------------------------------------------------------
     def set_medium(self, h: torch.Tensor, N: torch.Tensor, stream=None):
         m = self.n ** 3
