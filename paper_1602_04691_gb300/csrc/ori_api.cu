@@ -65,6 +65,7 @@ struct ori_plan_s {
   cpx<double>* S64 = nullptr;
   cpx<float>* w32 = nullptr;
   cpx<float>* S32 = nullptr;
+  cpx<double>* Sinv = nullptr;
   // spectrum and twiddles
   cpx<double>* ghat64 = nullptr;
   cpx<float>* ghat32 = nullptr;
@@ -129,7 +130,8 @@ static int t_rec(ori_plan_s* p, cudaStream_t s) {
   if (!p->timing) return -1;
   if (p->capturing) {
     if (p->gev_used >= p->gev_n) return -1;
-    cudaEventRecord(p->gev[p->gev_used], s);
+    // an external record becomes an event-record node of the graph
+    cudaEventRecordWithFlags(p->gev[p->gev_used], s, cudaEventRecordExternal);
     return p->gev_used++;
   }
   if (p->tev_used >= p->tev_n) return -1;
@@ -195,7 +197,7 @@ static void plan_free(ori_plan_s* p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
+  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->Sinv, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
                   p->T1f, p->T2f, p->T1d, p->T2d, p->sc, p->partials, p->d_count, p->b64, p->w,
                   p->r64, p->u0, p->p64, p->q64, p->x32, p->r32, p->p32, p->q32};
   for (void* q : ptrs)
@@ -272,6 +274,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.ncols = L; z.n_in = n; z.n_out = n; z.nouter = L;
   z.twL = tw; z.ghat = f32 ? (const void*)p->ghat32 : (const void*)p->ghat64; z.H = p->H;
   z.done = done;
+  z.sm_count = p->sm_count;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
@@ -328,7 +331,7 @@ static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N
   ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
-  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->n3, p->d_count)));
+  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->Sinv, p->n3, p->d_count)));
   ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   return ORI_OK;
@@ -476,7 +479,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     const size_t H3 = size_t(p->H) * p->H * p->H;
     const size_t t1 = size_t(p->n) * p->n * p->L, t2 = size_t(p->n) * p->L * p->L;
     if ((st = alloc_n(p, &p->h, n3)) || (st = alloc_n(p, &p->N, n3)) || (st = alloc_n(p, &p->w64, n3)) ||
-        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
+        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
         (st = alloc_n(p, &p->ghat64, H3)) || (st = alloc_n(p, &p->ghat32, H3)) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
         (st = alloc_n(p, &p->T1f, t1)) || (st = alloc_n(p, &p->T2f, t2)) ||
@@ -805,7 +808,7 @@ static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, 
   int outer = 0;
   while (rn > o.tol * bnorm && outer < o.max_outer && total < o.maxit) {
     ORI_VEC(p, ORI_PASS_VECTOR, (k_normalise_to_f32<<<p->vec_grid, 256, 0, p->ps>>>(p->r64, p->r32, n3, 1.0 / rn)));
-    const double want = 0.5 * o.tol * bnorm / rn;
+    const double want = 0.25 * o.tol * bnorm / rn;
     const double tin = std::min(0.5, std::max(o.inner_tol, want));
     InnerResult ir;
     ORI_TRY(cocg_inner<float>(p, p->x32, p->r32, p->p32, p->q32, p->S32, tin, o.maxit - total, o.check_every, graph, &ir));
@@ -865,7 +868,8 @@ ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, co
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
   ORI_VEC(p, ORI_PASS_VECTOR,
-          (k_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0,
+          (k_rhs<<<p->vec_grid, 256, rhs_dev ? 0 : 3 * size_t(p->n) * sizeof(cpx<double>), p->ps>>>(
+              reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0,
                                                   p->b64, p->n, p->d, p->origin[0], p->origin[1], p->origin[2],
                                                   p->k, al[0], al[1], al[2], p->sc, p->partials)));
   ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
@@ -876,7 +880,7 @@ ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, co
   // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
   if (p->zero_S == 0) {
     ORI_VEC(p, ORI_PASS_VECTOR,
-            (k_recover<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->S64, reinterpret_cast<cpx<double>*>(u_dev), p->n3)));
+            (k_recover<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->Sinv, reinterpret_cast<cpx<double>*>(u_dev), p->n3)));
   } else {
     XArgs pro{}, epi{};
     pro.mode = PRO_SCALE;

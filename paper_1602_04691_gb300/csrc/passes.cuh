@@ -26,6 +26,8 @@
 
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace ori {
 
 // Layout of the lines a CTA works on.
@@ -92,6 +94,7 @@ struct SArgs {
   const void* ghat;                // spectrum, H^3 entries (SMODE_ZCONV)
   int H;                           // L/2 + 1
   const int* done;
+  int sm_count;                    // persistent kernels: CTAs to launch
 };
 
 template <int L, int C, class T>

@@ -5,6 +5,9 @@
 #include "passes.cuh"
 #include "scalars.cuh"
 
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
 namespace ori {
 
 // ---------------------------------------------------------------------------
@@ -341,6 +344,133 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Z convolution on a cluster of Q CTAs (FP32, large L).  One cluster owns a
+// tile of C consecutive columns (C * 8 B = 256 B per row, so every global
+// row access is a full 256-byte segment even at the L^2 plane stride).  The
+// FFT's two transposes go through distributed shared memory:
+//   stage 1   CTA q: rows j1*L2 + j2 with j2 in its quarter, all C columns;
+//             DFT over j1; sends the k1-quarter k1/(L1/Q) to CTA k1/(L1/Q)
+//   stage 2   CTA q: its k1 quarter, DFT over j2 -> X[k1 + L1 k2];
+//             * spectrum; inverse DFT over k2; sends ja to CTA ja/(L2/Q)
+//   stage B   CTA q: its ja quarter, inverse DFT over k1 -> rows ja + L2 jb.
+// ---------------------------------------------------------------------------
+template <int L, int C, int Q, class T>
+struct ZTile {
+  static constexpr int L1 = Split<L>::L1;
+  static constexpr int L2 = Split<L>::L2;
+  static constexpr int J2Q = L2 / Q;           // j2 (and ja) values per CTA
+  static constexpr int K1Q = L1 / Q;           // k1 values per CTA
+  static constexpr int NT = C * J2Q;           // threads per CTA
+  static constexpr int NI = L1 / L2;           // stage-2 items per thread
+  static constexpr int PK = L2 + 1;            // buffer 1: [c][k1'][j2]
+  static constexpr int PC = (K1Q * PK) | 1;
+  static constexpr int PKI = L1 + 1;           // buffer 2: [c][ja'][k1]
+  static constexpr int PCI = (J2Q * PKI) | 1;
+  static constexpr int SMEM_ELEMS = (C * PC > C * PCI) ? C * PC : C * PCI;
+  static constexpr size_t SMEM_BYTES = size_t(SMEM_ELEMS) * sizeof(cpx<T>);
+};
+
+template <class T, int L, int C, int Q>
+__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(ZTile<L, C, Q, T>::NT, 2)
+k_zconv_cluster(SArgs a) {
+  using ZT = ZTile<L, C, Q, T>;
+  constexpr int L1 = ZT::L1, L2 = ZT::L2, J2Q = ZT::J2Q, K1Q = ZT::K1Q, NT = ZT::NT, NI = ZT::NI;
+  constexpr int PK = ZT::PK, PC = ZT::PC, PKI = ZT::PKI, PCI = ZT::PCI;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+  if (a.done != nullptr && *a.done != 0) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = int(cluster.block_rank());
+  const int tile = blockIdx.x / Q;
+  const int outer = tile / a.col_blocks;
+  const int cb = tile - outer * a.col_blocks;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + outer * a.in_outer + (long long)cb * C;
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + outer * a.out_outer + (long long)cb * C;
+  const int colmax = a.ncols - cb * C;
+  const int tid = threadIdx.x;
+  const int c = tid % C;
+  const int jl = tid / C;                 // local j2 / ja index in [0, J2Q)
+
+  // stage 1: rows j1*L2 + j2 (half-zero input), DFT over j1, twiddle, scatter
+  {
+    const int j2 = q * J2Q + jl;
+    cpx<T> r[L1];
+#pragma unroll
+    for (int j1 = 0; j1 < L1; ++j1) {
+      r[j1] = czero<T>();
+      if (j1 < L1 / 2) {
+        const int j = j1 * L2 + j2;
+        if (c < colmax && j < a.n_in) r[j1] = in[(long long)j * a.in_pt + c];
+      }
+    }
+    dft<L1, -1, true>(r);
+#pragma unroll
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
+#pragma unroll
+    for (int dst = 0; dst < Q; ++dst) {
+      cpx<T>* rsm = cluster.map_shared_rank(sm, dst);
+#pragma unroll
+      for (int kk = 0; kk < K1Q; ++kk) rsm[c * PC + kk * PK + j2] = r[dst * K1Q + kk];
+    }
+  }
+  cluster.sync();
+
+  // stage 2: this CTA's k1 quarter; DFT over j2; spectrum; inverse over k2
+  cpx<T> b[NI][L2];
+  const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
+  const int my = mirror_index(outer, L);
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    const int s = tid + it * NT;
+    const int c2 = s % C, kk = s / C;
+    const int k1 = q * K1Q + kk;
+#pragma unroll
+    for (int j = 0; j < L2; ++j) b[it][j] = sm[c2 * PC + kk * PK + j];
+    dft<L2, -1, false>(b[it]);
+    const int mx = mirror_index(min(cb * C + c2, L - 1), L);
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) {
+      const int mz = mirror_index(k1 + L1 * k2, L);
+      b[it][k2] = cmul(b[it][k2], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
+    }
+    dft<L2, +1, false>(b[it]);
+#pragma unroll
+    for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
+  }
+  cluster.sync();   // every CTA has read buffer 1 before buffer 2 is written
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    const int s = tid + it * NT;
+    const int c2 = s % C, kk = s / C;
+    const int k1 = q * K1Q + kk;
+#pragma unroll
+    for (int dst = 0; dst < Q; ++dst) {
+      cpx<T>* rsm = cluster.map_shared_rank(sm, dst);
+#pragma unroll
+      for (int jj = 0; jj < J2Q; ++jj) rsm[c2 * PCI + jj * PKI + k1] = b[it][dst * J2Q + jj];
+    }
+  }
+  cluster.sync();
+
+  // stage B: this CTA's ja quarter; inverse DFT over k1; rows ja + L2 jb
+  {
+    const int ja = q * J2Q + jl;
+    cpx<T> r[L1];
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) r[k1] = sm[c * PCI + jl * PKI + k1];
+    dft<L1, +1, false>(r);
+    if (c < colmax) {
+#pragma unroll
+      for (int jb = 0; jb < L1 / 2; ++jb) {
+        const int j = ja + L2 * jb;
+        if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (dispatch on the padded length)
 // ---------------------------------------------------------------------------
 template <class T> constexpr int cols_strided() { return sizeof(T) == 4 ? 8 : 4; }
@@ -384,6 +514,179 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Z convolution, persistent and software-pipelined.  Each CTA loops over
+// tiles of C columns (C * sizeof(cpx<T>) = 128 B per row).  While a tile is
+// transformed, the next tile's n input rows stream into a staging buffer
+// with cp.async, so the memory system stays busy through the compute.
+// Tiles are visited ky = 0, L/2, 1, L-1, 2, L-2, ... so that rows ky and
+// L - ky, which read the same spectrum entries, run at the same time and
+// the second read hits L2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int ky_of_slot(int i, int L) {
+  if (i == 0) return 0;
+  if (i == 1) return L / 2;
+  const int m = (i - 2) / 2 + 1;
+  return (i & 1) ? L - m : m;
+}
+
+template <int L, int C, class T>
+struct ZPipe {
+  using TL = Tile<L, C, T>;
+  static constexpr int NT = TL::NT;
+  static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
+  static constexpr size_t S_ELEMS = size_t(L / 2) * C;   // staged input rows (n <= L/2)
+  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS) * sizeof(cpx<T>);
+};
+
+template <class T, int L, int C>
+__device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, cpx<T>* S) {
+  constexpr int NT = ZPipe<L, C, T>::NT;
+  constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;    // 16-byte chunks per row
+  const int col_blocks = L / C;
+  const int ky = ky_of_slot(tile / col_blocks, L);
+  const int cb = tile % col_blocks;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + (long long)ky * a.in_outer + (long long)cb * C;
+  const int chunks = a.n_in * PER_ROW;
+  constexpr int EPC = 16 / int(sizeof(cpx<T>));             // elements per chunk
+  for (int k = threadIdx.x; k < chunks; k += NT) {
+    const int j = k / PER_ROW, cc = (k - j * PER_ROW) * EPC;
+    cp_async16(S + j * C + cc, src + (long long)j * a.in_pt + cc);
+  }
+  cp_async_commit();
+}
+
+template <class T, int L, int C>
+__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a) {
+  using TL = Tile<L, C, T>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
+  constexpr int PK = TL::PK, PC = TL::PC, PKI = TL::PKI, PCI = TL::PCI;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* S = E + ZPipe<L, C, T>::E_ELEMS;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
+  const int col_blocks = L / C;
+  const int ntiles = L * col_blocks;
+  const int tid = threadIdx.x;
+  const int c = tid % C, jl = tid / C;
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) zpipe_prefetch<T, L, C>(a, tile, S);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int ky = ky_of_slot(tile / col_blocks, L);
+    const int cb = tile % col_blocks;
+    cp_async_wait_all();
+    __syncthreads();   // staged rows visible; previous tile done with E
+    // stage 1: DFT over j1 of rows j1*L2 + j2 (zero padded beyond n_in)
+    cpx<T> r[L1];
+#pragma unroll
+    for (int j1 = 0; j1 < L1; ++j1) {
+      r[j1] = czero<T>();
+      if (j1 < L1 / 2) {
+        const int j = j1 * L2 + jl;
+        if (j < a.n_in) r[j1] = S[j * C + c];
+      }
+    }
+    __syncthreads();   // staging buffer consumed: stream the next tile in
+    if (tile + (int)gridDim.x < ntiles) zpipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
+    dft<L1, -1, true>(r);
+#pragma unroll
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (jl * k1) & (L - 1));
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
+    __syncthreads();
+    // stage 2 (DFT over j2), spectrum, inverse stage A (DFT over k2)
+    cpx<T> b[NI][L2];
+    const int my = mirror_index(ky, L);
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      const int s = tid + it * NT;
+      const int c2 = s % C, k1 = s / C;
+#pragma unroll
+      for (int j = 0; j < L2; ++j) b[it][j] = E[c2 * PC + k1 * PK + j];
+      dft<L2, -1, false>(b[it]);
+      const int mx = mirror_index(cb * C + c2, L);
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) {
+        const int mz = mirror_index(k1 + L1 * k2, L);
+        b[it][k2] = cmul(b[it][k2], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
+      }
+      dft<L2, +1, false>(b[it]);
+#pragma unroll
+      for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
+    }
+    __syncthreads();   // forward exchange fully read
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      const int s = tid + it * NT;
+      const int c2 = s % C, k1 = s / C;
+#pragma unroll
+      for (int ja = 0; ja < L2; ++ja) E[c2 * PCI + ja * PKI + k1] = b[it][ja];
+    }
+    __syncthreads();
+    // inverse stage B: DFT over k1 -> rows ja + L2 jb (keep z < n_out)
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) r[k1] = E[c * PCI + jl * PKI + k1];
+    dft<L1, +1, false>(r);
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)ky * a.out_outer + (long long)cb * C;
+#pragma unroll
+    for (int jb = 0; jb < L1 / 2; ++jb) {
+      const int j = jl + L2 * jb;
+      if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
+    }
+  }
+  cp_async_wait_all();
+}
+
+template <class T, int L>
+cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = 128 / int(sizeof(cpx<T>));
+  using ZP = ZPipe<L, C, T>;
+  auto kfn = k_zconv_pipe<T, L, C>;
+  static int per_sm = 0;   // resident CTAs per SM, measured once at set-up
+  if (setup) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZP::SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, ZP::NT, ZP::SMEM_BYTES);
+    per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
+    return e;
+  }
+  const int ntiles = L * (L / C);
+  const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm)));
+  kfn<<<grid, ZP::NT, ZP::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class T, int L>
+cudaError_t launch_zconv_cluster_L(SArgs a, cudaStream_t s, bool setup) {
+  constexpr int C = 32, Q = 4;
+  using ZT = ZTile<L, C, Q, T>;
+  auto kfn = k_zconv_cluster<T, L, C, Q>;
+  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZT::SMEM_BYTES));
+  a.col_blocks = (a.ncols + C - 1) / C;
+  const unsigned grid = unsigned(a.nouter) * unsigned(a.col_blocks) * Q;
+  kfn<<<grid, ZT::NT, ZT::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Z-pass kernel choice: the pipelined persistent kernel for L >= 64 (both
+// precisions); the plain strided kernel for small L.
+template <class T, int L>
+cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
+  if constexpr (L >= 64) return launch_zconv_pipe_L<T, L>(a, s, setup, a.sm_count);
+  else return launch_strided_L<T, L, SMODE_ZCONV, true>(a, s, setup);
+}
+
 #define ORI_FOR_EACH_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 template <class T>
@@ -415,7 +718,7 @@ cudaError_t run_strided(int L, int smode, bool half, const SArgs& a, cudaStream_
       if (smode == SMODE_FWD) return half ? launch_strided_L<T, LL, SMODE_FWD, true>(a, s, setup) \
                                           : launch_strided_L<T, LL, SMODE_FWD, false>(a, s, setup); \
       if (smode == SMODE_INV) return launch_strided_L<T, LL, SMODE_INV, false>(a, s, setup); \
-      return launch_strided_L<T, LL, SMODE_ZCONV, true>(a, s, setup);
+      return launch_zconv_L<T, LL>(a, s, setup);
     ORI_FOR_EACH_L(ORI_CASE)
 #undef ORI_CASE
     default: return cudaErrorInvalidValue;

@@ -28,7 +28,7 @@ __device__ __forceinline__ cpx<double> cdivd(cpx<double> a, cpx<double> b) {
 // counts cells with S == 0 and cells with h == 0 or N == 0.
 __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __restrict__ N,
                          cpx<double>* w64, cpx<double>* S64, cpx<float>* w32, cpx<float>* S32,
-                         long long n3, unsigned long long* zero_count) {
+                         cpx<double>* Sinv, long long n3, unsigned long long* zero_count) {
   unsigned long long zs = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x) {
@@ -40,7 +40,12 @@ __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __rest
     S64[i] = s;
     w32[i] = ccast<float>(w);
     S32[i] = ccast<float>(s);
-    if (w.x == 0.0 && w.y == 0.0) ++zs;
+    if (w.x == 0.0 && w.y == 0.0) {
+      ++zs;
+      Sinv[i] = {0.0, 0.0};
+    } else {
+      Sinv[i] = cdivd(cpx<double>{1.0, 0.0}, s);
+    }
   }
   if (zs) atomicAdd(zero_count, zs);
 }
@@ -82,14 +87,30 @@ __device__ __forceinline__ void block_partial2(double2 a, double2 b, double2* re
 }
 
 // Right-hand side of the symmetrised system: u0 = rhs or exp(ik alpha . x_p)
-// (Eq. 2.4, cell centres), b = S u0; sum |b|^2 -> sc->sum.x.
+// (Eq. 2.4, cell centres), b = S u0; sum |b|^2 -> sc->sum.x.  The plane wave
+// factors over the axes, exp(ik(a_x x + a_y y + a_z z)) = e_x(ix) e_y(iy)
+// e_z(iz), so each block evaluates 3n FP64 phases into shared memory and
+// every cell costs two complex products.
 __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __restrict__ S,
                       cpx<double>* u0, cpx<double>* b, int n, double d, double ox, double oy,
                       double oz, double k, double ax, double ay, double az, Scalars* sc,
                       double2* partials) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<double>* e = reinterpret_cast<cpx<double>*>(smraw);   // [3][n]
   __shared__ double2 red[64];
   __shared__ int s_last;
   const long long n3 = (long long)n * n * n;
+  if (rhs == nullptr) {
+    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
+      const int axis = t / n, i = t - axis * n;
+      const double o = axis == 0 ? ox : (axis == 1 ? oy : oz);
+      const double a = axis == 0 ? ax : (axis == 1 ? ay : az);
+      double sn, cs;
+      sincos(k * a * (o + (i + 0.5) * d), &sn, &cs);
+      e[t] = {cs, sn};
+    }
+    __syncthreads();
+  }
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x) {
@@ -98,10 +119,7 @@ __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __
       u = rhs[i];
     } else {
       const int ix = int(i % n), iy = int((i / n) % n), iz = int(i / ((long long)n * n));
-      const double x = ox + (ix + 0.5) * d, y = oy + (iy + 0.5) * d, z = oz + (iz + 0.5) * d;
-      double sn, cs;
-      sincos(k * (ax * x + ay * y + az * z), &sn, &cs);
-      u = {cs, sn};
+      u = cmul(cmul(e[ix], e[n + iy]), e[2 * n + iz]);
     }
     u0[i] = u;
     const cpx<double> bv = cmul(S[i], u);
@@ -129,6 +147,7 @@ __global__ void k_adj_rhs(const cpx<double>* __restrict__ ec, const cpx<double>*
 }
 
 // COCG start: x = 0, rho = r^T r, ||r||^2; sets tol/maxit and the flags.
+// Sums in T over 8 elements per thread, then in FP64.
 template <class T>
 __global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n3, Scalars* sc,
                             double2* partials, double tol, int maxit) {
@@ -136,14 +155,24 @@ __global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n
   __shared__ int s_last;
   double2 rho = make_double2(0.0, 0.0);
   double nn = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
-       i += (long long)gridDim.x * blockDim.x) {
-    const cpx<T> rv = r[i];
-    x[i] = czero<T>();
-    const double a = double(rv.x), b = double(rv.y);
-    rho.x += a * a - b * b;
-    rho.y += 2.0 * a * b;
-    nn += a * a + b * b;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x; base < n3;
+       base += 8 * stride) {
+    cpx<T> rs = czero<T>();
+    T ns = T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const long long i = base + u * stride;
+      if (i < n3) {
+        const cpx<T> rv = r[i];
+        x[i] = czero<T>();
+        rs = rs + cmul(rv, rv);
+        ns += rv.x * rv.x + rv.y * rv.y;
+      }
+    }
+    rho.x += double(rs.x);
+    rho.y += double(rs.y);
+    nn += double(ns);
   }
   block_partial2(rho, make_double2(nn, 0.0), red, partials);
   if (last_block_arrives(sc, s_last)) {
@@ -218,12 +247,12 @@ __global__ void k_accumulate(cpx<double>* w, const cpx<float>* __restrict__ d32,
   }
 }
 
-// u = w / S (every S != 0).
-__global__ void k_recover(const cpx<double>* __restrict__ w, const cpx<double>* __restrict__ S,
+// u = w / S = w * (1/S) (every S != 0; 1/S is kept by the plan).
+__global__ void k_recover(const cpx<double>* __restrict__ w, const cpx<double>* __restrict__ Sinv,
                           cpx<double>* u, long long n3) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x)
-    u[i] = cdivd(w[i], S[i]);
+    u[i] = cmul(w[i], Sinv[i]);
 }
 
 // Adjoint gradient: psi = S z, t = (conj(e) - psi) u,
