@@ -64,7 +64,9 @@ typedef enum {
 enum {
   ORI_FP64 = 0,   /* complex128 data, FP64 FFTs                                      */
   ORI_FP32 = 1,   /* complex64 data, FP32 FFTs (FP64 spectrum rounded once)          */
-  ORI_MIXED = 2   /* solve only: FP32 COCG inside FP64 iterative refinement          */
+  ORI_MIXED = 2,  /* solve only: FP32 COCG inside FP64 iterative refinement          */
+  ORI_DF = 3      /* paired-FP32 ("double-float", ~48-bit) arithmetic: hi + lo
+                     floats with error-free sums and products; complex128 data  */
 };
 
 /* Which operator ori_matvec applies. */
@@ -96,7 +98,10 @@ typedef struct {
   double alpha[3];     /* incidence direction when rhs_dev == NULL; (0,0,0)->(0,0,1) */
   int    use_graph;    /* 1 (default): replay the check_every-iteration block as a
                           captured CUDA graph; 0: plain launches                      */
-  int    reserved[7];
+  int    residual;     /* ORI_MIXED: arithmetic of the FP64-class refinement residual
+                          b - B w: ORI_DF (default; inputs and output complex128,
+                          FFT passes in paired FP32) or ORI_FP64 (native FP64)      */
+  int    reserved[6];
 } ori_solve_opts;
 
 typedef struct {
@@ -151,6 +156,8 @@ ori_status ori_plan_info(ori_plan_t plan, int64_t* n, int64_t* L, size_t* bytes)
  *   precision ORI_FP64: every pass in FP64.
  *   precision ORI_FP32: x is rounded to complex64, the passes run in FP32
  *                       with the FP32 spectrum, y is widened back.
+ *   precision ORI_DF:   x is split into paired floats, the passes run in
+ *                       paired-FP32 arithmetic, y is widened back.
  * x_dev and y_dev may not overlap.  Asynchronous on `stream`.
  */
 ori_status ori_matvec(ori_plan_t plan, const double* x_dev, double* y_dev,
@@ -211,17 +218,19 @@ enum {
   ORI_PASS_UPDATE = 5, /* COCG vector update and reductions                     */
   ORI_PASS_VECTOR = 6, /* other elementwise / reduction kernels of a solve      */
   ORI_PASS_FP64 = 8,   /* added to the kind for launches in FP64 arithmetic     */
-  ORI_PASS_KINDS = 16
+  ORI_PASS_DF = 16,    /* added to the kind for launches in paired-FP32 math    */
+  ORI_PASS_KINDS = 24
 };
 
 typedef struct {
   uint64_t kernel_launches;        /* kernels this plan launched (graph nodes
                                       counted at each replay) since the reset */
   double   pass_ms[ORI_PASS_KINDS];   /* summed device time per kind (FP32 kinds
-                                         0..6, FP64 kinds 8..14), timing on     */
+                                         0..6, FP64 8..14, paired FP32 16..22)  */
   uint64_t pass_count[ORI_PASS_KINDS];/* launches timed per kind               */
   uint64_t fp32_matvecs;           /* FP32 operator applications            */
   uint64_t fp64_matvecs;           /* FP64 operator applications            */
+  uint64_t df_matvecs;             /* paired-FP32 operator applications     */
 } ori_plan_stats;
 
 /* Turn per-kernel CUDA-event timing on (1) or off (0).  With timing on, every

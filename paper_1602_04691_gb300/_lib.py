@@ -25,6 +25,7 @@ ORI_ERR_UNSUPPORTED = 7
 ORI_FP64 = 0
 ORI_FP32 = 1
 ORI_MIXED = 2
+ORI_DF = 3
 ORI_FORM_A = 0
 ORI_FORM_B = 1
 
@@ -37,7 +38,8 @@ EXPORTS = [
 ]
 
 PASS_NAMES = ["xfwd", "yfwd", "zconv", "yinv", "xinv", "update", "vector", "unused"]
-PASS_NAMES = [k + "_f32" for k in PASS_NAMES] + [k + "_f64" for k in PASS_NAMES]
+PASS_NAMES = ([k + "_f32" for k in PASS_NAMES] + [k + "_f64" for k in PASS_NAMES]
+              + [k + "_df" for k in PASS_NAMES])
 
 
 class Domain(C.Structure):
@@ -51,7 +53,8 @@ class PlanOpts(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
-                ("alpha", C.c_double * 3), ("use_graph", C.c_int), ("reserved", C.c_int * 7)]
+                ("alpha", C.c_double * 3), ("use_graph", C.c_int), ("residual", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class SolveInfo(C.Structure):
@@ -64,17 +67,18 @@ class SolveInfo(C.Structure):
 
 
 class PlanStats(C.Structure):
-    _fields_ = [("kernel_launches", C.c_uint64), ("pass_ms", C.c_double * 16),
-                ("pass_count", C.c_uint64 * 16), ("fp32_matvecs", C.c_uint64),
-                ("fp64_matvecs", C.c_uint64)]
+    _fields_ = [("kernel_launches", C.c_uint64), ("pass_ms", C.c_double * 24),
+                ("pass_count", C.c_uint64 * 24), ("fp32_matvecs", C.c_uint64),
+                ("fp64_matvecs", C.c_uint64), ("df_matvecs", C.c_uint64)]
 
     def as_dict(self):
         return {
             "kernel_launches": int(self.kernel_launches),
-            "pass_ms": {PASS_NAMES[i]: float(self.pass_ms[i]) for i in range(16) if self.pass_count[i]},
-            "pass_count": {PASS_NAMES[i]: int(self.pass_count[i]) for i in range(16) if self.pass_count[i]},
+            "pass_ms": {PASS_NAMES[i]: float(self.pass_ms[i]) for i in range(24) if self.pass_count[i]},
+            "pass_count": {PASS_NAMES[i]: int(self.pass_count[i]) for i in range(24) if self.pass_count[i]},
             "fp32_matvecs": int(self.fp32_matvecs),
             "fp64_matvecs": int(self.fp64_matvecs),
+            "df_matvecs": int(self.df_matvecs),
         }
 
 

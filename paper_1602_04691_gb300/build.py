@@ -19,8 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libori.so")
 
-SOURCES = ["ori_api.cu", "passes_f32.cu", "passes_f64.cu"]
-HEADERS = ["common.cuh", "passes.cuh", "passes_impl.cuh", "scalars.cuh", "vector_kernels.cuh"]
+SOURCES = ["ori_api.cu", "passes_f32.cu", "passes_f64.cu", "passes_df.cu"]
+HEADERS = ["common.cuh", "dfloat.cuh", "passes.cuh", "passes_impl.cuh", "scalars.cuh", "vector_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]

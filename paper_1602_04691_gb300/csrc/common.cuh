@@ -127,7 +127,7 @@ __device__ __forceinline__ cpx<T> tw64_mul(cpx<T> z, int idx) {
   if (idx == 48) return SIGN > 0 ? cpx<T>{z.y, -z.x} : cpx<T>{-z.y, z.x};
   const T c = tw64c<T>(idx);
   const T s = SIGN > 0 ? tw64s<T>(idx) : -tw64s<T>(idx);
-  return {z.x * c - z.y * s, z.x * s + z.y * c};
+  return cmul(z, cpx<T>{c, s});
 }
 
 // Read-only cached loads of one complex number.
@@ -144,9 +144,7 @@ __device__ __forceinline__ cpx<double> ldgc(const cpx<double>* p) {
 template <int SIGN, class T>
 __device__ __forceinline__ cpx<T> twL_mul(cpx<T> z, const cpx<T>* __restrict__ tab, int m) {
   const cpx<T> w = ldgc(tab + m);
-  const T c = w.x;
-  const T s = SIGN > 0 ? w.y : -w.y;
-  return {z.x * c - z.y * s, z.x * s + z.y * c};
+  return cmul(z, cpx<T>{w.x, SIGN > 0 ? w.y : -w.y});
 }
 
 constexpr int bitrev(int i, int R) {

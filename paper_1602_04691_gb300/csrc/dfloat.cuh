@@ -1,0 +1,138 @@
+// dfloat.cuh - paired-FP32 ("double-float") arithmetic for the refinement
+// residual.  A value is hi + lo with |lo| <= ulp(hi)/2: about 48 significant
+// bits.  On a GPU whose FP64 rate is 1/64 of its FP32 rate this gives the
+// FP64-class residual of the iterative refinement several times faster than
+// native FP64.
+//
+// Building blocks (error-free transformations, published methods):
+//   two_sum     Knuth, TAOCP vol. 2, s + e = a + b exactly (6 flops)
+//   fast_two_sum Dekker 1971, same when |a| >= |b| (3 flops)
+//   two_prod    p + e = a * b exactly, e by one fused multiply-add
+// Addition is the "sloppy" pairwise form (one two_sum on the high parts, the
+// low parts added in FP32, one renormalisation): its error is bounded by a
+// small multiple of 2^-48 (|a| + |b|), which keeps FFT butterflies normwise
+// accurate.  Products accumulate all four partial products before one
+// renormalisation.
+#pragma once
+
+#include "common.cuh"
+
+namespace ori {
+
+struct alignas(8) dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e += a.lo + b.lo;
+  dfl r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = a.hi * b.hi;
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  dfl r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+// a*b - c*d with one renormalisation (the real part of a complex product).
+__device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d, float sign) {
+  const float p1 = a.hi * b.hi;
+  const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+  const float p2 = sign * (c.hi * d.hi);
+  const float e2 = __fmaf_rn(sign * c.hi, d.hi, -p2);
+  float s, e;
+  two_sum(p1, p2, s, e);
+  e += e1 + e2;
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  e = __fmaf_rn(sign * c.hi, d.lo, e);
+  e = __fmaf_rn(sign * c.lo, d.hi, e);
+  dfl r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// Complex product in double-float.
+__device__ __forceinline__ cpx<dfl> cmul(cpx<dfl> a, cpx<dfl> b) {
+  return {df_dot2(a.x, b.x, a.y, b.y, -1.0f), df_dot2(a.x, b.y, a.y, b.x, 1.0f)};
+}
+
+// Split a double into hi + lo (hi = nearest float, lo = nearest float of the rest).
+__device__ __forceinline__ dfl df_from_double(double v) {
+  const float hi = __double2float_rn(v);
+  const float lo = __double2float_rn(v - double(hi));
+  return {hi, lo};
+}
+__device__ __forceinline__ double df_to_double(dfl v) { return double(v.hi) + double(v.lo); }
+
+__host__ __forceinline__ dfl df_from_double_host(double v) {
+  const float hi = float(v);
+  const float lo = float(v - double(hi));
+  return {hi, lo};
+}
+
+// Conversions between complex128 and the pass arithmetic T.
+template <class T> __device__ __forceinline__ cpx<T> c_from_c64(cpx<double> v) {
+  return {T(v.x), T(v.y)};
+}
+template <> __device__ __forceinline__ cpx<dfl> c_from_c64<dfl>(cpx<double> v) {
+  return {df_from_double(v.x), df_from_double(v.y)};
+}
+template <class T> __device__ __forceinline__ cpx<double> c_to_c64(cpx<T> v) {
+  return {double(v.x), double(v.y)};
+}
+template <> __device__ __forceinline__ cpx<double> c_to_c64<dfl>(cpx<dfl> v) {
+  return {df_to_double(v.x), df_to_double(v.y)};
+}
+
+// Twiddles of the in-register DFTs in double-float: hi and lo of the FP64
+// compile-time values.
+struct Tw64df {
+  float ch[64], cl[64], sh[64], sl[64];
+};
+constexpr Tw64df make_tw64df() {
+  Tw64df t{};
+  for (int j = 0; j < 64; ++j) {
+    CosSin v = turn_cos_sin(j, 64);
+    t.ch[j] = float(v.c);
+    t.cl[j] = float(v.c - double(float(v.c)));
+    t.sh[j] = float(v.s);
+    t.sl[j] = float(v.s - double(float(v.s)));
+  }
+  return t;
+}
+__constant__ Tw64df c_tw64df = make_tw64df();
+
+template <>
+__device__ __forceinline__ dfl tw64c<dfl>(int i) { return {c_tw64df.ch[i], c_tw64df.cl[i]}; }
+template <>
+__device__ __forceinline__ dfl tw64s<dfl>(int i) { return {c_tw64df.sh[i], c_tw64df.sl[i]}; }
+
+__device__ __forceinline__ cpx<dfl> ldgc(const cpx<dfl>* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+
+template <>
+__device__ __forceinline__ cpx<dfl> czero<dfl>() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+
+}  // namespace ori

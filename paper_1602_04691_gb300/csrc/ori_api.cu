@@ -20,6 +20,7 @@ template <class T> cudaError_t run_xfwd(int, bool, const XArgs&, cudaStream_t, b
 template <class T> cudaError_t run_xinv(int, const XArgs&, Scalars*, int, cudaStream_t, bool, unsigned*);
 template <class T> cudaError_t run_strided(int, int, bool, const SArgs&, cudaStream_t, bool);
 }  // namespace ori
+#include "dfloat.cuh"
 
 using namespace ori;
 
@@ -66,6 +67,10 @@ struct ori_plan_s {
   cpx<float>* w32 = nullptr;
   cpx<float>* S32 = nullptr;
   cpx<double>* Sinv = nullptr;
+  cpx<dfl>* wdf = nullptr;     // h N and sqrt(h N) in paired FP32
+  cpx<dfl>* Sdf = nullptr;
+  cpx<dfl>* ghatdf = nullptr;
+  cpx<dfl>* twdf = nullptr;
   // spectrum and twiddles
   cpx<double>* ghat64 = nullptr;
   cpx<float>* ghat32 = nullptr;
@@ -197,7 +202,7 @@ static void plan_free(ori_plan_s* p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->Sinv, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
+  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->Sinv, p->wdf, p->Sdf, p->ghatdf, p->twdf, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
                   p->T1f, p->T2f, p->T1d, p->T2d, p->sc, p->partials, p->d_count, p->b64, p->w,
                   p->r64, p->u0, p->p64, p->q64, p->x32, p->r32, p->p32, p->q32};
   for (void* q : ptrs)
@@ -243,20 +248,27 @@ static ori_status leave(ori_plan_s* p, cudaStream_t user) {
 
 // One application of the convolution operator: X fwd (prologue), Y fwd, Z
 // conv, Y inv, X inv (epilogue).  `pro` and `epi` carry the mode and vectors.
+template <class T> struct ArithOf;
+template <> struct ArithOf<float> { static constexpr int kind = 0; };
+template <> struct ArithOf<double> { static constexpr int kind = ORI_PASS_FP64; };
+template <> struct ArithOf<dfl> { static constexpr int kind = ORI_PASS_DF; };
+
 template <class T>
 static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s,
                            const int* done) {
-  const bool f32 = sizeof(T) == 4;
+  constexpr int K = ArithOf<T>::kind;
+  const bool f32 = K == 0;
   cpx<T>* T1 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T1f : (void*)p->T1d);
   cpx<T>* T2 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T2f : (void*)p->T2d);
-  const void* tw = f32 ? (const void*)p->tw32 : (const void*)p->tw64;
+  const void* tw = K == 0 ? (const void*)p->tw32 : (K == ORI_PASS_FP64 ? (const void*)p->tw64 : (const void*)p->twdf);
+  const void* gh = K == 0 ? (const void*)p->ghat32 : (K == ORI_PASS_FP64 ? (const void*)p->ghat64 : (const void*)p->ghatdf);
   const int n = p->n, L = p->L;
   int e0 = t_rec(p, s), e1;
   pro.n = n; pro.nlines = n * n; pro.n_in = n; pro.line_len_in = n; pro.line_len_out = L;
   pro.fft_out = T1; pro.twL = tw; pro.done = done;
   ORI_CUDA(run_xfwd<T>(L, true, pro, s, false));
   launched(p);
-  e1 = t_rec(p, s); t_pair(p, ORI_PASS_XFWD + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_XFWD + K, e0, e1); e0 = e1;
 
   SArgs y{};
   y.in = T1; y.out = T2;
@@ -265,19 +277,19 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.twL = tw; y.done = done;
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
   launched(p);
-  e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + K, e0, e1); e0 = e1;
 
   SArgs z{};
   z.in = T2; z.out = T2;
   z.in_outer = L; z.out_outer = L;
   z.in_pt = (long long)L * L; z.out_pt = (long long)L * L;
   z.ncols = L; z.n_in = n; z.n_out = n; z.nouter = L;
-  z.twL = tw; z.ghat = f32 ? (const void*)p->ghat32 : (const void*)p->ghat64; z.H = p->H;
+  z.twL = tw; z.ghat = gh; z.H = p->H;
   z.done = done;
   z.sm_count = p->sm_count;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
   launched(p);
-  e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + K, e0, e1); e0 = e1;
 
   SArgs yi{};
   yi.in = T2; yi.out = T1;
@@ -286,16 +298,17 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   yi.twL = tw; yi.done = done;
   ORI_CUDA(run_strided<T>(L, SMODE_INV, false, yi, s, false));
   launched(p);
-  e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + (f32 ? 0 : ORI_PASS_FP64), e0, e1); e0 = e1;
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + K, e0, e1); e0 = e1;
 
   epi.n = n; epi.nlines = n * n; epi.line_len_in = L; epi.line_len_out = n;
   epi.in = T1; epi.twL = tw; epi.done = done; epi.partials = p->partials;
   ORI_CUDA(run_xinv<T>(L, epi, p->sc, fin, s, false, nullptr));
   launched(p);
-  e1 = t_rec(p, s); t_pair(p, ORI_PASS_XINV + (f32 ? 0 : ORI_PASS_FP64), e0, e1);
+  e1 = t_rec(p, s); t_pair(p, ORI_PASS_XINV + K, e0, e1);
   if (!p->capturing) {
-    if (f32) ++p->stats.fp32_matvecs;
-    else ++p->stats.fp64_matvecs;
+    if (K == 0) ++p->stats.fp32_matvecs;
+    else if (K == ORI_PASS_FP64) ++p->stats.fp64_matvecs;
+    else ++p->stats.df_matvecs;
   }
   return ORI_OK;
 }
@@ -331,7 +344,7 @@ static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N
   ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
-  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->Sinv, p->n3, p->d_count)));
+  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->Sinv, p->wdf, p->Sdf, p->n3, p->d_count)));
   ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   return ORI_OK;
@@ -380,7 +393,7 @@ static ori_status build_spectrum(ori_plan_s* p) {
     e = run_strided<double>(L, SMODE_FWD, false, z, p->ps, false);
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z pass: ") + cudaGetErrorString(e)); break; }
     const double scale = p->c_S * p->d * p->d * p->d / double(L3);
-    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64, p->ghat32, L, p->H, scale);
+    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64, p->ghat32, p->ghatdf, L, p->H, scale);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan extract: ") + cudaGetErrorString(e)); break; }
     e = cudaStreamSynchronize(p->ps);
@@ -411,6 +424,7 @@ void ori_default_solve_opts(ori_solve_opts* o) {
   o->check_every = 8;
   o->alpha[2] = 1.0;
   o->use_graph = 1;
+  o->residual = ORI_DF;
 }
 
 int ori_abi_version(void) { return ORI_ABI_VERSION; }
@@ -479,7 +493,8 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     const size_t H3 = size_t(p->H) * p->H * p->H;
     const size_t t1 = size_t(p->n) * p->n * p->L, t2 = size_t(p->n) * p->L * p->L;
     if ((st = alloc_n(p, &p->h, n3)) || (st = alloc_n(p, &p->N, n3)) || (st = alloc_n(p, &p->w64, n3)) ||
-        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
+        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->wdf, n3)) ||
+        (st = alloc_n(p, &p->Sdf, n3)) || (st = alloc_n(p, &p->ghatdf, H3)) || (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
         (st = alloc_n(p, &p->ghat64, H3)) || (st = alloc_n(p, &p->ghat32, H3)) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
         (st = alloc_n(p, &p->T1f, t1)) || (st = alloc_n(p, &p->T2f, t2)) ||
@@ -487,7 +502,11 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
         (st = alloc_n(p, &p->sc, 1)) || (st = alloc_n(p, &p->d_count, 1)))
       break;
     unsigned bx32 = 0, bx64 = 0;
-    if ((st = setup_kernels<float>(p->L, &bx32, p->n)) || (st = setup_kernels<double>(p->L, &bx64, p->n))) break;
+    unsigned bxdf = 0;
+    if ((st = setup_kernels<float>(p->L, &bx32, p->n)) || (st = setup_kernels<double>(p->L, &bx64, p->n)) ||
+        (st = setup_kernels<dfl>(p->L, &bxdf, p->n)))
+      break;
+    bx64 = std::max(bx64, bxdf);
     p->npartials = std::max<size_t>({size_t(bx32), size_t(bx64), size_t(2 * p->vec_grid)}) + 16;
     if ((st = alloc_n(p, &p->partials, p->npartials))) break;
     if (cudaMallocHost(&p->h_sc, sizeof(Scalars)) != cudaSuccess) { st = fail(ORI_ERR_OOM, "cudaMallocHost failed"); break; }
@@ -496,13 +515,17 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     {
       cpx<double>* twd = new cpx<double>[p->L];
       cpx<float>* twf = new cpx<float>[p->L];
+      cpx<dfl>* twdf = new cpx<dfl>[p->L];
       host_twiddles<double>(p->L, twd);
       host_twiddles<float>(p->L, twf);
+      for (int m = 0; m < p->L; ++m) twdf[m] = {df_from_double_host(twd[m].x), df_from_double_host(twd[m].y)};
       cudaError_t e1 = cudaMemcpy(p->tw64, twd, sizeof(cpx<double>) * p->L, cudaMemcpyHostToDevice);
       cudaError_t e2 = cudaMemcpy(p->tw32, twf, sizeof(cpx<float>) * p->L, cudaMemcpyHostToDevice);
+      cudaError_t e3 = cudaMemcpy(p->twdf, twdf, sizeof(cpx<dfl>) * p->L, cudaMemcpyHostToDevice);
       delete[] twd;
       delete[] twf;
-      if (e1 != cudaSuccess || e2 != cudaSuccess) { st = fail(ORI_ERR_CUDA, "twiddle upload failed"); break; }
+      delete[] twdf;
+      if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) { st = fail(ORI_ERR_CUDA, "twiddle upload failed"); break; }
     }
     if ((st = set_medium(p, h_dev, N_dev))) break;
     if ((st = build_spectrum(p))) break;
@@ -576,7 +599,8 @@ ori_status ori_matvec(ori_plan_t p, const double* x_dev, double* y_dev, int form
   g_last_error.clear();
   if (!p || !x_dev || !y_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
   if (form != ORI_FORM_A && form != ORI_FORM_B) return fail(ORI_ERR_INVALID_ARG, "form must be ORI_FORM_A or ORI_FORM_B");
-  if (precision != ORI_FP64 && precision != ORI_FP32) return fail(ORI_ERR_INVALID_ARG, "precision must be ORI_FP64 or ORI_FP32");
+  if (precision != ORI_FP64 && precision != ORI_FP32 && precision != ORI_DF)
+    return fail(ORI_ERR_INVALID_ARG, "precision must be ORI_FP64, ORI_FP32 or ORI_DF");
   if (x_dev == y_dev) return fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
   ORI_TRY(enter(p, user));
@@ -590,12 +614,18 @@ ori_status ori_matvec(ori_plan_t p, const double* x_dev, double* y_dev, int form
     epi.mode = form == ORI_FORM_A ? EPI_PLUS : EPI_PLUS_S;
     epi.scale = p->S64;
     ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, nullptr));
-  } else {
+  } else if (precision == ORI_FP32) {
     pro.mode = PRO_SCALE_D;
     pro.scale = form == ORI_FORM_A ? (const void*)p->w32 : (const void*)p->S32;
     epi.mode = form == ORI_FORM_A ? EPI_PLUS_D : EPI_PLUS_S_D;
     epi.scale = p->S32;
     ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+  } else {
+    pro.mode = PRO_SCALE_D;
+    pro.scale = form == ORI_FORM_A ? (const void*)p->wdf : (const void*)p->Sdf;
+    epi.mode = form == ORI_FORM_A ? EPI_PLUS_D : EPI_PLUS_S_D;
+    epi.scale = p->Sdf;
+    ORI_TRY(run_conv<dfl>(p, pro, epi, FIN_NONE, p->ps, nullptr));
   }
   return leave(p, user);
 }
@@ -740,18 +770,20 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
   return ORI_OK;
 }
 
-// r64 = b64 - B w in FP64; returns ||r64||.
-static ori_status fp64_residual(ori_plan_s* p, double* rnorm) {
+// r64 = b64 - B w with complex128 vectors; the FFT passes run in paired FP32
+// (use_df) or native FP64.  Returns ||r64||.
+static ori_status fp64_residual(ori_plan_s* p, double* rnorm, bool use_df) {
   XArgs pro{}, epi{};
-  pro.mode = PRO_SCALE;
+  pro.mode = use_df ? PRO_SCALE_D : PRO_SCALE;
   pro.x = p->w;
-  pro.scale = p->S64;
+  pro.scale = use_df ? (const void*)p->Sdf : (const void*)p->S64;
   epi.mode = EPI_RESID;
   epi.xin = p->w;
   epi.bvec = p->b64;
   epi.out = p->r64;
   epi.scale = p->S64;
-  ORI_TRY(run_conv<double>(p, pro, epi, FIN_SUM, p->ps, nullptr));
+  if (use_df) ORI_TRY(run_conv<dfl>(p, pro, epi, FIN_SUM, p->ps, nullptr));
+  else ORI_TRY(run_conv<double>(p, pro, epi, FIN_SUM, p->ps, nullptr));
   ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   if (p->timing) t_harvest(p);
@@ -791,7 +823,7 @@ static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, 
     info->outer_iters = 1;
     info->relres_recur = ir.relres_recur;
     double rn = 0;
-    ORI_TRY(fp64_residual(p, &rn));
+    ORI_TRY(fp64_residual(p, &rn, false));
     info->fp64_matvecs = 1;
     info->relres = rn / bnorm;
     info->status = ir.done == DONE_CONVERGED ? (info->relres <= 10 * o.tol ? ORI_OK : ORI_ERR_NOT_CONVERGED)
@@ -819,7 +851,7 @@ static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, 
     if (ir.done == DONE_NONFINITE) break;
     ORI_VEC(p, ORI_PASS_VECTOR, (k_accumulate<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->x32, n3, rn)));
     double rn_new = 0;
-    ORI_TRY(fp64_residual(p, &rn_new));
+    ORI_TRY(fp64_residual(p, &rn_new, o.residual == ORI_DF));
     info->fp64_matvecs += 1;
     const bool stalled = rn_new > 0.9 * rn;
     rn = rn_new;
@@ -848,6 +880,8 @@ static ori_status check_solve_opts(const ori_solve_opts* in, ori_solve_opts* o) 
   if (o->max_outer < 1) return fail(ORI_ERR_INVALID_ARG, "max_outer must be >= 1");
   if (o->check_every < 1 || o->check_every > 1024) return fail(ORI_ERR_INVALID_ARG, "check_every must be in [1, 1024]");
   if (!finite3(o->alpha)) return fail(ORI_ERR_INVALID_ARG, "alpha must be finite");
+  if (o->residual != ORI_DF && o->residual != ORI_FP64)
+    return fail(ORI_ERR_INVALID_ARG, "residual must be ORI_DF or ORI_FP64");
   return ORI_OK;
 }
 

@@ -2,6 +2,7 @@
 // Included by one translation unit per precision (passes_f32.cu, passes_f64.cu).
 #pragma once
 
+#include "dfloat.cuh"
 #include "passes.cuh"
 #include "scalars.cuh"
 
@@ -29,7 +30,7 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
     case PRO_SCALE_D: {
       const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
       const cpx<double> v = reinterpret_cast<const cpx<double>*>(a.x)[i];
-      return cmul(s, ccast<T>(v));
+      return cmul(s, c_from_c64<T>(v));
     }
     case PRO_COCG_FIRST: {
       const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
@@ -42,7 +43,7 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
       const cpx<T> r = reinterpret_cast<const cpx<T>*>(a.x)[i];
       cpx<T>* pp = reinterpret_cast<cpx<T>*>(a.p) + i;
       const double2 bd = *reinterpret_cast<const double2*>(a.beta);
-      const cpx<T> b = {T(bd.x), T(bd.y)};
+      const cpx<T> b = c_from_c64<T>(cpx<double>{bd.x, bd.y});
       const cpx<T> p = r + cmul(b, *pp);
       *pp = p;
       return cmul(s, p);
@@ -57,7 +58,7 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
       double sn, cs;
       sincos(a.k * r, &sn, &cs);
       const double g = 1.0 / (4.0 * kPi * r);   // G = exp(ikr) / (4 pi r)
-      return {T(cs * g), T(sn * g)};
+      return c_from_c64<T>(cpx<double>{cs * g, sn * g});
     }
   }
 }
@@ -177,13 +178,13 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc
           } break;
           case EPI_PLUS_D: {
             const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
-            const cpx<double> vd = ccast<double>(v);
+            const cpx<double> vd = c_to_c64(v);
             reinterpret_cast<cpx<double>*>(a.out)[i] = xi + vd;
           } break;
           case EPI_PLUS_S_D: {
             const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
             const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            reinterpret_cast<cpx<double>*>(a.out)[i] = xi + ccast<double>(cmul(s, v));
+            reinterpret_cast<cpx<double>*>(a.out)[i] = xi + c_to_c64(cmul(s, v));
           } break;
           case EPI_COCG: {
             const cpx<T> p = reinterpret_cast<const cpx<T>*>(a.xin)[i];
@@ -192,32 +193,34 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc
             reinterpret_cast<cpx<T>*>(a.out)[i] = q;
             accT = accT + cmul(p, q);                 // p^T q, no conjugate
           } break;
-          case EPI_RESID: {
-            const cpx<T> w = reinterpret_cast<const cpx<T>*>(a.xin)[i];
-            const cpx<T> b = reinterpret_cast<const cpx<T>*>(a.bvec)[i];
-            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            const cpx<T> rr = b - (w + cmul(s, v));
-            reinterpret_cast<cpx<T>*>(a.out)[i] = rr;
-            acc.x += double(rr.x) * double(rr.x) + double(rr.y) * double(rr.y);
+          case EPI_RESID: {   // complex128 vectors whatever T is
+            const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+            const cpx<double> b = reinterpret_cast<const cpx<double>*>(a.bvec)[i];
+            const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);
+            const cpx<double> rr = b - (w + cmul(s, c_to_c64(v)));
+            reinterpret_cast<cpx<double>*>(a.out)[i] = rr;
+            acc.x += rr.x * rr.x + rr.y * rr.y;
           } break;
-          default: {  // EPI_RECOVER: u = w / s where s != 0, else b - v
-            const cpx<T> w = reinterpret_cast<const cpx<T>*>(a.xin)[i];
-            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            cpx<T> u;
-            if (s.x != T(0) || s.y != T(0)) {
-              const T den = s.x * s.x + s.y * s.y;
+          default: {  // EPI_RECOVER: u = w / s where s != 0, else b - v (complex128)
+            const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+            const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);
+            const cpx<double> vd = c_to_c64(v);
+            cpx<double> u;
+            if (s.x != 0.0 || s.y != 0.0) {
+              const double den = s.x * s.x + s.y * s.y;
               u = {(w.x * s.x + w.y * s.y) / den, (w.y * s.x - w.x * s.y) / den};
             } else {
-              const cpx<T> b = reinterpret_cast<const cpx<T>*>(a.bvec)[i];
-              u = b - v;
+              const cpx<double> b = reinterpret_cast<const cpx<double>*>(a.bvec)[i];
+              u = b - vd;
             }
-            reinterpret_cast<cpx<T>*>(a.out)[i] = u;
+            reinterpret_cast<cpx<double>*>(a.out)[i] = u;
           } break;
         }
       }
     }
-    acc.x += double(accT.x);
-    acc.y += double(accT.y);
+    const cpx<double> accD = c_to_c64(accT);
+    acc.x += accD.x;
+    acc.y += accD.y;
   }
   if (fin == FIN_NONE) return;
   block_partial(acc, red, a.partials);

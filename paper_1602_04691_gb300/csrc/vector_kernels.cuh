@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "passes.cuh"
 #include "scalars.cuh"
 
@@ -28,7 +29,8 @@ __device__ __forceinline__ cpx<double> cdivd(cpx<double> a, cpx<double> b) {
 // counts cells with S == 0 and cells with h == 0 or N == 0.
 __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __restrict__ N,
                          cpx<double>* w64, cpx<double>* S64, cpx<float>* w32, cpx<float>* S32,
-                         cpx<double>* Sinv, long long n3, unsigned long long* zero_count) {
+                         cpx<double>* Sinv, cpx<dfl>* wdf, cpx<dfl>* Sdf, long long n3,
+                         unsigned long long* zero_count) {
   unsigned long long zs = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x) {
@@ -40,6 +42,8 @@ __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __rest
     S64[i] = s;
     w32[i] = ccast<float>(w);
     S32[i] = ccast<float>(s);
+    wdf[i] = c_from_c64<dfl>(w);
+    Sdf[i] = c_from_c64<dfl>(s);
     if (w.x == 0.0 && w.y == 0.0) {
       ++zs;
       Sinv[i] = {0.0, 0.0};
@@ -53,7 +57,7 @@ __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __rest
 // Spectrum of the kernel cube: keep the (L/2+1)^3 distinct entries of the
 // even cube and fold in c_S |Delta| / L^3.
 __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>* g64,
-                               cpx<float>* g32, int L, int H, double scale) {
+                               cpx<float>* g32, cpx<dfl>* gdf, int L, int H, double scale) {
   const long long total = (long long)H * H * H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -62,6 +66,7 @@ __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>
     const cpx<double> s = {v.x * scale, v.y * scale};
     g64[i] = s;
     g32[i] = ccast<float>(s);
+    gdf[i] = c_from_c64<dfl>(s);
   }
 }
 

@@ -14,10 +14,10 @@ import math
 import torch
 
 from . import _lib
-from ._lib import ORI_FORM_A, ORI_FORM_B, ORI_FP32, ORI_FP64, ORI_MIXED, OriError  # noqa: F401
+from ._lib import ORI_DF, ORI_FORM_A, ORI_FORM_B, ORI_FP32, ORI_FP64, ORI_MIXED, OriError  # noqa: F401
 
 _FORMS = {"A": ORI_FORM_A, "B": ORI_FORM_B}
-_PREC = {"fp64": ORI_FP64, "fp32": ORI_FP32, "mixed": ORI_MIXED}
+_PREC = {"fp64": ORI_FP64, "fp32": ORI_FP32, "mixed": ORI_MIXED, "df": ORI_DF}
 
 
 def _stream_ptr(stream=None) -> int:
@@ -36,7 +36,7 @@ def _need(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
 
 
 def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_outer=8,
-               check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True) -> _lib.SolveOpts:
+               check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True, residual="df") -> _lib.SolveOpts:
     lib = _lib.load()
     o = _lib.SolveOpts()
     lib.ori_default_solve_opts(C.byref(o))
@@ -49,6 +49,7 @@ def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_oute
     for i in range(3):
         o.alpha[i] = float(alpha[i])
     o.use_graph = 1 if use_graph else 0
+    o.residual = _PREC[residual]
     return o
 
 

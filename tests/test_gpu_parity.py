@@ -71,6 +71,31 @@ def test_fp64_matvec_B_vs_direct_sum(n):
     assert rel(y, ref) < 1e-12
 
 
+@pytest.mark.parametrize("n", [2, 3, 8, 13, 16])
+def test_df_matvec_vs_direct_sum(n):
+    """Paired-FP32 (double-float) operator: held to the FP64 bar (1e-12)."""
+    k = 3.3
+    h, N = inputs.random_h_N(n, 700 + n)
+    x = inputs.random_complex(n ** 3, 800 + n)
+    plan = make_plan(n, k, h, N)
+    yA = plan.matvec(to_dev(x), form="A", precision="df").cpu().numpy()
+    yB = plan.matvec(to_dev(x), form="B", precision="df").cpu().numpy()
+    assert rel(yA, O.red_matvec_direct(x, n, k, h, N)) < 1e-12
+    assert rel(yB, O.symmetrised_matvec_direct(x, n, k, h, N)) < 1e-12
+
+
+def test_df_matvec_sampled_rows_n64():
+    n, k = 64, 5.0
+    h, N = inputs.random_h_N(n, 3)
+    x = inputs.random_complex(n ** 3, 17)
+    plan = make_plan(n, k, h, N)
+    y = plan.matvec(to_dev(x), form="A", precision="df").cpu().numpy()
+    y64 = plan.matvec(to_dev(x), form="A", precision="fp64").cpu().numpy()
+    rows = np.random.default_rng(18).choice(n ** 3, 64, replace=False)
+    assert rel(y[rows], O.red_matvec_rows(x, rows, n, k, h, N)) < 1e-12
+    assert rel(y, y64) < 1e-12
+
+
 @pytest.mark.parametrize("n", [4, 9, 16, 24])
 def test_fp32_matvec_vs_direct_sum(n):
     k = 5.0
@@ -152,12 +177,13 @@ def test_config1_fp64_solve_vs_lu():
     assert rel(u.cpu().numpy(), u_lu) < 1e-9
 
 
-@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-11, 1e-9), ("mixed", 1e-6, 2e-5)])
-def test_variable_medium_solve_vs_lu(precision, tol, bound):
+@pytest.mark.parametrize("precision,tol,bound,residual", [("fp64", 1e-11, 1e-9, "df"), ("mixed", 1e-6, 2e-5, "df"),
+                                                          ("mixed", 1e-6, 2e-5, "fp64"), ("mixed", 1e-10, 1e-8, "df")])
+def test_variable_medium_solve_vs_lu(precision, tol, bound, residual):
     n, k = 10, 2.0
     h, N = inputs.random_h_N(n, 2)
     plan = make_plan(n, k, h, N)
-    u, info = plan.solve(tol=tol, precision=precision)
+    u, info = plan.solve(tol=tol, precision=precision, residual=residual)
     u_lu = O.solve_dense(O.red_matrix(n, k, h, N), O.plane_wave(O.cell_centres(n), k))
     assert info["relres"] <= tol
     assert rel(u.cpu().numpy(), u_lu) < bound
@@ -188,12 +214,13 @@ def test_fp64_solve_vs_oracle_fft_cocg_n24():
     assert rel(u.cpu().numpy(), u_or) < 1e-8
 
 
-def test_mixed_vs_fp64_n32():
+@pytest.mark.parametrize("residual", ["df", "fp64"])
+def test_mixed_vs_fp64_n32(residual):
     n, k = 32, 5.0
     h, N = inputs.random_h_N(n, 3)
     plan = make_plan(n, k, h, N)
     u64, i64 = plan.solve(tol=1e-10, precision="fp64")
-    um, im = plan.solve(tol=1e-6, precision="mixed")
+    um, im = plan.solve(tol=1e-6, precision="mixed", residual=residual)
     assert im["relres"] <= 1e-6
     assert im["outer_iters"] >= 1 and im["fp64_matvecs"] >= 1
     assert rel(um.cpu().numpy(), u64.cpu().numpy()) < 1e-5
