@@ -101,7 +101,11 @@ typedef struct {
   int    residual;     /* ORI_MIXED: arithmetic of the FP64-class refinement residual
                           b - B w: ORI_DF (default; inputs and output complex128,
                           FFT passes in paired FP32) or ORI_FP64 (native FP64)      */
-  int    reserved[6];
+  int    resid_update; /* ORI_MIXED: 1 (default) lets later refinement steps update
+                          the residual with an FP32 operator application when the
+                          error bound allows (see ori_solve_info.resid_updates);
+                          0 recomputes b - B w every step                           */
+  int    reserved[5];
 } ori_solve_opts;
 
 typedef struct {
@@ -113,6 +117,11 @@ typedef struct {
   double relres_recur;  /* last recursive residual of the inner COCG                 */
   int    status;        /* ori_status of the solve                                   */
   float  ms;            /* device time of the solve (CUDA events)                    */
+  int    resid_updates; /* ORI_MIXED: refinement residuals updated as r -= |r| B d
+                           with an FP32 operator application (allowed once |r| is
+                           small enough that the FP32 error bound times |r| stays
+                           under 5% of tol |RHS|)                                     */
+  double relres_bound;  /* bound on |relres - true relres| from those updates        */
 } ori_solve_info;
 
 /* Fill *o with the defaults named above. */

@@ -54,13 +54,13 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
                 ("alpha", C.c_double * 3), ("use_graph", C.c_int), ("residual", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("resid_update", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer_iters", C.c_int), ("fp64_matvecs", C.c_int),
                 ("relres", C.c_double), ("relres_recur", C.c_double), ("status", C.c_int),
-                ("ms", C.c_float)]
+                ("ms", C.c_float), ("resid_updates", C.c_int), ("relres_bound", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -52,7 +52,8 @@ enum { EPI_PLUS = 0,           // y = x + v                   (A form)
        EPI_PLUS_S_D = 3,       // y = x + s v, x,y complex128 (B form, FP32 math)
        EPI_COCG = 4,           // q = p + s v; partial sum p^T q
        EPI_RESID = 5,          // r = b - (w + s v); partial sum ||r||^2
-       EPI_RECOVER = 6 };      // u = w / s, or b - v where s == 0
+       EPI_RECOVER = 6,        // u = w / s, or b - v where s == 0
+       EPI_RUPDATE = 7 };      // r -= c (d + s v), r complex128; partial ||r||^2
 
 struct XArgs {
   // prologue
@@ -64,7 +65,8 @@ struct XArgs {
   double d, k;
   // epilogue
   const void* xin;      // x (EPI_PLUS*), p (EPI_COCG), w (EPI_RESID/RECOVER)
-  const void* bvec;     // b (EPI_RESID, EPI_RECOVER)
+  const void* bvec;     // b (EPI_RESID, EPI_RECOVER); r (EPI_RUPDATE, in place)
+  double coef;          // c of EPI_RUPDATE
   void* out;            // y / q / r / u
   double2* partials;    // per-block partial sums
   // geometry

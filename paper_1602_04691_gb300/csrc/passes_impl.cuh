@@ -201,6 +201,17 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc
             reinterpret_cast<cpx<double>*>(a.out)[i] = rr;
             acc.x += rr.x * rr.x + rr.y * rr.y;
           } break;
+          case EPI_RUPDATE: {  // r -= c (d + s v): residual update with this precision's operator
+            const cpx<double> dv = c_to_c64(reinterpret_cast<const cpx<T>*>(a.xin)[i]);
+            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+            const cpx<double> bd = c_to_c64(cmul(s, v));
+            cpx<double>* rp = reinterpret_cast<cpx<double>*>(const_cast<void*>(a.bvec)) + i;
+            cpx<double> rr = *rp;
+            rr.x -= a.coef * (dv.x + bd.x);
+            rr.y -= a.coef * (dv.y + bd.y);
+            *rp = rr;
+            acc.x += rr.x * rr.x + rr.y * rr.y;
+          } break;
           default: {  // EPI_RECOVER: u = w / s where s != 0, else b - v (complex128)
             const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
             const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);

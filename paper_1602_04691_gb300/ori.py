@@ -36,7 +36,8 @@ def _need(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
 
 
 def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_outer=8,
-               check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True, residual="df") -> _lib.SolveOpts:
+               check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True, residual="df",
+               resid_update=True) -> _lib.SolveOpts:
     lib = _lib.load()
     o = _lib.SolveOpts()
     lib.ori_default_solve_opts(C.byref(o))
@@ -50,6 +51,7 @@ def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_oute
         o.alpha[i] = float(alpha[i])
     o.use_graph = 1 if use_graph else 0
     o.residual = _PREC[residual]
+    o.resid_update = 1 if resid_update else 0
     return o
 
 

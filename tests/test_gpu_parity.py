@@ -226,6 +226,27 @@ def test_mixed_vs_fp64_n32(residual):
     assert rel(um.cpu().numpy(), u64.cpu().numpy()) < 1e-5
 
 
+@pytest.mark.parametrize("resid_update", [True, False])
+def test_mixed_residual_is_certified(resid_update):
+    """The mixed solve's reported residual (and bound) agrees with an independent
+    FP64 evaluation of ||S u0 - B (S u)|| / ||S u0|| from the returned u."""
+    n, k = 40, 5.0
+    h, N = inputs.random_h_N(n, 41)
+    plan = make_plan(n, k, h, N)
+    u, info = plan.solve(tol=1e-6, precision="mixed", resid_update=resid_update)
+    S = O.sqrt_hN(h, N)
+    u0 = O.plane_wave(O.cell_centres(n), k)
+    w = S * u.cpu().numpy()
+    Bw = plan.matvec(to_dev(w), form="B", precision="fp64").cpu().numpy()
+    true_rel = np.linalg.norm(S * u0 - Bw) / np.linalg.norm(S * u0)
+    assert true_rel <= 1e-6
+    assert abs(true_rel - info["relres"]) <= info["relres_bound"] + 1e-12
+    if resid_update:
+        assert info["resid_updates"] >= 1 and info["fp64_matvecs"] == 1
+    else:
+        assert info["resid_updates"] == 0
+
+
 def test_zero_impedance_returns_incident_field():
     n, k = 6, 1.5
     h, N = inputs.constant_h_N(n, 0.0, 1.0)
