@@ -143,7 +143,8 @@ __device__ __forceinline__ cpx<double> ldgc(const cpx<double>* p) {
 // z * exp(SIGN * 2 pi i m / L) from a table tab[m] = (cos, sin)(2 pi m / L).
 template <int SIGN, class T>
 __device__ __forceinline__ cpx<T> twL_mul(cpx<T> z, const cpx<T>* __restrict__ tab, int m) {
-  const cpx<T> w = ldgc(tab + m);
+  // generic load: the table may sit in global memory or in shared memory
+  const cpx<T> w = tab[m];
   return cmul(z, cpx<T>{w.x, SIGN > 0 ? w.y : -w.y});
 }
 

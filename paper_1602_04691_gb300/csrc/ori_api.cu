@@ -74,6 +74,7 @@ struct ori_plan_s {
   // spectrum and twiddles
   cpx<double>* ghat64 = nullptr;
   cpx<float>* ghat32 = nullptr;
+  cpx<float>* ghatZ32 = nullptr;   // FP32 spectrum in Z-tile order
   cpx<double>* tw64 = nullptr;
   cpx<float>* tw32 = nullptr;
   // pass scratch
@@ -202,7 +203,7 @@ static void plan_free(ori_plan_s* p) {
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->Sinv, p->wdf, p->Sdf, p->ghatdf, p->twdf, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
+  void* ptrs[] = {p->ghatZ32, p->h, p->N, p->w64, p->S64, p->Sinv, p->wdf, p->Sdf, p->ghatdf, p->twdf, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
                   p->T1f, p->T2f, p->T1d, p->T2d, p->sc, p->partials, p->d_count, p->b64, p->w,
                   p->r64, p->u0, p->p64, p->q64, p->x32, p->r32, p->p32, p->q32};
   for (void* q : ptrs)
@@ -284,7 +285,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.in_outer = L; z.out_outer = L;
   z.in_pt = (long long)L * L; z.out_pt = (long long)L * L;
   z.ncols = L; z.n_in = n; z.n_out = n; z.nouter = L;
-  z.twL = tw; z.ghat = gh; z.H = p->H;
+  z.twL = tw; z.ghat = gh; z.ghatZ = p->ghatZ32; z.H = p->H;
   z.done = done;
   z.sm_count = p->sm_count;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
@@ -396,6 +397,9 @@ static ori_status build_spectrum(ori_plan_s* p) {
     k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64, p->ghat32, p->ghatdf, L, p->H, scale);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan extract: ") + cudaGetErrorString(e)); break; }
+    k_build_ghatZ<<<p->vec_grid, 256, 0, p->ps>>>(p->ghat32, p->ghatZ32, L, p->H);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z spectrum: ") + cudaGetErrorString(e)); break; }
     e = cudaStreamSynchronize(p->ps);
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan spectrum: ") + cudaGetErrorString(e)); break; }
   } while (0);
@@ -497,6 +501,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
         (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->wdf, n3)) ||
         (st = alloc_n(p, &p->Sdf, n3)) || (st = alloc_n(p, &p->ghatdf, H3)) || (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
         (st = alloc_n(p, &p->ghat64, H3)) || (st = alloc_n(p, &p->ghat32, H3)) ||
+        (st = alloc_n(p, &p->ghatZ32, size_t(p->H) * p->H * p->L)) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
         (st = alloc_n(p, &p->T1f, t1)) || (st = alloc_n(p, &p->T2f, t2)) ||
         (st = alloc_n(p, &p->T1d, t1)) || (st = alloc_n(p, &p->T2d, t2)) ||

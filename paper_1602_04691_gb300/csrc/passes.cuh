@@ -94,6 +94,7 @@ struct SArgs {
   int nouter;
   const void* twL;
   const void* ghat;                // spectrum, H^3 entries (SMODE_ZCONV)
+  const void* ghatZ;               // FP32 spectrum in Z-tile order [my][kx/16][mz][16]
   int H;                           // L/2 + 1
   const int* done;
   int sm_count;                    // persistent kernels: CTAs to launch

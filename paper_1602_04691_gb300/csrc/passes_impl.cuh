@@ -555,9 +555,11 @@ template <int L, int C, class T>
 struct ZPipe {
   using TL = Tile<L, C, T>;
   static constexpr int NT = TL::NT;
+  static constexpr bool GZ = sizeof(T) == 4;              // spectrum staged through smem
   static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
-  static constexpr size_t S_ELEMS = size_t(L / 2) * C;   // staged input rows (n <= L/2)
-  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS) * sizeof(cpx<T>);
+  static constexpr size_t S_ELEMS = size_t(L / 2 + (GZ ? 1 : 0)) * C;  // input rows / spectrum slice
+  static constexpr size_t TW_ELEMS = GZ ? size_t(L) : 0;                // twiddle table copy
+  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + TW_ELEMS) * sizeof(cpx<T>);
 };
 
 template <class T, int L, int C>
@@ -577,16 +579,36 @@ __device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, cpx<T>*
   cp_async_commit();
 }
 
+// The spectrum slice of a tile: entries (mz, my(ky), kx) for mz in [0, L/2],
+// kx in the tile, stored contiguously as [mz][C] in the Z-tile order.
+template <class T, int L, int C>
+__device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int ky, int cb, cpx<T>* S) {
+  constexpr int NT = ZPipe<L, C, T>::NT;
+  const int my = mirror_index(ky, L);
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.ghatZ) + ((long long)my * (L / C) + cb) * (L / 2 + 1) * C;
+  constexpr int EPC = 16 / int(sizeof(cpx<T>));
+  constexpr int chunks = (L / 2 + 1) * C / EPC;
+  for (int k = threadIdx.x; k < chunks; k += NT) cp_async16(S + k * EPC, src + k * EPC);
+  cp_async_commit();
+}
+
 template <class T, int L, int C>
 __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a) {
   using TL = Tile<L, C, T>;
+  using ZP = ZPipe<L, C, T>;
+  constexpr bool GZ = ZP::GZ;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PK = TL::PK, PC = TL::PC, PKI = TL::PKI, PCI = TL::PCI;
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
-  cpx<T>* S = E + ZPipe<L, C, T>::E_ELEMS;
+  cpx<T>* S = E + ZP::E_ELEMS;
+  cpx<T>* TWS = S + ZP::S_ELEMS;
   if (a.done != nullptr && *a.done != 0) return;
-  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  if (GZ) {
+    for (int i = threadIdx.x; i < L; i += NT) TWS[i] = twg[i];
+  }
+  const cpx<T>* tw = GZ ? TWS : twg;
   const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
   const int col_blocks = L / C;
   const int ntiles = L * col_blocks;
@@ -610,13 +632,15 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
         if (j < a.n_in) r[j1] = S[j * C + c];
       }
     }
-    __syncthreads();   // staging buffer consumed: stream the next tile in
-    if (tile + (int)gridDim.x < ntiles) zpipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
+    __syncthreads();   // staging buffer consumed
+    if (GZ) zpipe_prefetch_ghat<T, L, C>(a, ky, cb, S);
+    else if (tile + (int)gridDim.x < ntiles) zpipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
     dft<L1, -1, true>(r);
 #pragma unroll
     for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (jl * k1) & (L - 1));
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
+    if (GZ) cp_async_wait_all();
     __syncthreads();
     // stage 2 (DFT over j2), spectrum, inverse stage A (DFT over k2)
     cpx<T> b[NI][L2];
@@ -632,13 +656,15 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
 #pragma unroll
       for (int k2 = 0; k2 < L2; ++k2) {
         const int mz = mirror_index(k1 + L1 * k2, L);
-        b[it][k2] = cmul(b[it][k2], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
+        const cpx<T> g = GZ ? S[mz * C + c2] : ldgc(gh + ((long long)mz * a.H + my) * a.H + mx);
+        b[it][k2] = cmul(b[it][k2], g);
       }
       dft<L2, +1, false>(b[it]);
 #pragma unroll
       for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
     }
-    __syncthreads();   // forward exchange fully read
+    __syncthreads();   // forward exchange and the spectrum slice fully read
+    if (GZ && tile + (int)gridDim.x < ntiles) zpipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
       const int s = tid + it * NT;

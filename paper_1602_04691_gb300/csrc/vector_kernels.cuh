@@ -70,6 +70,26 @@ __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>
   }
 }
 
+// FP32 spectrum in the order the Z pass reads it: for each my and each block
+// of 16 kx columns, the entries mz = 0..L/2 as rows of 16 (one contiguous
+// slice per Z tile).  gz[((my * (L/16) + cb) * H + mz) * 16 + c] =
+// g32[(mz * H + my) * H + m(cb*16 + c)].
+__global__ void k_build_ghatZ(const cpx<float>* __restrict__ g32, cpx<float>* gz, int L, int H) {
+  const long long total = (long long)H * (L / 16) * H * 16;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i % 16);
+    const long long r = i / 16;
+    const int mz = int(r % H);
+    const long long t = r / H;
+    const int cb = int(t % (L / 16));
+    const int my = int(t / (L / 16));
+    const int kx = cb * 16 + c;
+    const int mx = kx <= L / 2 ? kx : L - kx;
+    gz[i] = g32[((long long)mz * H + my) * H + mx];
+  }
+}
+
 // Reduction helper for the vector kernels: two double2 partials per block.
 __device__ __forceinline__ void block_partial2(double2 a, double2 b, double2* red,
                                                double2* partials) {
