@@ -181,6 +181,37 @@ ori_status ori_matvec32(ori_plan_t plan, const float* x_dev, float* y_dev,
                         int form, void* stream);
 
 /*
+ * ori_matvec_noalloc - y = A x, the operator of ori_matvec(ORI_FORM_A,
+ * ORI_FP64), for grids of at most ORI_NOALLOC_MAX_N cells per axis, without
+ * a plan and without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate —
+ * code whose device memory belongs to another framework's pool, where a raw
+ * cudaMalloc is not allowed; latency-critical code that must not risk the
+ * device-wide synchronisation cudaMalloc and cudaFree can cause; code under a
+ * rule that forbids dynamic allocation after start-up.
+ *   n, k, dom  as for ori_plan, with 2 <= n <= ORI_NOALLOC_MAX_N.
+ *   c_S        surface constant (0 -> 4 pi).
+ *   h_dev, N_dev, x_dev  n^3 complex128 / float64 / complex128 device inputs.
+ *   y_dev      n^3 complex128 device output; must not overlap x_dev.
+ * Every intermediate (twiddles, h N, the kernel cube and its spectrum, the FFT
+ * work cubes) lives in one static device array of ORI_NOALLOC_SCRATCH_BYTES
+ * bytes that each GPU loading the library holds until the process exits.
+ * The first call on a device (with that device current) looks up the array's
+ * device address and sets kernel attributes; make that first call before
+ * any stream capture.  Each call recomputes the spectrum (cheap at these
+ * sizes) and writes every scratch element it reads, so the array keeps the
+ * last call's contents without harm.  All calls share the one array: calls
+ * that overlap on the GPU (different streams, or threads on one device) race;
+ * serialise them.  n beyond the maximum returns ORI_ERR_INVALID_ARG before
+ * any device work.  Asynchronous on `stream` after the first call's set-up.
+ */
+#define ORI_NOALLOC_MAX_N 16
+#define ORI_NOALLOC_SCRATCH_BYTES 669184
+ori_status ori_matvec_noalloc(int64_t n, double k, const ori_domain* dom, double c_S,
+                              const double* h_dev, const double* N_dev,
+                              const double* x_dev, double* y_dev, void* stream);
+
+/*
  * ori_cocg_solve - solve A u = rhs (Eq. 2.19).
  *   rhs_dev  n^3 complex128 right-hand side, or NULL for the plane wave
  *            u0 = exp(ik alpha . x_p) with alpha = opts->alpha (Eq. 2.4).

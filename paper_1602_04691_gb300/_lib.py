@@ -34,7 +34,7 @@ EXPORTS = [
     "ori_default_solve_opts", "ori_default_plan_opts", "ori_plan", "ori_plan_set_medium",
     "ori_plan_destroy", "ori_plan_info", "ori_matvec", "ori_matvec32", "ori_cocg_solve",
     "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
-    "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats",
+    "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats", "ori_matvec_noalloc",
 ]
 
 PASS_NAMES = ["xfwd", "yfwd", "zconv", "yinv", "xinv", "update", "vector", "unused"]
@@ -128,6 +128,8 @@ def load():
     lib.ori_plan_get_stats.restype = i
     lib.ori_plan_reset_stats.argtypes = [vp]
     lib.ori_plan_reset_stats.restype = i
+    lib.ori_matvec_noalloc.argtypes = [i64, d, C.POINTER(Domain), d, vp, vp, vp, vp, vp]
+    lib.ori_matvec_noalloc.restype = i
     lib.ori_status_string.argtypes = [i]
     lib.ori_status_string.restype = C.c_char_p
     lib.ori_last_error.argtypes = []

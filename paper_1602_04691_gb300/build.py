@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libori.so")
 
-SOURCES = ["ori_api.cu", "passes_f32.cu", "passes_f64.cu", "passes_df.cu"]
+SOURCES = ["ori_api.cu", "ori_noalloc.cu", "passes_f32.cu", "passes_f64.cu", "passes_df.cu"]
 HEADERS = ["common.cuh", "dfloat.cuh", "passes.cuh", "passes_impl.cuh", "scalars.cuh", "vector_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -34,6 +34,10 @@ static ori_status fail(ori_status s, const std::string& msg) {
   return s;
 }
 
+namespace ori {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ori
+
 #define ORI_CUDA(call)                                                                  \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \
