@@ -3,10 +3,12 @@
 #pragma once
 
 #include "dfloat.cuh"
+#include "dfft.cuh"
 #include "passes.cuh"
 #include "scalars.cuh"
 
 #include <cooperative_groups.h>
+#include <type_traits>
 namespace cg = cooperative_groups;
 
 namespace ori {
@@ -114,6 +116,73 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xfwd(XArgs a) {
   }
 }
 
+// Operator epilogue at cell i (conv value v): see EPI_* in passes.cuh.
+// accT collects p^T q in the pass arithmetic, acc the FP64 sums.
+template <class T>
+__device__ __forceinline__ void x_epilogue(const XArgs& a, long long i, cpx<T> v, cpx<T>& accT, double2& acc) {
+    switch (a.mode) {
+      case EPI_PLUS: {
+        const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+        reinterpret_cast<cpx<T>*>(a.out)[i] = xi + v;
+      } break;
+      case EPI_PLUS_S: {
+        const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+        const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+        reinterpret_cast<cpx<T>*>(a.out)[i] = xi + cmul(s, v);
+      } break;
+      case EPI_PLUS_D: {
+        const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+        const cpx<double> vd = c_to_c64(v);
+        reinterpret_cast<cpx<double>*>(a.out)[i] = xi + vd;
+      } break;
+      case EPI_PLUS_S_D: {
+        const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+        const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+        reinterpret_cast<cpx<double>*>(a.out)[i] = xi + c_to_c64(cmul(s, v));
+      } break;
+      case EPI_COCG: {
+        const cpx<T> p = reinterpret_cast<const cpx<T>*>(a.xin)[i];
+        const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+        const cpx<T> q = p + cmul(s, v);
+        reinterpret_cast<cpx<T>*>(a.out)[i] = q;
+        accT = accT + cmul(p, q);                 // p^T q, no conjugate
+      } break;
+      case EPI_RESID: {   // complex128 vectors whatever T is
+        const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+        const cpx<double> b = reinterpret_cast<const cpx<double>*>(a.bvec)[i];
+        const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);
+        const cpx<double> rr = b - (w + cmul(s, c_to_c64(v)));
+        reinterpret_cast<cpx<double>*>(a.out)[i] = rr;
+        acc.x += rr.x * rr.x + rr.y * rr.y;
+      } break;
+      case EPI_RUPDATE: {  // r -= c (d + s v): residual update with this precision's operator
+        const cpx<double> dv = c_to_c64(reinterpret_cast<const cpx<T>*>(a.xin)[i]);
+        const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
+        const cpx<double> bd = c_to_c64(cmul(s, v));
+        cpx<double>* rp = reinterpret_cast<cpx<double>*>(const_cast<void*>(a.bvec)) + i;
+        cpx<double> rr = *rp;
+        rr.x -= a.coef * (dv.x + bd.x);
+        rr.y -= a.coef * (dv.y + bd.y);
+        *rp = rr;
+        acc.x += rr.x * rr.x + rr.y * rr.y;
+      } break;
+      default: {  // EPI_RECOVER: u = w / s where s != 0, else b - v (complex128)
+        const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
+        const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);
+        const cpx<double> vd = c_to_c64(v);
+        cpx<double> u;
+        if (s.x != 0.0 || s.y != 0.0) {
+          const double den = s.x * s.x + s.y * s.y;
+          u = {(w.x * s.x + w.y * s.y) / den, (w.y * s.x - w.x * s.y) / den};
+        } else {
+          const cpx<double> b = reinterpret_cast<const cpx<double>*>(a.bvec)[i];
+          u = b - vd;
+        }
+        reinterpret_cast<cpx<double>*>(a.out)[i] = u;
+      } break;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // X inverse pass + operator epilogue: T1[line][0..L) -> y[line][0..n)
 // ---------------------------------------------------------------------------
@@ -163,71 +232,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc
 #pragma unroll
     for (int jb = 0; jb < L1 / 2; ++jb) {
       const int x = ja + L2 * jb;
-      if (x < a.n) {
-        const long long i = line * a.n + x;
-        const cpx<T> v = r[jb];
-        switch (a.mode) {
-          case EPI_PLUS: {
-            const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
-            reinterpret_cast<cpx<T>*>(a.out)[i] = xi + v;
-          } break;
-          case EPI_PLUS_S: {
-            const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
-            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            reinterpret_cast<cpx<T>*>(a.out)[i] = xi + cmul(s, v);
-          } break;
-          case EPI_PLUS_D: {
-            const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
-            const cpx<double> vd = c_to_c64(v);
-            reinterpret_cast<cpx<double>*>(a.out)[i] = xi + vd;
-          } break;
-          case EPI_PLUS_S_D: {
-            const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
-            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            reinterpret_cast<cpx<double>*>(a.out)[i] = xi + c_to_c64(cmul(s, v));
-          } break;
-          case EPI_COCG: {
-            const cpx<T> p = reinterpret_cast<const cpx<T>*>(a.xin)[i];
-            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            const cpx<T> q = p + cmul(s, v);
-            reinterpret_cast<cpx<T>*>(a.out)[i] = q;
-            accT = accT + cmul(p, q);                 // p^T q, no conjugate
-          } break;
-          case EPI_RESID: {   // complex128 vectors whatever T is
-            const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
-            const cpx<double> b = reinterpret_cast<const cpx<double>*>(a.bvec)[i];
-            const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);
-            const cpx<double> rr = b - (w + cmul(s, c_to_c64(v)));
-            reinterpret_cast<cpx<double>*>(a.out)[i] = rr;
-            acc.x += rr.x * rr.x + rr.y * rr.y;
-          } break;
-          case EPI_RUPDATE: {  // r -= c (d + s v): residual update with this precision's operator
-            const cpx<double> dv = c_to_c64(reinterpret_cast<const cpx<T>*>(a.xin)[i]);
-            const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-            const cpx<double> bd = c_to_c64(cmul(s, v));
-            cpx<double>* rp = reinterpret_cast<cpx<double>*>(const_cast<void*>(a.bvec)) + i;
-            cpx<double> rr = *rp;
-            rr.x -= a.coef * (dv.x + bd.x);
-            rr.y -= a.coef * (dv.y + bd.y);
-            *rp = rr;
-            acc.x += rr.x * rr.x + rr.y * rr.y;
-          } break;
-          default: {  // EPI_RECOVER: u = w / s where s != 0, else b - v (complex128)
-            const cpx<double> w = reinterpret_cast<const cpx<double>*>(a.xin)[i];
-            const cpx<double> s = ldgc(reinterpret_cast<const cpx<double>*>(a.scale) + i);
-            const cpx<double> vd = c_to_c64(v);
-            cpx<double> u;
-            if (s.x != 0.0 || s.y != 0.0) {
-              const double den = s.x * s.x + s.y * s.y;
-              u = {(w.x * s.x + w.y * s.y) / den, (w.y * s.x - w.x * s.y) / den};
-            } else {
-              const cpx<double> b = reinterpret_cast<const cpx<double>*>(a.bvec)[i];
-              u = b - vd;
-            }
-            reinterpret_cast<cpx<double>*>(a.out)[i] = u;
-          } break;
-        }
-      }
+      if (x < a.n) x_epilogue<T>(a, line * a.n + x, r[jb], accT, acc);
     }
     const cpx<double> accD = c_to_c64(accT);
     acc.x += accD.x;
@@ -485,6 +490,167 @@ k_zconv_cluster(SArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// X and Y passes for the paired-FP32 residual, shared-memory resident (see
+// dfft.cuh): a tile of C lines (X) or C columns (Y) of L points per CTA.
+// ---------------------------------------------------------------------------
+template <int L, int C, class T>
+struct LSmem {
+  static constexpr int NT = 256;
+  static constexpr size_t X_ELEMS = size_t(L) * C;
+  static constexpr size_t SMEM_BYTES = (X_ELEMS + size_t(L)) * sizeof(cpx<T>);
+};
+
+template <class T, int L, int C, int SMODE>
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a) {
+  using LS = LSmem<L, C, T>;
+  constexpr int NT = LS::NT, S8 = L / 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* TW = X + LS::X_ELEMS;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < L; i += NT) TW[i] = twg[i];
+  const int outer = blockIdx.x / a.col_blocks;
+  const int cb = blockIdx.x - outer * a.col_blocks;
+  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + outer * a.in_outer + (long long)cb * C;
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + outer * a.out_outer + (long long)cb * C;
+  const int colmax = a.ncols - cb * C;
+  if (SMODE == SMODE_FWD) {
+    __syncthreads();
+    for (int g = tid; g < C * S8; g += NT) {
+      const int c = g % C, j = g / C;
+      cpx<T> v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        v[t] = czero<T>();
+        if (t < 4 && c < colmax && j + t * S8 < a.n_in) v[t] = in[(long long)(j + t * S8) * a.in_pt + c];
+      }
+      dft<8, -1, true>(v);
+#pragma unroll
+      for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
+#pragma unroll
+      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
+    }
+    __syncthreads();
+    dif_rest<L, C>(X, TW, tid, NT);
+    for (int e = tid; e < C * L; e += NT) {
+      const int c = e % C, p = e / C;
+      const int k = digit_rev<L>(p);
+      if (c < colmax && k < a.n_out) out[(long long)k * a.out_pt + c] = X[sidx<C>(p, c)];
+    }
+  } else {
+    for (int e = tid; e < C * L; e += NT) {
+      const int c = e % C, p = e / C;
+      const int k = digit_rev<L>(p);
+      X[sidx<C>(p, c)] = c < colmax ? in[(long long)k * a.in_pt + c] : czero<T>();
+    }
+    __syncthreads();
+    dit_head<L, C>(X, TW, tid, NT);
+    for (int g = tid; g < C * S8; g += NT) {
+      const int c = g % C, j = g / C;
+      cpx<T> v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
+#pragma unroll
+      for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
+      dft<8, +1, false>(v);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int z = j + t * S8;
+        if (c < colmax && z < a.n_out) out[(long long)z * a.out_pt + c] = v[t];
+      }
+    }
+  }
+}
+
+template <class T, int L, int C>
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a) {
+  using LS = LSmem<L, C, T>;
+  constexpr int NT = LS::NT, S8 = L / 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* TW = X + LS::X_ELEMS;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < L; i += NT) TW[i] = twg[i];
+  __syncthreads();
+  // first stage: consecutive threads take consecutive points of one line
+  for (int g = tid; g < C * S8; g += NT) {
+    const int j = g % S8, c = g / S8;
+    const long long line = (long long)blockIdx.x * C + c;
+    cpx<T> v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      v[t] = czero<T>();
+      if (t < 4 && line < a.nlines && j + t * S8 < a.n_in) v[t] = x_prologue<T>(a, line, j + t * S8, L);
+    }
+    dft<8, -1, true>(v);
+#pragma unroll
+    for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
+#pragma unroll
+    for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
+  }
+  __syncthreads();
+  dif_rest<L, C>(X, TW, tid, NT);
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.fft_out);
+  for (int e = tid; e < C * L; e += NT) {
+    const int k = e % L, c = e / L;
+    const long long line = (long long)blockIdx.x * C + c;
+    if (line < a.nlines) out[line * a.line_len_out + k] = X[sidx<C>(inv_digit_rev<L>(k), c)];
+  }
+}
+
+template <class T, int L, int C>
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xinv_smem(XArgs a, Scalars* sc, int fin) {
+  using LS = LSmem<L, C, T>;
+  constexpr int NT = LS::NT, S8 = L / 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* TW = X + LS::X_ELEMS;
+  __shared__ double2 red[32];
+  __shared__ int s_last;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < L; i += NT) TW[i] = twg[i];
+  for (int e = tid; e < C * L; e += NT) {
+    const int k = e % L, c = e / L;
+    const long long line = (long long)blockIdx.x * C + c;
+    X[sidx<C>(inv_digit_rev<L>(k), c)] = line < a.nlines ? in[line * a.line_len_in + k] : czero<T>();
+  }
+  __syncthreads();
+  dit_head<L, C>(X, TW, tid, NT);
+  double2 acc = make_double2(0.0, 0.0);
+  cpx<T> accT = czero<T>();
+  for (int g = tid; g < C * S8; g += NT) {
+    const int j = g % S8, c = g / S8;
+    const long long line = (long long)blockIdx.x * C + c;
+    cpx<T> v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
+    dft<8, +1, false>(v);
+    if (line < a.nlines) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int x = j + t * S8;
+        if (x < a.n) x_epilogue<T>(a, line * a.n + x, v[t], accT, acc);
+      }
+    }
+  }
+  const cpx<double> accD = c_to_c64(accT);
+  acc.x += accD.x;
+  acc.y += accD.y;
+  if (fin == FIN_NONE) return;
+  block_partial(acc, red, a.partials);
+  if (last_block_arrives(sc, s_last)) finalize(sc, a.partials, gridDim.x, fin, red);
+}
+
+// ---------------------------------------------------------------------------
 // Launchers (dispatch on the padded length)
 // ---------------------------------------------------------------------------
 template <class T> constexpr int cols_strided() { return sizeof(T) == 4 ? 8 : 4; }
@@ -495,6 +661,14 @@ template <class T, int L> constexpr int lines_contig() {
 
 template <class T, int L, bool HALF>
 cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
+  if constexpr (std::is_same<T, dfl>::value && HALF && L >= 64) {
+    constexpr int CS = 4;
+    using LS = LSmem<L, CS, T>;
+    auto kfs = k_xfwd_smem<T, L, CS>;
+    if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
+    kfs<<<unsigned((a.nlines + CS - 1) / CS), LS::NT, LS::SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+  }
   constexpr int C = lines_contig<T, L>();
   using TL = Tile<L, C, T>;
   auto kfn = k_xfwd<T, L, C, HALF>;
@@ -506,6 +680,16 @@ cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
 
 template <class T, int L>
 cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
+  if constexpr (std::is_same<T, dfl>::value && L >= 64) {
+    constexpr int CS = 4;
+    using LS = LSmem<L, CS, T>;
+    auto kfs = k_xinv_smem<T, L, CS>;
+    const unsigned grid = unsigned((a.nlines + CS - 1) / CS);
+    if (nblocks) *nblocks = grid;
+    if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
+    kfs<<<grid, LS::NT, LS::SMEM_BYTES, s>>>(a, sc, fin);
+    return cudaGetLastError();
+  }
   constexpr int C = lines_contig<T, L>();
   using TL = Tile<L, C, T>;
   auto kfn = k_xinv<T, L, C>;
@@ -518,6 +702,15 @@ cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, 
 
 template <class T, int L, int SMODE, bool HALF>
 cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
+  if constexpr (std::is_same<T, dfl>::value && L >= 64 && ((SMODE == SMODE_FWD && HALF) || SMODE == SMODE_INV)) {
+    constexpr int CS = 4;
+    using LS = LSmem<L, CS, T>;
+    auto kfs = k_strided_smem<T, L, CS, SMODE>;
+    if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
+    a.col_blocks = (a.ncols + CS - 1) / CS;
+    kfs<<<unsigned(a.nouter) * unsigned(a.col_blocks), LS::NT, LS::SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+  }
   constexpr int C = cols_strided<T>();
   using TL = Tile<L, C, T>;
   auto kfn = k_strided<T, L, C, SMODE, HALF>;
@@ -572,6 +765,23 @@ __device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, cpx<T>*
   const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + (long long)ky * a.in_outer + (long long)cb * C;
   const int chunks = a.n_in * PER_ROW;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));             // elements per chunk
+  for (int k = threadIdx.x; k < chunks; k += NT) {
+    const int j = k / PER_ROW, cc = (k - j * PER_ROW) * EPC;
+    cp_async16(S + j * C + cc, src + (long long)j * a.in_pt + cc);
+  }
+  cp_async_commit();
+}
+
+// Stage the n_in input rows of a Z tile (C columns) into S, NT threads.
+template <class T, int L, int C, int NT>
+__device__ __forceinline__ void zpipe_prefetch_rows(const SArgs& a, int tile, cpx<T>* S) {
+  constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;
+  constexpr int EPC = 16 / int(sizeof(cpx<T>));
+  const int col_blocks = L / C;
+  const int ky = ky_of_slot(tile / col_blocks, L);
+  const int cb = tile % col_blocks;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + (long long)ky * a.in_outer + (long long)cb * C;
+  const int chunks = a.n_in * PER_ROW;
   for (int k = threadIdx.x; k < chunks; k += NT) {
     const int j = k / PER_ROW, cc = (k - j * PER_ROW) * EPC;
     cp_async16(S + j * C + cc, src + (long long)j * a.in_pt + cc);
@@ -687,6 +897,105 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
   cp_async_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Z convolution for the paired-FP32 residual: persistent CTAs, a tile of C
+// columns (C * 16 B = 128 B rows) held in shared memory and transformed in
+// place by looped radix-8 stages (dfft.cuh); the next tile's input rows
+// stream into a staging buffer with cp.async meanwhile.
+// ---------------------------------------------------------------------------
+template <int L, int C, class T>
+struct ZSmem {
+  static constexpr int NT = 512;
+  static constexpr size_t X_ELEMS = size_t(L) * C;
+  static constexpr size_t S_ELEMS = size_t(L / 2) * C;
+  static constexpr size_t SMEM_BYTES = (X_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>);
+};
+
+template <class T, int L, int C>
+__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a) {
+  using ZS = ZSmem<L, C, T>;
+  constexpr int NT = ZS::NT;
+  constexpr int S8 = L / 8;          // span of the first (and last) radix-8 stage
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* S = X + ZS::X_ELEMS;
+  cpx<T>* TW = S + ZS::S_ELEMS;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
+  const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
+  const int col_blocks = L / C;
+  const int ntiles = L * col_blocks;
+  const int tid = threadIdx.x;
+
+  int tile = blockIdx.x;
+  if (tile < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, tile, S);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int ky = ky_of_slot(tile / col_blocks, L);
+    const int cb = tile % col_blocks;
+    cp_async_wait_all();
+    __syncthreads();
+    // first forward stage (M = L): inputs beyond L/2 are the zero padding
+    for (int g = tid; g < C * S8; g += NT) {
+      const int c = g % C, j = g / C;
+      cpx<T> v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        v[t] = czero<T>();
+        if (t < 4 && j + t * S8 < a.n_in) v[t] = S[(j + t * S8) * C + c];
+      }
+      dft<8, -1, true>(v);
+#pragma unroll
+      for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
+#pragma unroll
+      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
+    }
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, tile + gridDim.x, S);
+    dif_rest<L, C>(X, TW, tid, NT);
+    // spectrum: position p holds frequency kz = digit_rev(p)
+    const int my = mirror_index(ky, L);
+    for (int e = tid; e < C * L; e += NT) {
+      const int c = e % C, p = e / C;
+      const int mz = mirror_index(digit_rev<L>(p), L);
+      const int mx = mirror_index(cb * C + c, L);
+      const int si = sidx<C>(p, c);
+      X[si] = cmul(X[si], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
+    }
+    __syncthreads();
+    dit_head<L, C>(X, TW, tid, NT);
+    // last inverse stage (M = L), keep rows z < n_out
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)ky * a.out_outer + (long long)cb * C;
+    for (int g = tid; g < C * S8; g += NT) {
+      const int c = g % C, j = g / C;
+      cpx<T> v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
+#pragma unroll
+      for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
+      dft<8, +1, false>(v);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int z = j + t * S8;
+        if (z < a.n_out) out[(long long)z * a.out_pt + c] = v[t];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+template <class T, int L>
+cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = 8;
+  using ZS = ZSmem<L, C, T>;
+  auto kfn = k_zconv_smem<T, L, C>;
+  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZS::SMEM_BYTES));
+  const int ntiles = L * (L / C);
+  const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count)));
+  kfn<<<grid, ZS::NT, ZS::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class T, int L>
 cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
   constexpr int C = 128 / int(sizeof(cpx<T>));
@@ -719,11 +1028,13 @@ cudaError_t launch_zconv_cluster_L(SArgs a, cudaStream_t s, bool setup) {
   return cudaGetLastError();
 }
 
-// Z-pass kernel choice: the pipelined persistent kernel for L >= 64 (both
-// precisions); the plain strided kernel for small L.
+// Z-pass kernel choice for L >= 64: the shared-memory radix-8 kernel for
+// paired FP32, the pipelined register kernel for FP32 and FP64; the plain
+// strided kernel for small L.
 template <class T, int L>
 cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
-  if constexpr (L >= 64) return launch_zconv_pipe_L<T, L>(a, s, setup, a.sm_count);
+  if constexpr (L >= 64 && std::is_same<T, dfl>::value) return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
+  else if constexpr (L >= 64) return launch_zconv_pipe_L<T, L>(a, s, setup, a.sm_count);
   else return launch_strided_L<T, L, SMODE_ZCONV, true>(a, s, setup);
 }
 

@@ -96,6 +96,23 @@ def test_df_matvec_sampled_rows_n64():
     assert rel(y, y64) < 1e-12
 
 
+@pytest.mark.parametrize("n", [70, 130, 260])
+def test_df_matvec_matches_fp64_large(n):
+    """Paired-FP32 operator against the native FP64 one at L = 256, 512, 1024."""
+    k = 5.0
+    h, N = inputs.random_h_N(n, 40 + n)
+    x = inputs.random_complex(n ** 3, 50 + n)
+    plan = make_plan(n, k, h, N)
+    xd = to_dev(x)
+    for form in ("A", "B"):
+        y = plan.matvec(xd, form=form, precision="df")
+        y64 = plan.matvec(xd, form=form, precision="fp64")
+        err = float(torch.linalg.vector_norm(y - y64) / torch.linalg.vector_norm(y64))
+        assert err < 1e-12, (form, err)
+    plan.close()
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("n", [4, 9, 16, 24])
 def test_fp32_matvec_vs_direct_sum(n):
     k = 5.0
