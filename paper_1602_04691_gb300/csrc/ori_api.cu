@@ -111,9 +111,10 @@ struct ori_plan_s {
   // accounting (ori_plan_stats) and optional per-kernel event timing
   ori_plan_stats stats{};
   bool capturing = false;
+  int cap_iter = 0;   // iteration being captured (timing attribution)
   unsigned long long cap_launches = 0, graph_f_kernels = 0, graph_d_kernels = 0;
   bool timing = false;
-  struct Pend { int kind, e0, e1; };
+  struct Pend { int kind, e0, e1, iter; };   // iter: iteration index inside a captured block
   cudaEvent_t* tev = nullptr;      // immediate pool
   int tev_n = 0, tev_used = 0;
   Pend* pend = nullptr;
@@ -152,9 +153,9 @@ static int t_rec(ori_plan_s* p, cudaStream_t s) {
 static void t_pair(ori_plan_s* p, int kind, int e0, int e1) {
   if (e0 < 0 || e1 < 0) return;
   if (p->capturing) {
-    if (p->gpend_cur && *p->ngpend_cur < kEvPool) p->gpend_cur[(*p->ngpend_cur)++] = {kind, e0, e1};
+    if (p->gpend_cur && *p->ngpend_cur < kEvPool) p->gpend_cur[(*p->ngpend_cur)++] = {kind, e0, e1, p->cap_iter};
   } else if (p->npend < kEvPool) {
-    p->pend[p->npend++] = {kind, e0, e1};
+    p->pend[p->npend++] = {kind, e0, e1, 0};
   }
 }
 
@@ -172,8 +173,11 @@ static void t_harvest(ori_plan_s* p) {
   p->tev_used = 0;
 }
 
-static void t_harvest_graph(ori_plan_s* p, const ori_plan_s::Pend* g, int ng) {
+// Only the first `real_iters` iterations of a replayed block ran; the rest
+// returned at once (the solver had converged) and are not counted.
+static void t_harvest_graph(ori_plan_s* p, const ori_plan_s::Pend* g, int ng, int real_iters) {
   for (int i = 0; i < ng; ++i) {
+    if (g[i].iter >= real_iters) continue;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->gev[g[i].e0], p->gev[g[i].e1]) == cudaSuccess) {
       p->stats.pass_ms[g[i].kind] += ms;
@@ -737,7 +741,10 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
       ORI_CUDA(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal));
       p->capturing = true;
       ori_status cs = ORI_OK;
-      for (int i = 0; i < check_every && cs == ORI_OK; ++i) cs = cocg_iteration<T>(p, x, r, pp, q, S, false);
+      for (int i = 0; i < check_every && cs == ORI_OK; ++i) {
+        p->cap_iter = i;
+        cs = cocg_iteration<T>(p, x, r, pp, q, S, false);
+      }
       p->capturing = false;
       cudaError_t ee = cudaStreamEndCapture(p->ps, &g);
       if (cs != ORI_OK) { if (g) cudaGraphDestroy(g); return cs; }
@@ -751,20 +758,20 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
     }
     int launched_iters = 1;
     bool graph_pending = false;
+    int iter_before = 0;
     for (;;) {
       ORI_CUDA(cudaMemcpyAsync(&p->h_sc->done, &p->sc->done, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->ps));
       ORI_CUDA(cudaStreamSynchronize(p->ps));
       if (p->timing) {
         t_harvest(p);
-        if (graph_pending) t_harvest_graph(p, gpend, ngpend);
+        if (graph_pending) t_harvest_graph(p, gpend, ngpend, p->h_sc->iter - iter_before);
       }
+      iter_before = p->h_sc->iter;
       graph_pending = false;
       if (p->h_sc->done != DONE_RUNNING || launched_iters >= maxit) break;
       if (use_graph) {
         ORI_CUDA(cudaGraphLaunch(gexec, p->ps));
         p->stats.kernel_launches += gkern;
-        if (f32) p->stats.fp32_matvecs += check_every;
-        else p->stats.fp64_matvecs += check_every;
         graph_pending = true;
       } else {
         for (int i = 0; i < check_every; ++i) ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, false));
@@ -774,6 +781,10 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
   }
   ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (use_graph && p->h_sc->iter > 1) {   // iterations after the first ran inside replayed graphs
+    if (sizeof(T) == 4) p->stats.fp32_matvecs += p->h_sc->iter - 1;
+    else p->stats.fp64_matvecs += p->h_sc->iter - 1;
+  }
   res->iters = p->h_sc->iter;
   res->done = p->h_sc->done;
   res->relres_recur = p->h_sc->rnorm2_0 > 0 ? std::sqrt(p->h_sc->rnorm2 / p->h_sc->rnorm2_0) : 0.0;
