@@ -157,4 +157,18 @@ __device__ __forceinline__ void block_partial(double2 v, double2* red, double2* 
   }
 }
 
+// Like block_partial, but v is already reduced over the warp (valid in lane 0).
+__device__ __forceinline__ void block_partial_lane0(double2 v, double2* red, double2* partials) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = 0; i < nw; ++i) { s.x += red[i].x; s.y += red[i].y; }
+    partials[blockIdx.x] = s;
+  }
+}
+
 }  // namespace ori

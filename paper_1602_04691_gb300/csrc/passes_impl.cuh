@@ -21,7 +21,15 @@ template <class T>
 __device__ __forceinline__ int signed_offset(int j, int L) { return j <= L / 2 ? j : j - L; }
 
 template <class T>
-__device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int j, int L) {
+__device__ __forceinline__ cpx<T> x_beta(const XArgs& a) {
+  if (a.mode != PRO_COCG) return czero<T>();
+  const double2 bd = *reinterpret_cast<const double2*>(a.beta);
+  return c_from_c64<T>(cpx<double>{bd.x, bd.y});
+}
+
+// beta: the COCG coefficient in the pass arithmetic, converted once per thread (x_beta).
+template <class T>
+__device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int j, int L, cpx<T> b) {
   const long long i = line * a.n + j;
   switch (a.mode) {
     case PRO_SCALE: {
@@ -44,8 +52,6 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
       const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
       const cpx<T> r = reinterpret_cast<const cpx<T>*>(a.x)[i];
       cpx<T>* pp = reinterpret_cast<cpx<T>*>(a.p) + i;
-      const double2 bd = *reinterpret_cast<const double2*>(a.beta);
-      const cpx<T> b = c_from_c64<T>(cpx<double>{bd.x, bd.y});
       const cpx<T> p = r + cmul(b, *pp);
       *pp = p;
       return cmul(s, p);
@@ -83,13 +89,14 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xfwd(XArgs a) {
   map_t<LAYOUT_CONTIG, C, L2>(tid, c, j2);
   const long long line = (long long)blockIdx.x * C + c;
   const bool ok = line < a.nlines;
+  const cpx<T> beta = x_beta<T>(a);
   cpx<T> r[L1];
 #pragma unroll
   for (int j1 = 0; j1 < L1; ++j1) {
     r[j1] = czero<T>();
     if (!HALF || j1 < L1 / 2) {
       const int j = j1 * L2 + j2;
-      if (ok && j < a.n_in) r[j1] = x_prologue<T>(a, line, j, L);
+      if (ok && j < a.n_in) r[j1] = x_prologue<T>(a, line, j, L, beta);
     }
   }
   dft<L1, -1, HALF>(r);
@@ -227,19 +234,35 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc
   dft<L1, +1, false>(r);
 
   double2 acc = make_double2(0.0, 0.0);
+  cpx<T> accT = czero<T>();
   if (line < a.nlines) {
-    cpx<T> accT = czero<T>();
 #pragma unroll
     for (int jb = 0; jb < L1 / 2; ++jb) {
       const int x = ja + L2 * jb;
       if (x < a.n) x_epilogue<T>(a, line * a.n + x, r[jb], accT, acc);
     }
-    const cpx<double> accD = c_to_c64(accT);
-    acc.x += accD.x;
-    acc.y += accD.y;
+    if constexpr (sizeof(T) != 4) {
+      const cpx<double> accD = c_to_c64(accT);
+      acc.x += accD.x;
+      acc.y += accD.y;
+    }
   }
   if (fin == FIN_NONE) return;
-  block_partial(acc, red, a.partials);
+  bool done_partial = false;
+  if constexpr (sizeof(T) == 4) {
+    if (a.mode == EPI_COCG) {
+      // FP32 sums (p^T q): reduce across the warp in FP32, widen once per warp
+      float ax = accT.x, ay = accT.y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      }
+      block_partial_lane0(make_double2(double(ax), double(ay)), red, a.partials);
+      done_partial = true;
+    }
+  }
+  if (!done_partial) block_partial(acc, red, a.partials);
   if (last_block_arrives(sc, s_last)) finalize(sc, a.partials, gridDim.x, fin, red);
 }
 
@@ -576,6 +599,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a) {
   const int tid = threadIdx.x;
   for (int i = tid; i < L; i += NT) TW[i] = twg[i];
   __syncthreads();
+  const cpx<T> beta = x_beta<T>(a);
   // first stage: consecutive threads take consecutive points of one line
   for (int g = tid; g < C * S8; g += NT) {
     const int j = g % S8, c = g / S8;
@@ -584,7 +608,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       v[t] = czero<T>();
-      if (t < 4 && line < a.nlines && j + t * S8 < a.n_in) v[t] = x_prologue<T>(a, line, j + t * S8, L);
+      if (t < 4 && line < a.nlines && j + t * S8 < a.n_in) v[t] = x_prologue<T>(a, line, j + t * S8, L, beta);
     }
     dft<8, -1, true>(v);
 #pragma unroll

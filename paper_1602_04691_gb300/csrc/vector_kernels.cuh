@@ -209,8 +209,20 @@ __global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n
   }
 }
 
+// Compensated (Kahan) FP32 accumulator: keeps the sum of many FP32 terms
+// accurate to about FP32 rounding of the total, without FP64 arithmetic.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
 // COCG update: x += alpha p, r -= alpha q; rho' = r^T r and ||r||^2 of the new
-// residual (sums in T over 8 elements per thread, then in FP64).
+// residual.  FP64 vectors: sums over 8 elements per thread in FP64.
 template <class T>
 __global__ void k_cocg_update(cpx<T>* __restrict__ x, const cpx<T>* __restrict__ p,
                               cpx<T>* __restrict__ r, const cpx<T>* __restrict__ q, long long n3,
@@ -246,6 +258,67 @@ __global__ void k_cocg_update(cpx<T>* __restrict__ x, const cpx<T>* __restrict__
     nn += double(ns);
   }
   block_partial2(rho, make_double2(nn, 0.0), red, partials);
+  if (last_block_arrives(sc, s_last)) finalize(sc, partials, gridDim.x, FIN_UPDATE, red);
+}
+
+// FP32 vectors: two complex numbers per 16-byte access, all loads of an
+// unrolled group issued before any arithmetic, Kahan-compensated FP32 sums
+// widened to FP64 once per thread.
+template <>
+__global__ void k_cocg_update<float>(cpx<float>* __restrict__ x, const cpx<float>* __restrict__ p,
+                                     cpx<float>* __restrict__ r, const cpx<float>* __restrict__ q,
+                                     long long n3, Scalars* sc, double2* partials) {
+  __shared__ double2 red[64];
+  __shared__ int s_last;
+  if (sc->done != 0) return;
+  const double2 ad = sc->alpha;
+  const float ar = float(ad.x), ai = float(ad.y);
+  KahanF kr, ki, kn;
+  const long long nv = n3 / 2;                        // float4 = two complex numbers
+  float4* x4 = reinterpret_cast<float4*>(x);
+  float4* r4 = reinterpret_cast<float4*>(r);
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+  const float4* q4 = reinterpret_cast<const float4*>(q);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  constexpr int U = 4;
+  for (long long base = blockIdx.x * (long long)blockDim.x + threadIdx.x; base < nv; base += U * stride) {
+    float4 pv[U], qv[U], xv[U], rv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = base + u * stride;
+      if (i < nv) { pv[u] = __ldcs(p4 + i); qv[u] = __ldcs(q4 + i); xv[u] = x4[i]; rv[u] = r4[i]; }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = base + u * stride;
+      if (i < nv) {
+        float4 X = xv[u], R = rv[u];
+        X.x += ar * pv[u].x - ai * pv[u].y;  X.y += ar * pv[u].y + ai * pv[u].x;
+        X.z += ar * pv[u].z - ai * pv[u].w;  X.w += ar * pv[u].w + ai * pv[u].z;
+        R.x -= ar * qv[u].x - ai * qv[u].y;  R.y -= ar * qv[u].y + ai * qv[u].x;
+        R.z -= ar * qv[u].z - ai * qv[u].w;  R.w -= ar * qv[u].w + ai * qv[u].z;
+        x4[i] = X;
+        r4[i] = R;
+        kr.add(R.x * R.x - R.y * R.y + R.z * R.z - R.w * R.w);
+        ki.add(2.f * (R.x * R.y + R.z * R.w));
+        kn.add(R.x * R.x + R.y * R.y + R.z * R.z + R.w * R.w);
+      }
+    }
+  }
+  if ((n3 & 1) && blockIdx.x == 0 && threadIdx.x == 0) {   // odd length: the last element
+    const long long i = n3 - 1;
+    cpx<float> X = x[i], R = r[i];
+    const cpx<float> P = p[i], Q = q[i];
+    X.x += ar * P.x - ai * P.y;  X.y += ar * P.y + ai * P.x;
+    R.x -= ar * Q.x - ai * Q.y;  R.y -= ar * Q.y + ai * Q.x;
+    x[i] = X;
+    r[i] = R;
+    kr.add(R.x * R.x - R.y * R.y);
+    ki.add(2.f * R.x * R.y);
+    kn.add(R.x * R.x + R.y * R.y);
+  }
+  block_partial2(make_double2(double(kr.s) - double(kr.c), double(ki.s) - double(ki.c)),
+                 make_double2(double(kn.s) - double(kn.c), 0.0), red, partials);
   if (last_block_arrives(sc, s_last)) finalize(sc, partials, gridDim.x, FIN_UPDATE, red);
 }
 
