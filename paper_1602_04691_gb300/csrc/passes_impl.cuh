@@ -75,7 +75,7 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
 // X forward pass (contiguous lines): x[line][0..n) -> T1[line][0..L)
 // ---------------------------------------------------------------------------
 template <class T, int L, int C, bool HALF>
-__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xfwd(XArgs a) {
+__global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xfwd(XArgs a) {
   using TL = Tile<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
   constexpr int PK = TL::PK, PC = TL::PC;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void x_epilogue(const XArgs& a, long long i, cpx<T> v
 // X inverse pass + operator epilogue: T1[line][0..L) -> y[line][0..n)
 // ---------------------------------------------------------------------------
 template <class T, int L, int C>
-__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_xinv(XArgs a, Scalars* sc, int fin) {
+__global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv(XArgs a, Scalars* sc, int fin) {
   using TL = Tile<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
   constexpr int PKI = TL::PKI, PCI = TL::PCI;
