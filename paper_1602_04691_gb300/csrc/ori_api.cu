@@ -283,7 +283,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.in = T1; y.out = T2;
   y.in_outer = (long long)n * L; y.out_outer = (long long)L * L;
   y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = n; y.n_out = L; y.nouter = n;
-  y.twL = tw; y.done = done;
+  y.twL = tw; y.done = done; y.sm_count = p->sm_count;
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + K, e0, e1); e0 = e1;

@@ -724,8 +724,13 @@ cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, 
   return cudaGetLastError();
 }
 
+template <class T, int L>
+cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count);
+
 template <class T, int L, int SMODE, bool HALF>
 cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
+  if constexpr (sizeof(T) == 4 && SMODE == SMODE_FWD && HALF && L >= 64)
+    return launch_yfwd_pipe_L<T, L>(a, s, setup, a.sm_count);
   if constexpr (std::is_same<T, dfl>::value && L >= 64 && ((SMODE == SMODE_FWD && HALF) || SMODE == SMODE_INV)) {
     constexpr int CS = 4;
     using LS = LSmem<L, CS, T>;
@@ -1017,6 +1022,115 @@ cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
   const int ntiles = L * (L / C);
   const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count)));
   kfn<<<grid, ZS::NT, ZS::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Y forward pass, persistent and software-pipelined like the Z pass: each CTA
+// loops over tiles (outer index z, C columns); the next tile's n input rows
+// stream into shared memory with cp.async while the current one is
+// transformed.
+// ---------------------------------------------------------------------------
+template <int L, int C, class T>
+struct YPipe {
+  using TL = Tile<L, C, T>;
+  static constexpr int NT = TL::NT;
+  static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
+  static constexpr size_t S_ELEMS = size_t(L / 2) * C;
+  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>);
+};
+
+template <class T, int L, int C>
+__device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, cpx<T>* S) {
+  constexpr int NT = YPipe<L, C, T>::NT;
+  constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;
+  constexpr int EPC = 16 / int(sizeof(cpx<T>));
+  const int outer = tile / a.col_blocks, cb = tile - outer * a.col_blocks;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + outer * a.in_outer + (long long)cb * C;
+  const int chunks = a.n_in * PER_ROW;
+  for (int k = threadIdx.x; k < chunks; k += NT) {
+    const int j = k / PER_ROW, cc = (k - j * PER_ROW) * EPC;
+    cp_async16(S + j * C + cc, src + (long long)j * a.in_pt + cc);
+  }
+  cp_async_commit();
+}
+
+template <class T, int L, int C>
+__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT)) k_yfwd_pipe(SArgs a) {
+  using TL = Tile<L, C, T>;
+  using YP = YPipe<L, C, T>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
+  constexpr int PK = TL::PK, PC = TL::PC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* S = E + YP::E_ELEMS;
+  cpx<T>* TW = S + YP::S_ELEMS;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
+  const int ntiles = a.nouter * a.col_blocks;
+  const int tid = threadIdx.x;
+  const int c = tid % C, jl = tid / C;
+  int tile = blockIdx.x;
+  if (tile < ntiles) ypipe_prefetch<T, L, C>(a, tile, S);
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int outer = tile / a.col_blocks, cb = tile - outer * a.col_blocks;
+    cp_async_wait_all();
+    __syncthreads();
+    cpx<T> r[L1];
+#pragma unroll
+    for (int j1 = 0; j1 < L1; ++j1) {
+      r[j1] = czero<T>();
+      if (j1 < L1 / 2) {
+        const int j = j1 * L2 + jl;
+        if (j < a.n_in) r[j1] = S[j * C + c];
+      }
+    }
+    __syncthreads();
+    if (tile + (int)gridDim.x < ntiles) ypipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
+    dft<L1, -1, true>(r);
+#pragma unroll
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], TW, (jl * k1) & (L - 1));
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
+    __syncthreads();
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + outer * a.out_outer + (long long)cb * C;
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      const int sidx2 = tid + it * NT;
+      const int c2 = sidx2 % C, k1 = sidx2 / C;
+      cpx<T> b[L2];
+#pragma unroll
+      for (int j = 0; j < L2; ++j) b[j] = E[c2 * PC + k1 * PK + j];
+      dft<L2, -1, false>(b);
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) {
+        const int k = k1 + L1 * k2;
+        if (k < a.n_out) out[(long long)k * a.out_pt + c2] = b[k2];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+template <class T, int L>
+cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = cols_strided<T>();
+  using YP = YPipe<L, C, T>;
+  auto kfn = k_yfwd_pipe<T, L, C>;
+  static int per_sm = 0;
+  if (setup) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(YP::SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, YP::NT, YP::SMEM_BYTES);
+    per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
+    return e;
+  }
+  a.col_blocks = (a.ncols + C - 1) / C;
+  const int ntiles = a.nouter * a.col_blocks;
+  const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm)));
+  kfn<<<grid, YP::NT, YP::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
