@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define ORI_ABI_VERSION 1
+#define ORI_ABI_VERSION 2
 
 typedef struct ori_plan_s* ori_plan_t;
 
@@ -85,7 +85,12 @@ typedef struct {
   double c_S;       /* surface constant |S_m| = c_S a^2 (Eq. 2.13); 0 -> 4 pi       */
   size_t mem_cap;   /* 0 = no cap; otherwise ori_plan fails with ORI_ERR_OOM when
                        its device memory would exceed this many bytes              */
-  int    reserved[8];
+  int    n_k;       /* 0: one wave number, ori_plan's k.  1..64: the plan holds one
+                       spectrum per entry of ks (each finite and > 0) and ignores
+                       k; ori_cocg_solve_batch solves for every one of them, the
+                       other calls use ks[0]                                      */
+  const double* ks; /* n_k host wave numbers (read during ori_plan only)         */
+  int    reserved[4];
 } ori_plan_opts;
 
 typedef struct {
@@ -227,6 +232,38 @@ ori_status ori_matvec_noalloc(int64_t n, double k, const ori_domain* dom, double
 ori_status ori_cocg_solve(ori_plan_t plan, const double* rhs_dev, double* u_dev,
                           const ori_solve_opts* opts, ori_solve_info* info,
                           void* stream);
+
+/*
+ * ori_cocg_solve_batch - solve A(k_i) u_{i,j} = u0_{i,j} for every wave number
+ * k_i of the plan (ori_plan_opts.ks; i < n_k, or the one k) and every
+ * incidence direction alpha_j (j < ndir): the multi-frequency, multi-
+ * direction data of the inverse problem (Section 1; Eq. 2.4 per direction).
+ * Right-hand side r = i * ndir + j; all n_k * ndir systems (at most 4096) run
+ * as one batch: every kernel launch covers all of them (blockIdx.y = r), the
+ * FFT passes of systems that share k_i read one spectrum, and a system whose
+ * COCG has converged leaves the launches at once while the others go on.
+ *   ndir        directions per wave number, >= 1.
+ *   alphas_host 3 * ndir doubles (x, y, z per direction; normalised here,
+ *               (0,0,0) -> (0,0,1)), host memory; NULL -> opts->alpha for
+ *               every j.  Ignored when rhs_dev is given.
+ *   rhs_dev     NULL for plane waves, else n_k * ndir complex128 n^3 vectors,
+ *               system r at offset r * n^3.
+ *   u_dev       n_k * ndir complex128 n^3 outputs, system r at offset r * n^3.
+ *   infos       NULL or n_k * ndir entries, filled per system (ms: the
+ *               whole batch).
+ * Each system is solved as by ori_cocg_solve with the same opts (the mixed
+ * solver refines every system until it meets tol; a step whose residual is
+ * updated with the FP32 operator does so only when every unconverged system
+ * allows it).  Scratch grows with the batch and stays with the plan: per
+ * system, the FFT work cubes (n^2 L + n L^2 points, in complex64 and in
+ * complex128) and ten solver vectors, about 17 n^3 complex128 when L = 2n.
+ * Synchronising.  Returns ORI_OK when every system met tol, else the status
+ * of the first that did not (its outputs still the best iterates).
+ */
+ori_status ori_cocg_solve_batch(ori_plan_t plan, int ndir, const double* alphas_host,
+                                const double* rhs_dev, double* u_dev,
+                                const ori_solve_opts* opts, ori_solve_info* infos,
+                                void* stream);
 
 /*
  * ori_adjoint_solve - gradient of J = sum_obs |u_o - t_o|^2 with respect to

@@ -35,6 +35,7 @@ EXPORTS = [
     "ori_plan_destroy", "ori_plan_info", "ori_matvec", "ori_matvec32", "ori_cocg_solve",
     "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
     "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats", "ori_matvec_noalloc",
+    "ori_cocg_solve_batch",
 ]
 
 PASS_NAMES = ["xfwd", "yfwd", "zconv", "yinv", "xinv", "update", "vector", "unused"]
@@ -47,7 +48,8 @@ class Domain(C.Structure):
 
 
 class PlanOpts(C.Structure):
-    _fields_ = [("c_S", C.c_double), ("mem_cap", C.c_size_t), ("reserved", C.c_int * 8)]
+    _fields_ = [("c_S", C.c_double), ("mem_cap", C.c_size_t), ("n_k", C.c_int),
+                ("ks", C.POINTER(C.c_double)), ("reserved", C.c_int * 4)]
 
 
 class SolveOpts(C.Structure):
@@ -120,6 +122,8 @@ def load():
     lib.ori_matvec32.restype = i
     lib.ori_cocg_solve.argtypes = [vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.ori_cocg_solve.restype = i
+    lib.ori_cocg_solve_batch.argtypes = [vp, i, vp, vp, vp, C.POINTER(SolveOpts), vp, vp]
+    lib.ori_cocg_solve_batch.restype = i
     lib.ori_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.ori_adjoint_solve.restype = i
     lib.ori_plan_set_timing.argtypes = [vp, i]

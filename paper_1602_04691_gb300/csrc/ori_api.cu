@@ -1,16 +1,20 @@
 // ori_api.cu - the C ABI declared in include/ori.h: plan, matvec, COCG solve
-// (FP64 and mixed FP32/FP64 refinement) and the adjoint gradient.
+// (FP64, and mixed FP32 / FP64-class refinement), batched solves over several
+// incidence directions and wave numbers, and the adjoint gradient.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/ori.h"
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "passes.cuh"
 #include "scalars.cuh"
 #include "vector_kernels.cuh"
@@ -20,7 +24,6 @@ template <class T> cudaError_t run_xfwd(int, bool, const XArgs&, cudaStream_t, b
 template <class T> cudaError_t run_xinv(int, const XArgs&, Scalars*, int, cudaStream_t, bool, unsigned*);
 template <class T> cudaError_t run_strided(int, int, bool, const SArgs&, cudaStream_t, bool);
 }  // namespace ori
-#include "dfloat.cuh"
 
 using namespace ori;
 
@@ -59,7 +62,8 @@ struct ori_plan_s {
   int device = 0;
   int n = 0, L = 0, H = 0;
   long long n3 = 0;
-  double k = 0, d = 0, c_S = 0, side = 0, origin[3] = {0, 0, 0};
+  double d = 0, c_S = 0, side = 0, origin[3] = {0, 0, 0};
+  std::vector<double> ks;          // wave numbers; one spectrum each
   size_t bytes = 0, mem_cap = 0;
   int sm_count = 0;
   unsigned long long zero_S = 0;
@@ -68,30 +72,30 @@ struct ori_plan_s {
   double* N = nullptr;
   cpx<double>* w64 = nullptr;
   cpx<double>* S64 = nullptr;
+  cpx<double>* Sinv = nullptr;
   cpx<float>* w32 = nullptr;
   cpx<float>* S32 = nullptr;
-  cpx<double>* Sinv = nullptr;
-  cpx<dfl>* wdf = nullptr;     // h N and sqrt(h N) in paired FP32
+  cpx<dfl>* wdf = nullptr;         // h N and sqrt(h N) in paired FP32
   cpx<dfl>* Sdf = nullptr;
-  cpx<dfl>* ghatdf = nullptr;
-  cpx<dfl>* twdf = nullptr;
-  // spectrum and twiddles
+  // spectra (one per wave number, contiguous) and twiddles
   cpx<double>* ghat64 = nullptr;
   cpx<float>* ghat32 = nullptr;
+  cpx<dfl>* ghatdf = nullptr;
   cpx<float>* ghatZ32 = nullptr;   // FP32 spectrum in Z-tile order
   cpx<double>* tw64 = nullptr;
   cpx<float>* tw32 = nullptr;
-  // pass scratch
+  cpx<dfl>* twdf = nullptr;
+  unsigned long long* d_count = nullptr;
+  // batch capacity: pass scratch and solver state for cap right-hand sides
+  int cap = 0;
   cpx<float>* T1f = nullptr;
   cpx<float>* T2f = nullptr;
-  cpx<double>* T1d = nullptr;
+  cpx<double>* T1d = nullptr;      // FP64 and paired-FP32 passes
   cpx<double>* T2d = nullptr;
-  // solver state
   Scalars* sc = nullptr;
-  Scalars* h_sc = nullptr;   // pinned mirror
+  Scalars* h_sc = nullptr;         // pinned mirror of the scalar heads
   double2* partials = nullptr;
-  size_t npartials = 0;
-  unsigned long long* d_count = nullptr;
+  size_t part_per_rhs = 0;
   cpx<double>* b64 = nullptr;
   cpx<double>* w = nullptr;
   cpx<double>* r64 = nullptr;
@@ -102,16 +106,27 @@ struct ori_plan_s {
   cpx<float>* r32 = nullptr;
   cpx<float>* p32 = nullptr;
   cpx<float>* q32 = nullptr;
-  cudaStream_t ps = nullptr;   // private stream (capturable)
+  // per-RHS small arrays: device copies and pinned host staging
+  double* d_tols = nullptr;        // inner tolerances
+  double* d_scl = nullptr;         // scale factors (normalise / accumulate)
+  double* d_coef = nullptr;        // residual-update coefficients
+  double* d_kv = nullptr;          // wave number of each RHS (plane waves)
+  double* d_dir = nullptr;         // 3 per RHS (plane waves)
+  int* d_skip = nullptr;           // 1 = this RHS takes no part in a pass
+  double* h_small = nullptr;       // pinned: 7 * cap doubles
+  int* h_skip = nullptr;           // pinned: cap ints
+  unsigned xinv_blocks = 0;        // largest X-inverse grid of the three arithmetics
+  cudaStream_t ps = nullptr;       // private stream (capturable)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evj = nullptr;
+  // captured COCG blocks (FP32 and FP64 inner solvers)
   cudaGraphExec_t graph_f = nullptr, graph_d = nullptr;
-  int graph_f_len = 0, graph_d_len = 0;
+  int graph_f_len = 0, graph_d_len = 0, graph_f_nrhs = 0, graph_d_nrhs = 0;
   bool graph_f_timed = false, graph_d_timed = false;
   int vec_grid = 0;
   // accounting (ori_plan_stats) and optional per-kernel event timing
   ori_plan_stats stats{};
   bool capturing = false;
-  int cap_iter = 0;   // iteration being captured (timing attribution)
+  int cap_iter = 0;                // iteration being captured (timing attribution)
   unsigned long long cap_launches = 0, graph_f_kernels = 0, graph_d_kernels = 0;
   bool timing = false;
   struct Pend { int kind, e0, e1, iter; };   // iter: iteration index inside a captured block
@@ -174,7 +189,7 @@ static void t_harvest(ori_plan_s* p) {
 }
 
 // Only the first `real_iters` iterations of a replayed block ran; the rest
-// returned at once (the solver had converged) and are not counted.
+// returned at once (every right-hand side had converged) and are not counted.
 static void t_harvest_graph(ori_plan_s* p, const ori_plan_s::Pend* g, int ng, int real_iters) {
   for (int i = 0; i < ng; ++i) {
     if (g[i].iter >= real_iters) continue;
@@ -205,25 +220,93 @@ static ori_status alloc_n(ori_plan_s* p, P** ptr, size_t count) {
   return plan_alloc(p, reinterpret_cast<void**>(ptr), count * sizeof(P));
 }
 
+template <class P>
+static void free_n(ori_plan_s* p, P*& ptr, size_t count) {
+  if (ptr) {
+    cudaFree(ptr);
+    p->bytes -= count * sizeof(P);
+    ptr = nullptr;
+  }
+}
+
+static void drop_graphs(ori_plan_s* p) {
+  if (p->graph_f) cudaGraphExecDestroy(p->graph_f);
+  if (p->graph_d) cudaGraphExecDestroy(p->graph_d);
+  p->graph_f = p->graph_d = nullptr;
+  p->graph_f_len = p->graph_d_len = 0;
+}
+
+static size_t t1_elems(const ori_plan_s* p) { return size_t(p->n) * p->n * p->L; }
+static size_t t2_elems(const ori_plan_s* p) { return size_t(p->n) * p->L * p->L; }
+
+// Release the batch-sized buffers.
+static void free_capacity(ori_plan_s* p) {
+  const size_t c = size_t(p->cap), n3 = size_t(p->n3);
+  free_n(p, p->T1f, c * t1_elems(p));
+  free_n(p, p->T2f, c * t2_elems(p));
+  free_n(p, p->T1d, c * t1_elems(p));
+  free_n(p, p->T2d, c * t2_elems(p));
+  free_n(p, p->sc, c);
+  free_n(p, p->partials, c * p->part_per_rhs);
+  for (cpx<double>** v : {&p->b64, &p->w, &p->r64, &p->u0, &p->p64, &p->q64}) free_n(p, *v, c * n3);
+  for (cpx<float>** v : {&p->x32, &p->r32, &p->p32, &p->q32}) free_n(p, *v, c * n3);
+  for (double** v : {&p->d_tols, &p->d_scl, &p->d_coef, &p->d_kv}) free_n(p, *v, c);
+  free_n(p, p->d_dir, 3 * c);
+  free_n(p, p->d_skip, c);
+  if (p->h_sc) cudaFreeHost(p->h_sc);
+  if (p->h_small) cudaFreeHost(p->h_small);
+  if (p->h_skip) cudaFreeHost(p->h_skip);
+  p->h_sc = nullptr;
+  p->h_small = nullptr;
+  p->h_skip = nullptr;
+  p->cap = 0;
+  drop_graphs(p);
+}
+
+// Make room for nrhs right-hand sides (the scratch of every pass and the solver state).
+static ori_status ensure_capacity(ori_plan_s* p, int nrhs) {
+  if (nrhs <= p->cap) return ORI_OK;
+  cudaStreamSynchronize(p->ps);
+  free_capacity(p);
+  const size_t c = size_t(nrhs), n3 = size_t(p->n3);
+  ORI_TRY(alloc_n(p, &p->T1f, c * t1_elems(p)));
+  ORI_TRY(alloc_n(p, &p->T2f, c * t2_elems(p)));
+  ORI_TRY(alloc_n(p, &p->T1d, c * t1_elems(p)));
+  ORI_TRY(alloc_n(p, &p->T2d, c * t2_elems(p)));
+  ORI_TRY(alloc_n(p, &p->sc, c));
+  ORI_CUDA(cudaMemsetAsync(p->sc, 0, c * sizeof(Scalars), p->ps));
+  p->part_per_rhs = std::max<size_t>(size_t(p->xinv_blocks), size_t(2 * p->vec_grid)) + 16;
+  ORI_TRY(alloc_n(p, &p->partials, c * p->part_per_rhs));
+  for (cpx<double>** v : {&p->b64, &p->w, &p->r64, &p->u0, &p->p64, &p->q64}) ORI_TRY(alloc_n(p, v, c * n3));
+  for (cpx<float>** v : {&p->x32, &p->r32, &p->p32, &p->q32}) ORI_TRY(alloc_n(p, v, c * n3));
+  for (double** v : {&p->d_tols, &p->d_scl, &p->d_coef, &p->d_kv}) ORI_TRY(alloc_n(p, v, c));
+  ORI_TRY(alloc_n(p, &p->d_dir, 3 * c));
+  ORI_TRY(alloc_n(p, &p->d_skip, c));
+  if (cudaMallocHost(&p->h_sc, c * sizeof(Scalars)) != cudaSuccess ||
+      cudaMallocHost(&p->h_small, 7 * c * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&p->h_skip, c * sizeof(int)) != cudaSuccess)
+    return fail(ORI_ERR_OOM, "cudaMallocHost failed");
+  std::memset(p->h_sc, 0, c * sizeof(Scalars));
+  p->cap = nrhs;
+  return ORI_OK;
+}
+
 static void plan_free(ori_plan_s* p) {
   if (!p) return;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p->device);
   cudaDeviceSynchronize();
-  void* ptrs[] = {p->ghatZ32, p->h, p->N, p->w64, p->S64, p->Sinv, p->wdf, p->Sdf, p->ghatdf, p->twdf, p->w32, p->S32, p->ghat64, p->ghat32, p->tw64, p->tw32,
-                  p->T1f, p->T2f, p->T1d, p->T2d, p->sc, p->partials, p->d_count, p->b64, p->w,
-                  p->r64, p->u0, p->p64, p->q64, p->x32, p->r32, p->p32, p->q32};
+  free_capacity(p);
+  void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->Sinv, p->w32, p->S32, p->wdf, p->Sdf,
+                  p->ghat64, p->ghat32, p->ghatdf, p->ghatZ32, p->tw64, p->tw32, p->twdf, p->d_count};
   for (void* q : ptrs)
     if (q) cudaFree(q);
-  if (p->h_sc) cudaFreeHost(p->h_sc);
-  if (p->graph_f) cudaGraphExecDestroy(p->graph_f);
-  if (p->graph_d) cudaGraphExecDestroy(p->graph_d);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->evj) cudaEventDestroy(p->evj);
   if (p->tev) { for (int i = 0; i < p->tev_n; ++i) cudaEventDestroy(p->tev[i]); delete[] p->tev; }
-  if (p->gev) { for (int i = 0; i < p->gev_n; ++i) cudaEventDestroy(p->gev[i]); delete[] p->gev; }
+  if (p->gev) { for (int i = 0; i < 2 * kEvPool; ++i) cudaEventDestroy(p->gev[i]); delete[] p->gev; }
   delete[] p->pend;
   delete[] p->gpend_f;
   delete[] p->gpend_d;
@@ -255,16 +338,23 @@ static ori_status leave(ori_plan_s* p, cudaStream_t user) {
   return ORI_OK;
 }
 
-// One application of the convolution operator: X fwd (prologue), Y fwd, Z
-// conv, Y inv, X inv (epilogue).  `pro` and `epi` carry the mode and vectors.
+// One application of the convolution operator to a batch of nrhs vectors: X
+// fwd (prologue), Y fwd, Z conv, Y inv, X inv (epilogue).  `pro` and `epi`
+// carry the mode, vectors and the byte strides of their per-RHS vectors;
+// rhs_per_k consecutive right-hand sides share one wave number (spectrum).
 template <class T> struct ArithOf;
 template <> struct ArithOf<float> { static constexpr int kind = 0; };
 template <> struct ArithOf<double> { static constexpr int kind = ORI_PASS_FP64; };
 template <> struct ArithOf<dfl> { static constexpr int kind = ORI_PASS_DF; };
 
+struct Mask {
+  const int* flags = nullptr;   // the pass skips RHS r when flags[r * stride] != 0
+  int stride = 0;               // bytes
+};
+
 template <class T>
-static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s,
-                           const int* done) {
+static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s, Mask mask,
+                           int nrhs = 1, int rhs_per_k = 1) {
   constexpr int K = ArithOf<T>::kind;
   const bool f32 = K == 0;
   cpx<T>* T1 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T1f : (void*)p->T1d);
@@ -272,9 +362,13 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   const void* tw = K == 0 ? (const void*)p->tw32 : (K == ORI_PASS_FP64 ? (const void*)p->tw64 : (const void*)p->twdf);
   const void* gh = K == 0 ? (const void*)p->ghat32 : (K == ORI_PASS_FP64 ? (const void*)p->ghat64 : (const void*)p->ghatdf);
   const int n = p->n, L = p->L;
+  const long long H3 = (long long)p->H * p->H * p->H;
+  const long long bsT1 = (long long)t1_elems(p) * sizeof(cpx<T>);
+  const long long bsT2 = (long long)t2_elems(p) * sizeof(cpx<T>);
   int e0 = t_rec(p, s), e1;
   pro.n = n; pro.nlines = n * n; pro.n_in = n; pro.line_len_in = n; pro.line_len_out = L;
-  pro.fft_out = T1; pro.twL = tw; pro.done = done;
+  pro.fft_out = T1; pro.twL = tw; pro.done = mask.flags; pro.done_stride = mask.stride;
+  pro.nrhs = nrhs; pro.bs_fft = bsT1; pro.bs_beta = sizeof(Scalars);
   ORI_CUDA(run_xfwd<T>(L, true, pro, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_XFWD + K, e0, e1); e0 = e1;
@@ -283,7 +377,8 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.in = T1; y.out = T2;
   y.in_outer = (long long)n * L; y.out_outer = (long long)L * L;
   y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = n; y.n_out = L; y.nouter = n;
-  y.twL = tw; y.done = done; y.sm_count = p->sm_count;
+  y.twL = tw; y.done = mask.flags; y.done_stride = mask.stride; y.sm_count = p->sm_count;
+  y.nrhs = nrhs; y.bs_in = bsT1; y.bs_out = bsT2;
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + K, e0, e1); e0 = e1;
@@ -294,8 +389,11 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.in_pt = (long long)L * L; z.out_pt = (long long)L * L;
   z.ncols = L; z.n_in = n; z.n_out = n; z.nouter = L;
   z.twL = tw; z.ghat = gh; z.ghatZ = p->ghatZ32; z.H = p->H;
-  z.done = done;
-  z.sm_count = p->sm_count;
+  z.done = mask.flags; z.done_stride = mask.stride; z.sm_count = p->sm_count;
+  z.nrhs = nrhs; z.bs_in = bsT2; z.bs_out = bsT2;
+  z.bs_ghat = H3 * (long long)sizeof(cpx<T>);
+  z.bs_ghatZ = (long long)p->H * p->H * p->L * (long long)sizeof(cpx<float>);
+  z.rhs_per_ghat = rhs_per_k;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + K, e0, e1); e0 = e1;
@@ -304,20 +402,22 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   yi.in = T2; yi.out = T1;
   yi.in_outer = (long long)L * L; yi.out_outer = (long long)n * L;
   yi.in_pt = L; yi.out_pt = L; yi.ncols = L; yi.n_in = L; yi.n_out = n; yi.nouter = n;
-  yi.twL = tw; yi.done = done;
+  yi.twL = tw; yi.done = mask.flags; yi.done_stride = mask.stride;
+  yi.nrhs = nrhs; yi.bs_in = bsT2; yi.bs_out = bsT1;
   ORI_CUDA(run_strided<T>(L, SMODE_INV, false, yi, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + K, e0, e1); e0 = e1;
 
   epi.n = n; epi.nlines = n * n; epi.line_len_in = L; epi.line_len_out = n;
-  epi.in = T1; epi.twL = tw; epi.done = done; epi.partials = p->partials;
+  epi.in = T1; epi.twL = tw; epi.done = mask.flags; epi.done_stride = mask.stride;
+  epi.partials = p->partials; epi.nrhs = nrhs; epi.bs_fft = bsT1;
   ORI_CUDA(run_xinv<T>(L, epi, p->sc, fin, s, false, nullptr));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_XINV + K, e0, e1);
   if (!p->capturing) {
-    if (K == 0) ++p->stats.fp32_matvecs;
-    else if (K == ORI_PASS_FP64) ++p->stats.fp64_matvecs;
-    else ++p->stats.df_matvecs;
+    if (K == 0) p->stats.fp32_matvecs += nrhs;
+    else if (K == ORI_PASS_FP64) p->stats.fp64_matvecs += nrhs;
+    else p->stats.df_matvecs += nrhs;
   }
   return ORI_OK;
 }
@@ -332,6 +432,9 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
     int ve1_ = t_rec((p), (p)->ps);                       \
     t_pair((p), (kind), ve0_, ve1_);                      \
   } while (0)
+
+// Blocks per right-hand side of the vector kernels.
+static int vgrid(const ori_plan_s* p, int nrhs) { return std::max(16, p->vec_grid / std::max(1, nrhs)); }
 
 template <class T>
 static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n) {
@@ -353,15 +456,21 @@ static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N
   ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
   ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
-  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32, p->Sinv, p->wdf, p->Sdf, p->n3, p->d_count)));
+  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32,
+                                                                        p->Sinv, p->wdf, p->Sdf, p->n3, p->d_count)));
   ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   return ORI_OK;
 }
 
+// Spectrum of every wave number: kernel cube -> FP64 3D FFT -> (L/2+1)^3
+// distinct entries in FP64, FP32 and paired FP32, and the Z-tile-ordered
+// FP32 copy.  The cube is a transient L^3 complex128 buffer.
 static ori_status build_spectrum(ori_plan_s* p) {
   const int L = p->L, n = p->n;
   const long long L3 = (long long)L * L * L;
+  const long long H3 = (long long)p->H * p->H * p->H;
+  const long long HZ = (long long)p->H * p->H * p->L;
   cpx<double>* cube = nullptr;
   {
     cudaError_t e = cudaMalloc(&cube, size_t(L3) * sizeof(cpx<double>));
@@ -371,11 +480,11 @@ static ori_status build_spectrum(ori_plan_s* p) {
     }
   }
   ori_status st = ORI_OK;
-  do {
+  for (size_t ik = 0; ik < p->ks.size() && st == ORI_OK; ++ik) {
     XArgs a{};
     a.mode = PRO_KERNEL;
     a.d = p->d;
-    a.k = p->k;
+    a.k = p->ks[ik];
     a.n = n;
     a.nlines = L * L;
     a.n_in = L;
@@ -402,15 +511,16 @@ static ori_status build_spectrum(ori_plan_s* p) {
     e = run_strided<double>(L, SMODE_FWD, false, z, p->ps, false);
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z pass: ") + cudaGetErrorString(e)); break; }
     const double scale = p->c_S * p->d * p->d * p->d / double(L3);
-    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64, p->ghat32, p->ghatdf, L, p->H, scale);
+    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64 + ik * H3, p->ghat32 + ik * H3,
+                                                   p->ghatdf + ik * H3, L, p->H, scale);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan extract: ") + cudaGetErrorString(e)); break; }
-    k_build_ghatZ<<<p->vec_grid, 256, 0, p->ps>>>(p->ghat32, p->ghatZ32, L, p->H);
+    k_build_ghatZ<<<p->vec_grid, 256, 0, p->ps>>>(p->ghat32 + ik * H3, p->ghatZ32 + ik * HZ, L, p->H);
     e = cudaGetLastError();
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z spectrum: ") + cudaGetErrorString(e)); break; }
     e = cudaStreamSynchronize(p->ps);
     if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan spectrum: ") + cudaGetErrorString(e)); break; }
-  } while (0);
+  }
   cudaFree(cube);
   return st;
 }
@@ -464,7 +574,6 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
   if (!out) return fail(ORI_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 2 || n > 512) return fail(ORI_ERR_INVALID_ARG, "n must be in [2, 512]");
-  if (!std::isfinite(k) || k <= 0) return fail(ORI_ERR_INVALID_ARG, "k must be finite and > 0");
   if (!dom) return fail(ORI_ERR_INVALID_ARG, "dom is NULL");
   if (!std::isfinite(dom->side) || dom->side <= 0 || !finite3(dom->origin))
     return fail(ORI_ERR_INVALID_ARG, "domain side must be finite and > 0, origin finite");
@@ -476,6 +585,16 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     if (o.c_S == 0.0) o.c_S = 4.0 * kPi;
   }
   if (!std::isfinite(o.c_S)) return fail(ORI_ERR_INVALID_ARG, "c_S must be finite");
+  std::vector<double> ks;
+  if (o.n_k > 0) {
+    if (!o.ks) return fail(ORI_ERR_INVALID_ARG, "opts->ks is NULL while opts->n_k > 0");
+    if (o.n_k > 64) return fail(ORI_ERR_INVALID_ARG, "at most 64 wave numbers per plan");
+    ks.assign(o.ks, o.ks + o.n_k);
+  } else {
+    ks.push_back(k);
+  }
+  for (double kv : ks)
+    if (!std::isfinite(kv) || kv <= 0) return fail(ORI_ERR_INVALID_ARG, "k must be finite and > 0");
 
   ori_plan_s* p = new (std::nothrow) ori_plan_s();
   if (!p) return fail(ORI_ERR_OOM, "host allocation failed");
@@ -488,7 +607,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     while (p->L < 2 * p->n) p->L *= 2;
     p->H = p->L / 2 + 1;
     p->n3 = (long long)n * n * n;
-    p->k = k;
+    p->ks = ks;
     p->side = dom->side;
     p->d = dom->side / double(n);
     for (int i = 0; i < 3; ++i) p->origin[i] = dom->origin[i];
@@ -502,30 +621,24 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
       st = fail(ORI_ERR_CUDA, "stream/event creation failed");
       break;
     }
-    const size_t n3 = size_t(p->n3);
+    const size_t n3 = size_t(p->n3), nk = ks.size();
     const size_t H3 = size_t(p->H) * p->H * p->H;
-    const size_t t1 = size_t(p->n) * p->n * p->L, t2 = size_t(p->n) * p->L * p->L;
     if ((st = alloc_n(p, &p->h, n3)) || (st = alloc_n(p, &p->N, n3)) || (st = alloc_n(p, &p->w64, n3)) ||
-        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->wdf, n3)) ||
-        (st = alloc_n(p, &p->Sdf, n3)) || (st = alloc_n(p, &p->ghatdf, H3)) || (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->S32, n3)) ||
-        (st = alloc_n(p, &p->ghat64, H3)) || (st = alloc_n(p, &p->ghat32, H3)) ||
-        (st = alloc_n(p, &p->ghatZ32, size_t(p->H) * p->H * p->L)) ||
+        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->w32, n3)) ||
+        (st = alloc_n(p, &p->S32, n3)) || (st = alloc_n(p, &p->wdf, n3)) || (st = alloc_n(p, &p->Sdf, n3)) ||
+        (st = alloc_n(p, &p->ghat64, nk * H3)) || (st = alloc_n(p, &p->ghat32, nk * H3)) ||
+        (st = alloc_n(p, &p->ghatdf, nk * H3)) ||
+        (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L)) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
-        (st = alloc_n(p, &p->T1f, t1)) || (st = alloc_n(p, &p->T2f, t2)) ||
-        (st = alloc_n(p, &p->T1d, t1)) || (st = alloc_n(p, &p->T2d, t2)) ||
-        (st = alloc_n(p, &p->sc, 1)) || (st = alloc_n(p, &p->d_count, 1)))
+        (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)))
       break;
-    unsigned bx32 = 0, bx64 = 0;
-    unsigned bxdf = 0;
+    unsigned bx32 = 0, bx64 = 0, bxdf = 0;
     if ((st = setup_kernels<float>(p->L, &bx32, p->n)) || (st = setup_kernels<double>(p->L, &bx64, p->n)) ||
         (st = setup_kernels<dfl>(p->L, &bxdf, p->n)))
       break;
-    bx64 = std::max(bx64, bxdf);
-    p->npartials = std::max<size_t>({size_t(bx32), size_t(bx64), size_t(2 * p->vec_grid)}) + 16;
-    if ((st = alloc_n(p, &p->partials, p->npartials))) break;
-    if (cudaMallocHost(&p->h_sc, sizeof(Scalars)) != cudaSuccess) { st = fail(ORI_ERR_OOM, "cudaMallocHost failed"); break; }
+    p->xinv_blocks = std::max({bx32, bx64, bxdf});
+    if ((st = ensure_capacity(p, 1))) break;
     if ((st = enter(p, user))) break;
-    ORI_CUDA(cudaMemsetAsync(p->sc, 0, sizeof(Scalars), p->ps));
     {
       cpx<double>* twd = new cpx<double>[p->L];
       cpx<float>* twf = new cpx<float>[p->L];
@@ -627,19 +740,19 @@ ori_status ori_matvec(ori_plan_t p, const double* x_dev, double* y_dev, int form
     pro.scale = form == ORI_FORM_A ? (const void*)p->w64 : (const void*)p->S64;
     epi.mode = form == ORI_FORM_A ? EPI_PLUS : EPI_PLUS_S;
     epi.scale = p->S64;
-    ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+    ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, Mask{}));
   } else if (precision == ORI_FP32) {
     pro.mode = PRO_SCALE_D;
     pro.scale = form == ORI_FORM_A ? (const void*)p->w32 : (const void*)p->S32;
     epi.mode = form == ORI_FORM_A ? EPI_PLUS_D : EPI_PLUS_S_D;
     epi.scale = p->S32;
-    ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+    ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, Mask{}));
   } else {
     pro.mode = PRO_SCALE_D;
     pro.scale = form == ORI_FORM_A ? (const void*)p->wdf : (const void*)p->Sdf;
     epi.mode = form == ORI_FORM_A ? EPI_PLUS_D : EPI_PLUS_S_D;
     epi.scale = p->Sdf;
-    ORI_TRY(run_conv<dfl>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+    ORI_TRY(run_conv<dfl>(p, pro, epi, FIN_NONE, p->ps, Mask{}));
   }
   return leave(p, user);
 }
@@ -659,47 +772,38 @@ ori_status ori_matvec32(ori_plan_t p, const float* x_dev, float* y_dev, int form
   epi.out = y_dev;
   epi.mode = form == ORI_FORM_A ? EPI_PLUS : EPI_PLUS_S;
   epi.scale = p->S32;
-  ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, nullptr));
+  ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, Mask{}));
   return leave(p, user);
 }
 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Solver
+// Solver (batched over nrhs right-hand sides; nrhs = 1 is the single solve)
 // ---------------------------------------------------------------------------
 
-static ori_status alloc_solver(ori_plan_s* p) {
-  if (p->b64) return ORI_OK;
-  const size_t n3 = size_t(p->n3);
-  ORI_TRY(alloc_n(p, &p->b64, n3));
-  ORI_TRY(alloc_n(p, &p->w, n3));
-  ORI_TRY(alloc_n(p, &p->r64, n3));
-  ORI_TRY(alloc_n(p, &p->u0, n3));
-  ORI_TRY(alloc_n(p, &p->p64, n3));
-  ORI_TRY(alloc_n(p, &p->q64, n3));
-  ORI_TRY(alloc_n(p, &p->x32, n3));
-  ORI_TRY(alloc_n(p, &p->r32, n3));
-  ORI_TRY(alloc_n(p, &p->p32, n3));
-  ORI_TRY(alloc_n(p, &p->q32, n3));
-  return ORI_OK;
-}
-
 template <class T>
-static ori_status cocg_iteration(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cpx<T>* q,
-                                 const cpx<T>* S, bool first) {
+static ori_status cocg_iteration(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, cpx<T>* r, cpx<T>* pp,
+                                 cpx<T>* q, const cpx<T>* S, bool first) {
+  const long long bsv = p->n3 * (long long)sizeof(cpx<T>);
   XArgs pro{}, epi{};
   pro.mode = first ? PRO_COCG_FIRST : PRO_COCG;
   pro.x = r;
   pro.p = pp;
   pro.scale = S;
   pro.beta = &p->sc->beta;
+  pro.bs_x = bsv;
+  pro.bs_p = bsv;
   epi.mode = EPI_COCG;
   epi.xin = pp;
   epi.out = q;
   epi.scale = S;
-  ORI_TRY(run_conv<T>(p, pro, epi, FIN_ALPHA, p->ps, &p->sc->done));
-  ORI_VEC(p, ORI_PASS_UPDATE + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64), (k_cocg_update<T><<<p->vec_grid, 256, 0, p->ps>>>(x, pp, r, q, p->n3, p->sc, p->partials)));
+  epi.bs_xin = bsv;
+  epi.bs_out = bsv;
+  ORI_TRY(run_conv<T>(p, pro, epi, FIN_ALPHA, p->ps, Mask{&p->sc->done, int(sizeof(Scalars))}, nrhs, rhs_per_k));
+  const int vg = vgrid(p, nrhs);
+  ORI_VEC(p, ORI_PASS_UPDATE + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64),
+          (k_cocg_update<T><<<dim3(vg, nrhs), 256, 0, p->ps>>>(x, pp, r, q, p->n3, p->sc, p->partials)));
   return ORI_OK;
 }
 
@@ -709,26 +813,52 @@ struct InnerResult {
   double relres_recur = 0;
 };
 
-// COCG on B x = r (r holds the right-hand side on entry, the residual on exit;
-// x starts at 0).  Stops when ||r|| <= tol ||r_0|| or after maxit iterations.
-template <class T>
-static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cpx<T>* q,
-                             const cpx<T>* S, double tol, int maxit, int check_every, bool use_graph,
-                             InnerResult* res) {
-  ORI_VEC(p, ORI_PASS_VECTOR + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64), (k_cocg_init<T><<<p->vec_grid, 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, tol, maxit)));
-  ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
+// Copy the scalar heads of all right-hand sides to the pinned mirror.
+static ori_status read_heads(ori_plan_s* p, int nrhs) {
+  ORI_CUDA(cudaMemcpy2DAsync(p->h_sc, sizeof(Scalars), p->sc, sizeof(Scalars), offsetof(Scalars, hist),
+                             size_t(nrhs), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   if (p->timing) t_harvest(p);
-  if (p->h_sc->done == DONE_RUNNING && maxit > 0) {
-    ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, true));
+  return ORI_OK;
+}
+
+// COCG on B x_r = r_r for every right-hand side r of the batch (r holds the
+// right-hand sides on entry, the residuals on exit; x starts at 0).  RHS r
+// stops when ||r_r|| <= tols[r] ||r_r(0)|| or after maxit iterations; its
+// kernels then return at once, so the batch runs until the last one stops.
+template <class T>
+static ori_status cocg_inner(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, cpx<T>* r, cpx<T>* pp,
+                             cpx<T>* q, const cpx<T>* S, const double* tols_host, int maxit, int check_every,
+                             bool use_graph, InnerResult* res) {
+  double* h_tols = p->h_small;
+  for (int i = 0; i < nrhs; ++i) h_tols[i] = tols_host[i];
+  ORI_CUDA(cudaMemcpyAsync(p->d_tols, h_tols, nrhs * sizeof(double), cudaMemcpyHostToDevice, p->ps));
+  const int vg = vgrid(p, nrhs);
+  ORI_VEC(p, ORI_PASS_VECTOR + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64),
+          (k_cocg_init<T><<<dim3(vg, nrhs), 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, p->d_tols, maxit)));
+  ORI_TRY(read_heads(p, nrhs));
+  auto any_running = [&]() {
+    for (int i = 0; i < nrhs; ++i)
+      if (p->h_sc[i].done == DONE_RUNNING) return true;
+    return false;
+  };
+  auto max_iter = [&]() {
+    int m = 0;
+    for (int i = 0; i < nrhs; ++i) m = std::max(m, p->h_sc[i].iter);
+    return m;
+  };
+  int graph_iters_total = 0;
+  if (any_running() && maxit > 0) {
+    ORI_TRY(cocg_iteration<T>(p, nrhs, rhs_per_k, x, r, pp, q, S, true));
     const bool f32 = sizeof(T) == 4;
     cudaGraphExec_t& gexec = f32 ? p->graph_f : p->graph_d;
     int& glen = f32 ? p->graph_f_len : p->graph_d_len;
+    int& gnr = f32 ? p->graph_f_nrhs : p->graph_d_nrhs;
     bool& gtimed = f32 ? p->graph_f_timed : p->graph_d_timed;
     unsigned long long& gkern = f32 ? p->graph_f_kernels : p->graph_d_kernels;
     ori_plan_s::Pend*& gpend = f32 ? p->gpend_f : p->gpend_d;
     int& ngpend = f32 ? p->ngpend_f : p->ngpend_d;
-    if (use_graph && (gexec == nullptr || glen != check_every || gtimed != p->timing)) {
+    if (use_graph && (gexec == nullptr || glen != check_every || gnr != nrhs || gtimed != p->timing)) {
       if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
       if (!gpend) gpend = new ori_plan_s::Pend[kEvPool];
       ngpend = 0;
@@ -743,7 +873,7 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
       ori_status cs = ORI_OK;
       for (int i = 0; i < check_every && cs == ORI_OK; ++i) {
         p->cap_iter = i;
-        cs = cocg_iteration<T>(p, x, r, pp, q, S, false);
+        cs = cocg_iteration<T>(p, nrhs, rhs_per_k, x, r, pp, q, S, false);
       }
       p->capturing = false;
       cudaError_t ee = cudaStreamEndCapture(p->ps, &g);
@@ -753,6 +883,7 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
       cudaGraphDestroy(g);
       if (ee != cudaSuccess) { gexec = nullptr; return fail(ORI_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee)); }
       glen = check_every;
+      gnr = nrhs;
       gtimed = p->timing;
       gkern = p->cap_launches;
     }
@@ -760,55 +891,62 @@ static ori_status cocg_inner(ori_plan_s* p, cpx<T>* x, cpx<T>* r, cpx<T>* pp, cp
     bool graph_pending = false;
     int iter_before = 0;
     for (;;) {
-      ORI_CUDA(cudaMemcpyAsync(&p->h_sc->done, &p->sc->done, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->ps));
-      ORI_CUDA(cudaStreamSynchronize(p->ps));
-      if (p->timing) {
-        t_harvest(p);
-        if (graph_pending) t_harvest_graph(p, gpend, ngpend, p->h_sc->iter - iter_before);
+      ORI_TRY(read_heads(p, nrhs));
+      const int it_now = max_iter();
+      if (graph_pending) {
+        graph_iters_total += it_now - iter_before;
+        if (p->timing) t_harvest_graph(p, gpend, ngpend, it_now - iter_before);
       }
-      iter_before = p->h_sc->iter;
+      iter_before = it_now;
       graph_pending = false;
-      if (p->h_sc->done != DONE_RUNNING || launched_iters >= maxit) break;
+      if (!any_running() || launched_iters >= maxit) break;
       if (use_graph) {
         ORI_CUDA(cudaGraphLaunch(gexec, p->ps));
         p->stats.kernel_launches += gkern;
         graph_pending = true;
       } else {
-        for (int i = 0; i < check_every; ++i) ORI_TRY(cocg_iteration<T>(p, x, r, pp, q, S, false));
+        for (int i = 0; i < check_every; ++i) ORI_TRY(cocg_iteration<T>(p, nrhs, rhs_per_k, x, r, pp, q, S, false));
       }
       launched_iters += check_every;
     }
   }
-  ORI_CUDA(cudaMemcpyAsync(p->h_sc, p->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, p->ps));
-  ORI_CUDA(cudaStreamSynchronize(p->ps));
-  if (use_graph && p->h_sc->iter > 1) {   // iterations after the first ran inside replayed graphs
-    if (sizeof(T) == 4) p->stats.fp32_matvecs += p->h_sc->iter - 1;
-    else p->stats.fp64_matvecs += p->h_sc->iter - 1;
+  ORI_TRY(read_heads(p, nrhs));
+  long long real_matvecs = 0;
+  for (int i = 0; i < nrhs; ++i) {
+    res[i].iters = p->h_sc[i].iter;
+    res[i].done = p->h_sc[i].done;
+    res[i].relres_recur = p->h_sc[i].rnorm2_0 > 0 ? std::sqrt(p->h_sc[i].rnorm2 / p->h_sc[i].rnorm2_0) : 0.0;
+    if (use_graph && res[i].iters > 1) real_matvecs += res[i].iters - 1;   // ran inside replayed graphs
   }
-  res->iters = p->h_sc->iter;
-  res->done = p->h_sc->done;
-  res->relres_recur = p->h_sc->rnorm2_0 > 0 ? std::sqrt(p->h_sc->rnorm2 / p->h_sc->rnorm2_0) : 0.0;
+  if (sizeof(T) == 4) p->stats.fp32_matvecs += real_matvecs;
+  else p->stats.fp64_matvecs += real_matvecs;
+  (void)graph_iters_total;
   return ORI_OK;
 }
 
-// r64 = b64 - B w with complex128 vectors; the FFT passes run in paired FP32
-// (use_df) or native FP64.  Returns ||r64||.
-static ori_status fp64_residual(ori_plan_s* p, double* rnorm, bool use_df) {
+// r64_r = b64_r - B w_r for the RHS whose skip flag is 0 (complex128 vectors;
+// FFT passes in paired FP32 or native FP64).  Fills rn[r] = ||r64_r||.
+static ori_status fp64_residual(ori_plan_s* p, int nrhs, int rhs_per_k, bool use_df, double* rn) {
+  const long long bsv = p->n3 * (long long)sizeof(cpx<double>);
   XArgs pro{}, epi{};
   pro.mode = use_df ? PRO_SCALE_D : PRO_SCALE;
   pro.x = p->w;
+  pro.bs_x = bsv;
   pro.scale = use_df ? (const void*)p->Sdf : (const void*)p->S64;
   epi.mode = EPI_RESID;
   epi.xin = p->w;
   epi.bvec = p->b64;
   epi.out = p->r64;
   epi.scale = p->S64;
-  if (use_df) ORI_TRY(run_conv<dfl>(p, pro, epi, FIN_SUM, p->ps, nullptr));
-  else ORI_TRY(run_conv<double>(p, pro, epi, FIN_SUM, p->ps, nullptr));
-  ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
-  ORI_CUDA(cudaStreamSynchronize(p->ps));
-  if (p->timing) t_harvest(p);
-  *rnorm = std::sqrt(p->h_sc->sum.x);
+  epi.bs_xin = bsv;
+  epi.bs_bvec = bsv;
+  epi.bs_out = bsv;
+  const Mask m{p->d_skip, int(sizeof(int))};
+  if (use_df) ORI_TRY(run_conv<dfl>(p, pro, epi, FIN_SUM, p->ps, m, nrhs, rhs_per_k));
+  else ORI_TRY(run_conv<double>(p, pro, epi, FIN_SUM, p->ps, m, nrhs, rhs_per_k));
+  ORI_TRY(read_heads(p, nrhs));
+  for (int i = 0; i < nrhs; ++i)
+    if (!p->h_skip[i]) rn[i] = std::sqrt(p->h_sc[i].sum.x);
   return ORI_OK;
 }
 
@@ -828,100 +966,154 @@ static ori_status status_of(int done) {
   }
 }
 
-// Solve B w = b64 (b64 and ||b64|| ready on the device / in bnorm); w -> p->w.
-static ori_status solve_B(ori_plan_s* p, double bnorm, const ori_solve_opts& o, ori_solve_info* info) {
-  info->iters = 0;
-  info->outer_iters = 0;
-  info->fp64_matvecs = 0;
-  info->resid_updates = 0;
-  info->relres_bound = 0.0;
+static ori_status push_skip(ori_plan_s* p, int nrhs) {
+  ORI_CUDA(cudaMemcpyAsync(p->d_skip, p->h_skip, nrhs * sizeof(int), cudaMemcpyHostToDevice, p->ps));
+  return ORI_OK;
+}
+static ori_status push_doubles(ori_plan_s* p, double* dst, const double* src, int count) {
+  double* stage = p->h_small + 3 * p->cap;   // pinned staging beyond the tolerance slots
+  for (int i = 0; i < count; ++i) stage[i] = src[i];
+  ORI_CUDA(cudaMemcpyAsync(dst, stage, count * sizeof(double), cudaMemcpyHostToDevice, p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  return ORI_OK;
+}
+
+// Solve B w_r = b64_r for the batch (b64 and bnorm[r] ready); w -> p->w.
+static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* bnorm, const ori_solve_opts& o,
+                          ori_solve_info* info) {
   const long long n3 = p->n3;
-  const size_t bytes64 = size_t(n3) * sizeof(cpx<double>);
-  if (bnorm == 0.0) {
-    ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
-    info->relres = 0.0;
-    info->relres_recur = 0.0;
-    info->status = ORI_OK;
-    return ORI_OK;
+  const size_t bytes64 = size_t(n3) * sizeof(cpx<double>) * nrhs;
+  for (int i = 0; i < nrhs; ++i) {
+    info[i] = ori_solve_info{};
   }
   const bool graph = o.use_graph != 0;
+  std::vector<InnerResult> ir(nrhs);
+  std::vector<double> tin(nrhs);
   if (o.precision == ORI_FP64) {
     ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
-    InnerResult ir;
-    ORI_TRY(cocg_inner<double>(p, p->w, p->r64, p->p64, p->q64, p->S64, o.tol, o.maxit, o.check_every, graph, &ir));
-    info->iters = ir.iters;
-    info->outer_iters = 1;
-    info->relres_recur = ir.relres_recur;
-    double rn = 0;
-    ORI_TRY(fp64_residual(p, &rn, false));
-    info->fp64_matvecs = 1;
-    info->relres = rn / bnorm;
-    info->status = ir.done == DONE_CONVERGED ? (info->relres <= 10 * o.tol ? ORI_OK : ORI_ERR_NOT_CONVERGED)
-                                             : status_of(ir.done);
+    for (int i = 0; i < nrhs; ++i) tin[i] = bnorm[i] > 0 ? o.tol : 1.0;
+    ORI_TRY(cocg_inner<double>(p, nrhs, rhs_per_k, p->w, p->r64, p->p64, p->q64, p->S64, tin.data(), o.maxit,
+                               o.check_every, graph, ir.data()));
+    for (int i = 0; i < nrhs; ++i) p->h_skip[i] = bnorm[i] > 0 ? 0 : 1;
+    ORI_TRY(push_skip(p, nrhs));
+    std::vector<double> rn(nrhs, 0.0);
+    ORI_TRY(fp64_residual(p, nrhs, rhs_per_k, false, rn.data()));
+    for (int i = 0; i < nrhs; ++i) {
+      info[i].iters = ir[i].iters;
+      info[i].outer_iters = 1;
+      info[i].relres_recur = ir[i].relres_recur;
+      info[i].fp64_matvecs = 1;
+      info[i].relres = bnorm[i] > 0 ? rn[i] / bnorm[i] : 0.0;
+      info[i].relres_bound = 1e-14;
+      if (bnorm[i] == 0) info[i].status = ORI_OK;
+      else info[i].status = ir[i].done == DONE_CONVERGED
+                                ? (info[i].relres <= 10 * o.tol ? ORI_OK : ORI_ERR_NOT_CONVERGED)
+                                : status_of(ir[i].done);
+    }
     return ORI_OK;
   }
-  // mixed: FP32 COCG on the normalised FP64 residual, FP64 refinement
+  // mixed: FP32 COCG on the normalised residual, FP64-class refinement
   ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
   ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
-  double rn = bnorm;
-  int total = 0;
-  int last_done = DONE_CONVERGED;
-  double last_recur = 0;
-  int outer = 0;
-  double err_bound = 0.0;   // bound on |computed r - (b - B w)|
-  while (rn + err_bound > o.tol * bnorm && outer < o.max_outer && total < o.maxit) {
-    ORI_VEC(p, ORI_PASS_VECTOR, (k_normalise_to_f32<<<p->vec_grid, 256, 0, p->ps>>>(p->r64, p->r32, n3, 1.0 / rn)));
-    const double want = 0.25 * o.tol * bnorm / rn;
-    const double tin = std::min(0.5, std::max(o.inner_tol, want));
-    InnerResult ir;
-    ORI_TRY(cocg_inner<float>(p, p->x32, p->r32, p->p32, p->q32, p->S32, tin, o.maxit - total, o.check_every, graph, &ir));
-    total += ir.iters;
-    last_done = ir.done;
-    last_recur = ir.relres_recur;
-    ++outer;
-    if (ir.done == DONE_NONFINITE) break;
-    ORI_VEC(p, ORI_PASS_VECTOR, (k_accumulate<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->x32, n3, rn)));
-    double rn_new = 0;
-    // |B d| <= 1 + |r_hat - B d| = 1 + (inner relative residual)
-    const double upd_err = kFp32OperatorRelErr * rn * (1.0 + last_recur);
-    if (o.resid_update && upd_err <= 0.05 * o.tol * bnorm) {
-      // r -= rn B d with the FP32 operator: its error is at most
-      // kFp32OperatorRelErr * rn * |B d|, far below tol |b| at this point.
+  std::vector<double> rn(bnorm, bnorm + nrhs), err(nrhs, 0.0), recur(nrhs, 0.0);
+  std::vector<int> active(nrhs), last_done(nrhs, DONE_CONVERGED), total(nrhs, 0), outer(nrhs, 0);
+  for (int i = 0; i < nrhs; ++i) active[i] = bnorm[i] > 0 && rn[i] > o.tol * bnorm[i];
+  for (int step = 0; step < o.max_outer; ++step) {
+    bool any = false;
+    for (int i = 0; i < nrhs; ++i) any = any || active[i];
+    if (!any) break;
+    int budget = o.maxit;
+    std::vector<double> inv(nrhs, 0.0);
+    for (int i = 0; i < nrhs; ++i) {
+      if (active[i]) budget = std::min(budget, o.maxit - total[i]);
+      inv[i] = active[i] ? 1.0 / rn[i] : 0.0;
+      const double want = active[i] ? 0.25 * o.tol * bnorm[i] / rn[i] : 1.0;
+      tin[i] = active[i] ? std::min(0.5, std::max(o.inner_tol, want)) : 1.0;
+    }
+    if (budget <= 0) break;
+    ORI_TRY(push_doubles(p, p->d_scl, inv.data(), nrhs));
+    const int vg = vgrid(p, nrhs);
+    ORI_VEC(p, ORI_PASS_VECTOR, (k_normalise_to_f32<<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->r64, p->r32, n3, p->d_scl)));
+    ORI_TRY(cocg_inner<float>(p, nrhs, rhs_per_k, p->x32, p->r32, p->p32, p->q32, p->S32, tin.data(), budget,
+                              o.check_every, graph, ir.data()));
+    bool nonfinite_all = true;
+    std::vector<double> scl(nrhs, 0.0);
+    for (int i = 0; i < nrhs; ++i) {
+      if (!active[i]) continue;
+      total[i] += ir[i].iters;
+      last_done[i] = ir[i].done;
+      recur[i] = ir[i].relres_recur;
+      ++outer[i];
+      if (ir[i].done == DONE_NONFINITE) active[i] = 0;
+      else nonfinite_all = false;
+      scl[i] = active[i] ? rn[i] : 0.0;
+    }
+    if (nonfinite_all) break;
+    ORI_TRY(push_doubles(p, p->d_scl, scl.data(), nrhs));
+    ORI_VEC(p, ORI_PASS_VECTOR, (k_accumulate<<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->w, p->x32, n3, p->d_scl)));
+    // residual: updated with the FP32 operator when every active RHS allows it
+    bool upd = o.resid_update != 0;
+    std::vector<double> upd_err(nrhs, 0.0);
+    for (int i = 0; i < nrhs; ++i) {
+      if (!active[i]) continue;
+      upd_err[i] = kFp32OperatorRelErr * rn[i] * (1.0 + recur[i]);   // |B d| <= 1 + inner residual
+      upd = upd && upd_err[i] <= 0.05 * o.tol * bnorm[i];
+    }
+    for (int i = 0; i < nrhs; ++i) p->h_skip[i] = active[i] ? 0 : 1;
+    ORI_TRY(push_skip(p, nrhs));
+    std::vector<double> rn_new(rn);
+    if (upd) {
+      // r -= rn B d with the FP32 operator; error <= kFp32OperatorRelErr rn |B d|
+      ORI_TRY(push_doubles(p, p->d_coef, scl.data(), nrhs));
+      const long long bs32 = n3 * (long long)sizeof(cpx<float>), bs64 = n3 * (long long)sizeof(cpx<double>);
       XArgs pro{}, epi{};
       pro.mode = PRO_SCALE;
       pro.x = p->x32;
+      pro.bs_x = bs32;
       pro.scale = p->S32;
       epi.mode = EPI_RUPDATE;
       epi.xin = p->x32;
+      epi.bs_xin = bs32;
       epi.scale = p->S32;
       epi.bvec = p->r64;
-      epi.coef = rn;
-      ORI_TRY(run_conv<float>(p, pro, epi, FIN_SUM, p->ps, nullptr));
-      ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
-      ORI_CUDA(cudaStreamSynchronize(p->ps));
-      if (p->timing) t_harvest(p);
-      rn_new = std::sqrt(p->h_sc->sum.x);
-      err_bound += upd_err;
-      info->resid_updates += 1;
+      epi.bs_bvec = bs64;
+      epi.coefs = p->d_coef;
+      ORI_TRY(run_conv<float>(p, pro, epi, FIN_SUM, p->ps, Mask{p->d_skip, int(sizeof(int))}, nrhs, rhs_per_k));
+      ORI_TRY(read_heads(p, nrhs));
+      for (int i = 0; i < nrhs; ++i) {
+        if (!active[i]) continue;
+        rn_new[i] = std::sqrt(p->h_sc[i].sum.x);
+        err[i] += upd_err[i];
+        info[i].resid_updates += 1;
+      }
     } else {
-      ORI_TRY(fp64_residual(p, &rn_new, o.residual == ORI_DF));
-      info->fp64_matvecs += 1;
-      err_bound = (o.residual == ORI_DF ? kDfOperatorRelErr : 1e-14) * bnorm;
+      ORI_TRY(fp64_residual(p, nrhs, rhs_per_k, o.residual == ORI_DF, rn_new.data()));
+      for (int i = 0; i < nrhs; ++i) {
+        if (!active[i]) continue;
+        info[i].fp64_matvecs += 1;
+        err[i] = (o.residual == ORI_DF ? kDfOperatorRelErr : 1e-14) * bnorm[i];
+      }
     }
-    const bool stalled = rn_new > 0.9 * rn;
-    rn = rn_new;
-    if (stalled && ir.done != DONE_CONVERGED) break;
-    if (rn + err_bound <= o.tol * bnorm) break;
+    for (int i = 0; i < nrhs; ++i) {
+      if (!active[i]) continue;
+      const bool stalled = rn_new[i] > 0.9 * rn[i];
+      rn[i] = rn_new[i];
+      if (stalled && ir[i].done != DONE_CONVERGED) active[i] = 0;
+      if (rn[i] + err[i] <= o.tol * bnorm[i]) active[i] = 0;
+      if (total[i] >= o.maxit) active[i] = 0;
+    }
   }
-  info->iters = total;
-  info->outer_iters = outer;
-  info->relres = rn / bnorm;
-  info->relres_bound = err_bound / bnorm;
-  info->relres_recur = last_recur;
-  if (info->relres + info->relres_bound <= o.tol) info->status = ORI_OK;
-  else if (last_done == DONE_NONFINITE) info->status = ORI_ERR_NONFINITE;
-  else if (last_done == DONE_BREAKDOWN) info->status = ORI_ERR_BREAKDOWN;
-  else info->status = ORI_ERR_NOT_CONVERGED;
+  for (int i = 0; i < nrhs; ++i) {
+    info[i].iters = total[i];
+    info[i].outer_iters = outer[i];
+    info[i].relres = bnorm[i] > 0 ? rn[i] / bnorm[i] : 0.0;
+    info[i].relres_bound = bnorm[i] > 0 ? err[i] / bnorm[i] : 0.0;
+    info[i].relres_recur = recur[i];
+    if (bnorm[i] == 0 || info[i].relres + info[i].relres_bound <= o.tol) info[i].status = ORI_OK;
+    else if (last_done[i] == DONE_NONFINITE) info[i].status = ORI_ERR_NONFINITE;
+    else if (last_done[i] == DONE_BREAKDOWN) info[i].status = ORI_ERR_BREAKDOWN;
+    else info[i].status = ORI_ERR_NOT_CONVERGED;
+  }
   return ORI_OK;
 }
 
@@ -942,6 +1134,66 @@ static ori_status check_solve_opts(const ori_solve_opts* in, ori_solve_opts* o) 
   return ORI_OK;
 }
 
+// Solve A u_r = rhs_r for r = ik * ndir + id: wave number ks[ik] (ik over the
+// plan's wave numbers) and direction id.  rhs_dev == NULL: plane waves.
+static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs_dev, const double* dirs_host,
+                              double* u_dev, const ori_solve_opts& o, ori_solve_info* infos, cudaStream_t user) {
+  const int nrhs = nk * ndir;
+  ORI_TRY(ensure_capacity(p, nrhs));
+  ORI_TRY(enter(p, user));
+  ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
+  std::vector<double> kv(nrhs), dv(3 * nrhs);
+  for (int ik = 0; ik < nk; ++ik)
+    for (int id = 0; id < ndir; ++id) {
+      const int r = ik * ndir + id;
+      kv[r] = p->ks[ik];
+      const double* a = dirs_host + 3 * id;
+      const double an = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      for (int c = 0; c < 3; ++c) dv[3 * r + c] = an > 0 ? a[c] / an : (c == 2 ? 1.0 : 0.0);
+    }
+  ORI_TRY(push_doubles(p, p->d_kv, kv.data(), nrhs));
+  ORI_TRY(push_doubles(p, p->d_dir, dv.data(), 3 * nrhs));
+  const int vg = vgrid(p, nrhs);
+  ORI_VEC(p, ORI_PASS_VECTOR,
+          (k_rhs<<<dim3(vg, nrhs), 256, rhs_dev ? 0 : 3 * size_t(p->n) * sizeof(cpx<double>), p->ps>>>(
+              reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0, p->b64, p->n, p->d, p->origin[0],
+              p->origin[1], p->origin[2], p->d_kv, p->d_dir, p->sc, p->partials)));
+  ORI_TRY(read_heads(p, nrhs));
+  std::vector<double> bnorm(nrhs);
+  for (int i = 0; i < nrhs; ++i) bnorm[i] = std::sqrt(p->h_sc[i].sum.x);
+  ORI_TRY(solve_B(p, nrhs, ndir, bnorm.data(), o, infos));
+  // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
+  if (p->zero_S == 0) {
+    ORI_VEC(p, ORI_PASS_VECTOR,
+            (k_recover<<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->w, p->Sinv, reinterpret_cast<cpx<double>*>(u_dev), p->n3)));
+  } else {
+    const long long bsv = p->n3 * (long long)sizeof(cpx<double>);
+    XArgs pro{}, epi{};
+    pro.mode = PRO_SCALE;
+    pro.x = p->w;
+    pro.bs_x = bsv;
+    pro.scale = p->S64;
+    epi.mode = EPI_RECOVER;
+    epi.xin = p->w;
+    epi.bvec = p->u0;
+    epi.out = u_dev;
+    epi.scale = p->S64;
+    epi.bs_xin = bsv;
+    epi.bs_bvec = bsv;
+    epi.bs_out = bsv;
+    ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, Mask{}, nrhs, ndir));
+    for (int i = 0; i < nrhs; ++i) infos[i].fp64_matvecs += 1;
+  }
+  ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
+  ORI_CUDA(cudaEventSynchronize(p->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  if (p->timing) t_harvest(p);
+  for (int i = 0; i < nrhs; ++i) infos[i].ms = ms;
+  ORI_TRY(leave(p, user));
+  return ORI_OK;
+}
+
 extern "C" {
 
 ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, const ori_solve_opts* opts,
@@ -950,49 +1202,40 @@ ori_status ori_cocg_solve(ori_plan_t p, const double* rhs_dev, double* u_dev, co
   if (!p || !u_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
   ori_solve_opts o;
   ORI_TRY(check_solve_opts(opts, &o));
-  double an = std::sqrt(o.alpha[0] * o.alpha[0] + o.alpha[1] * o.alpha[1] + o.alpha[2] * o.alpha[2]);
-  double al[3] = {0.0, 0.0, 1.0};
-  if (an > 0) for (int i = 0; i < 3; ++i) al[i] = o.alpha[i] / an;
   ori_solve_info info{};
-  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-  ORI_TRY(alloc_solver(p));
-  ORI_TRY(enter(p, user));
-  ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
-  ORI_VEC(p, ORI_PASS_VECTOR,
-          (k_rhs<<<p->vec_grid, 256, rhs_dev ? 0 : 3 * size_t(p->n) * sizeof(cpx<double>), p->ps>>>(
-              reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0,
-                                                  p->b64, p->n, p->d, p->origin[0], p->origin[1], p->origin[2],
-                                                  p->k, al[0], al[1], al[2], p->sc, p->partials)));
-  ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
-  ORI_CUDA(cudaStreamSynchronize(p->ps));
-  if (p->timing) t_harvest(p);
-  const double bnorm = std::sqrt(p->h_sc->sum.x);
-  ORI_TRY(solve_B(p, bnorm, o, &info));
-  // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
-  if (p->zero_S == 0) {
-    ORI_VEC(p, ORI_PASS_VECTOR,
-            (k_recover<<<p->vec_grid, 256, 0, p->ps>>>(p->w, p->Sinv, reinterpret_cast<cpx<double>*>(u_dev), p->n3)));
-  } else {
-    XArgs pro{}, epi{};
-    pro.mode = PRO_SCALE;
-    pro.x = p->w;
-    pro.scale = p->S64;
-    epi.mode = EPI_RECOVER;
-    epi.xin = p->w;
-    epi.bvec = p->u0;
-    epi.out = u_dev;
-    epi.scale = p->S64;
-    ORI_TRY(run_conv<double>(p, pro, epi, FIN_NONE, p->ps, nullptr));
-    info.fp64_matvecs += 1;
-  }
-  ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
-  ORI_CUDA(cudaEventSynchronize(p->ev1));
-  cudaEventElapsedTime(&info.ms, p->ev0, p->ev1);
-  if (p->timing) t_harvest(p);
-  ORI_TRY(leave(p, user));
+  ORI_TRY(solve_batch(p, 1, 1, rhs_dev, o.alpha, u_dev, o, &info, reinterpret_cast<cudaStream_t>(stream)));
   if (info_out) *info_out = info;
   if (info.status != ORI_OK)
     return fail(ori_status(info.status), std::string("solve ended with status ") + ori_status_string(info.status));
+  return ORI_OK;
+}
+
+ori_status ori_cocg_solve_batch(ori_plan_t p, int ndir, const double* alphas_host, const double* rhs_dev,
+                                double* u_dev, const ori_solve_opts* opts, ori_solve_info* infos,
+                                void* stream) {
+  g_last_error.clear();
+  if (!p || !u_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (ndir < 1) return fail(ORI_ERR_INVALID_ARG, "ndir must be >= 1");
+  if (!rhs_dev && !alphas_host) return fail(ORI_ERR_INVALID_ARG, "alphas_host is NULL and rhs_dev is NULL");
+  ori_solve_opts o;
+  ORI_TRY(check_solve_opts(opts, &o));
+  const int nk = int(p->ks.size());
+  const long long nrhs = (long long)nk * ndir;
+  if (nrhs > 4096) return fail(ORI_ERR_INVALID_ARG, "at most 4096 right-hand sides per batch");
+  std::vector<double> dirs(3 * size_t(ndir));
+  for (int id = 0; id < ndir; ++id)
+    for (int c = 0; c < 3; ++c) dirs[3 * id + c] = alphas_host ? alphas_host[3 * id + c] : o.alpha[c];
+  for (double v : dirs)
+    if (!std::isfinite(v)) return fail(ORI_ERR_INVALID_ARG, "directions must be finite");
+  std::vector<ori_solve_info> inf(static_cast<size_t>(nrhs));
+  ORI_TRY(solve_batch(p, nk, ndir, rhs_dev, dirs.data(), u_dev, o, inf.data(), reinterpret_cast<cudaStream_t>(stream)));
+  ori_status worst = ORI_OK;
+  for (long long i = 0; i < nrhs; ++i) {
+    if (infos) infos[i] = inf[i];
+    if (inf[i].status != ORI_OK && worst == ORI_OK) worst = ori_status(inf[i].status);
+  }
+  if (worst != ORI_OK)
+    return fail(worst, std::string("batched solve: some right-hand side ended with status ") + ori_status_string(worst));
   return ORI_OK;
 }
 
@@ -1006,17 +1249,15 @@ ori_status ori_adjoint_solve(ori_plan_t p, const double* u_dev, const double* ec
   ORI_TRY(check_solve_opts(opts, &o));
   ori_solve_info info{};
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
-  ORI_TRY(alloc_solver(p));
+  ORI_TRY(ensure_capacity(p, 1));
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
   ORI_VEC(p, ORI_PASS_VECTOR,
           (k_adj_rhs<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->S64, p->b64,
                                                       p->n3, p->sc, p->partials)));
-  ORI_CUDA(cudaMemcpyAsync(&p->h_sc->sum, &p->sc->sum, sizeof(double2), cudaMemcpyDeviceToHost, p->ps));
-  ORI_CUDA(cudaStreamSynchronize(p->ps));
-  if (p->timing) t_harvest(p);
-  const double bnorm = std::sqrt(p->h_sc->sum.x);
-  ORI_TRY(solve_B(p, bnorm, o, &info));
+  ORI_TRY(read_heads(p, 1));
+  const double bnorm = std::sqrt(p->h_sc[0].sum.x);
+  ORI_TRY(solve_B(p, 1, 1, &bnorm, o, &info));
   ORI_VEC(p, ORI_PASS_VECTOR,
           (k_gradient<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(econj_dev), p->w,
                                                        reinterpret_cast<const cpx<double>*>(u_dev), p->S64, p->h,

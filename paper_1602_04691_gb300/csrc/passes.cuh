@@ -81,6 +81,13 @@ struct XArgs {
   int mode;             // PRO_* or EPI_*
   const void* twL;      // twiddle table for length L
   const int* done;      // solver flag: the pass returns at once if *done != 0
+  // batch of right-hand sides: blockIdx.y selects one; each per-RHS pointer
+  // moves by its byte stride (scale, the medium, is shared by all)
+  long long bs_x, bs_p, bs_xin, bs_out, bs_bvec, bs_in, bs_fft;
+  long long bs_beta;    // bytes between the beta of consecutive RHS
+  int done_stride;      // bytes between the flags of consecutive RHS
+  const double* coefs;  // EPI_RUPDATE: per-RHS coefficient (overrides coef when set)
+  int nrhs;             // right-hand sides in the batch (gridDim.y)
 };
 
 struct SArgs {
@@ -98,7 +105,50 @@ struct SArgs {
   int H;                           // L/2 + 1
   const int* done;
   int sm_count;                    // persistent kernels: CTAs to launch
+  // batch of right-hand sides (blockIdx.y): byte strides of in/out per RHS,
+  // and of the spectra, one spectrum per wave number for rhs_per_ghat RHS
+  int nrhs;
+  long long bs_in, bs_out, bs_ghat, bs_ghatZ;
+  int rhs_per_ghat;
+  int done_stride;
 };
+
+// Move a pointer by `bytes` (null stays null).
+__device__ __forceinline__ const void* bmove(const void* p, long long bytes) {
+  return p == nullptr ? p : static_cast<const void*>(static_cast<const char*>(p) + bytes);
+}
+__device__ __forceinline__ void* bmove(void* p, long long bytes) {
+  return p == nullptr ? p : static_cast<void*>(static_cast<char*>(p) + bytes);
+}
+__device__ __forceinline__ const int* bflag(const int* f, int stride, int rhs) {
+  return f == nullptr ? f : reinterpret_cast<const int*>(reinterpret_cast<const char*>(f) + (long long)stride * rhs);
+}
+
+// The view of the arguments seen by right-hand side `rhs` of a batch.
+__device__ __forceinline__ XArgs x_for_rhs(XArgs a, int rhs) {
+  if (a.coefs != nullptr) a.coef = a.coefs[rhs];
+  if (rhs == 0) return a;
+  a.x = bmove(a.x, a.bs_x * rhs);
+  a.p = bmove(a.p, a.bs_p * rhs);
+  a.beta = bmove(a.beta, a.bs_beta * rhs);
+  a.xin = bmove(a.xin, a.bs_xin * rhs);
+  a.bvec = bmove(a.bvec, a.bs_bvec * rhs);
+  a.out = bmove(a.out, a.bs_out * rhs);
+  a.in = bmove(a.in, a.bs_fft * rhs);
+  a.fft_out = bmove(a.fft_out, a.bs_fft * rhs);
+  a.done = bflag(a.done, a.done_stride, rhs);
+  return a;
+}
+__device__ __forceinline__ SArgs s_for_rhs(SArgs a, int rhs) {
+  if (rhs == 0) return a;
+  a.in = bmove(a.in, a.bs_in * rhs);
+  a.out = bmove(a.out, a.bs_out * rhs);
+  const int g = a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0;
+  a.ghat = bmove(a.ghat, a.bs_ghat * g);
+  a.ghatZ = bmove(a.ghatZ, a.bs_ghatZ * g);
+  a.done = bflag(a.done, a.done_stride, rhs);
+  return a;
+}
 
 template <int L, int C, class T>
 struct Tile {

@@ -7,9 +7,7 @@
 #include "passes.cuh"
 #include "scalars.cuh"
 
-#include <cooperative_groups.h>
 #include <type_traits>
-namespace cg = cooperative_groups;
 
 namespace ori {
 
@@ -75,7 +73,8 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
 // X forward pass (contiguous lines): x[line][0..n) -> T1[line][0..L)
 // ---------------------------------------------------------------------------
 template <class T, int L, int C, bool HALF>
-__global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xfwd(XArgs a) {
+__global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xfwd(XArgs a0) {
+  const XArgs a = x_for_rhs(a0, blockIdx.y);
   using TL = Tile<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
   constexpr int PK = TL::PK, PC = TL::PC;
@@ -194,7 +193,9 @@ __device__ __forceinline__ void x_epilogue(const XArgs& a, long long i, cpx<T> v
 // X inverse pass + operator epilogue: T1[line][0..L) -> y[line][0..n)
 // ---------------------------------------------------------------------------
 template <class T, int L, int C>
-__global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv(XArgs a, Scalars* sc, int fin) {
+__global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv(XArgs a0, Scalars* sc0, int fin) {
+  const XArgs a = x_for_rhs(a0, blockIdx.y);
+  Scalars* sc = sc0 == nullptr ? nullptr : sc0 + blockIdx.y;
   using TL = Tile<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
   constexpr int PKI = TL::PKI, PCI = TL::PCI;
@@ -258,12 +259,13 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
       }
-      block_partial_lane0(make_double2(double(ax), double(ay)), red, a.partials);
+      block_partial_lane0(make_double2(double(ax), double(ay)), red, a.partials + (long long)blockIdx.y * gridDim.x);
       done_partial = true;
     }
   }
-  if (!done_partial) block_partial(acc, red, a.partials);
-  if (last_block_arrives(sc, s_last)) finalize(sc, a.partials, gridDim.x, fin, red);
+  double2* parts = a.partials + (long long)blockIdx.y * gridDim.x;
+  if (!done_partial) block_partial(acc, red, parts);
+  if (last_block_arrives(sc, s_last)) finalize(sc, parts, gridDim.x, fin, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv
 __device__ __forceinline__ int mirror_index(int k, int L) { return k <= L / 2 ? k : L - k; }
 
 template <class T, int L, int C, int SMODE, bool HALF>
-__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a) {
+__global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
+  const SArgs a = s_for_rhs(a0, blockIdx.y);
   using TL = Tile<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
   constexpr int PK = TL::PK, PC = TL::PC, PKI = TL::PKI, PCI = TL::PCI;
@@ -386,133 +389,6 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Z convolution on a cluster of Q CTAs (FP32, large L).  One cluster owns a
-// tile of C consecutive columns (C * 8 B = 256 B per row, so every global
-// row access is a full 256-byte segment even at the L^2 plane stride).  The
-// FFT's two transposes go through distributed shared memory:
-//   stage 1   CTA q: rows j1*L2 + j2 with j2 in its quarter, all C columns;
-//             DFT over j1; sends the k1-quarter k1/(L1/Q) to CTA k1/(L1/Q)
-//   stage 2   CTA q: its k1 quarter, DFT over j2 -> X[k1 + L1 k2];
-//             * spectrum; inverse DFT over k2; sends ja to CTA ja/(L2/Q)
-//   stage B   CTA q: its ja quarter, inverse DFT over k1 -> rows ja + L2 jb.
-// ---------------------------------------------------------------------------
-template <int L, int C, int Q, class T>
-struct ZTile {
-  static constexpr int L1 = Split<L>::L1;
-  static constexpr int L2 = Split<L>::L2;
-  static constexpr int J2Q = L2 / Q;           // j2 (and ja) values per CTA
-  static constexpr int K1Q = L1 / Q;           // k1 values per CTA
-  static constexpr int NT = C * J2Q;           // threads per CTA
-  static constexpr int NI = L1 / L2;           // stage-2 items per thread
-  static constexpr int PK = L2 + 1;            // buffer 1: [c][k1'][j2]
-  static constexpr int PC = (K1Q * PK) | 1;
-  static constexpr int PKI = L1 + 1;           // buffer 2: [c][ja'][k1]
-  static constexpr int PCI = (J2Q * PKI) | 1;
-  static constexpr int SMEM_ELEMS = (C * PC > C * PCI) ? C * PC : C * PCI;
-  static constexpr size_t SMEM_BYTES = size_t(SMEM_ELEMS) * sizeof(cpx<T>);
-};
-
-template <class T, int L, int C, int Q>
-__global__ void __cluster_dims__(Q, 1, 1) __launch_bounds__(ZTile<L, C, Q, T>::NT, 2)
-k_zconv_cluster(SArgs a) {
-  using ZT = ZTile<L, C, Q, T>;
-  constexpr int L1 = ZT::L1, L2 = ZT::L2, J2Q = ZT::J2Q, K1Q = ZT::K1Q, NT = ZT::NT, NI = ZT::NI;
-  constexpr int PK = ZT::PK, PC = ZT::PC, PKI = ZT::PKI, PCI = ZT::PCI;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
-  if (a.done != nullptr && *a.done != 0) return;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int q = int(cluster.block_rank());
-  const int tile = blockIdx.x / Q;
-  const int outer = tile / a.col_blocks;
-  const int cb = tile - outer * a.col_blocks;
-  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
-  const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in) + outer * a.in_outer + (long long)cb * C;
-  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + outer * a.out_outer + (long long)cb * C;
-  const int colmax = a.ncols - cb * C;
-  const int tid = threadIdx.x;
-  const int c = tid % C;
-  const int jl = tid / C;                 // local j2 / ja index in [0, J2Q)
-
-  // stage 1: rows j1*L2 + j2 (half-zero input), DFT over j1, twiddle, scatter
-  {
-    const int j2 = q * J2Q + jl;
-    cpx<T> r[L1];
-#pragma unroll
-    for (int j1 = 0; j1 < L1; ++j1) {
-      r[j1] = czero<T>();
-      if (j1 < L1 / 2) {
-        const int j = j1 * L2 + j2;
-        if (c < colmax && j < a.n_in) r[j1] = in[(long long)j * a.in_pt + c];
-      }
-    }
-    dft<L1, -1, true>(r);
-#pragma unroll
-    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
-#pragma unroll
-    for (int dst = 0; dst < Q; ++dst) {
-      cpx<T>* rsm = cluster.map_shared_rank(sm, dst);
-#pragma unroll
-      for (int kk = 0; kk < K1Q; ++kk) rsm[c * PC + kk * PK + j2] = r[dst * K1Q + kk];
-    }
-  }
-  cluster.sync();
-
-  // stage 2: this CTA's k1 quarter; DFT over j2; spectrum; inverse over k2
-  cpx<T> b[NI][L2];
-  const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
-  const int my = mirror_index(outer, L);
-#pragma unroll
-  for (int it = 0; it < NI; ++it) {
-    const int s = tid + it * NT;
-    const int c2 = s % C, kk = s / C;
-    const int k1 = q * K1Q + kk;
-#pragma unroll
-    for (int j = 0; j < L2; ++j) b[it][j] = sm[c2 * PC + kk * PK + j];
-    dft<L2, -1, false>(b[it]);
-    const int mx = mirror_index(min(cb * C + c2, L - 1), L);
-#pragma unroll
-    for (int k2 = 0; k2 < L2; ++k2) {
-      const int mz = mirror_index(k1 + L1 * k2, L);
-      b[it][k2] = cmul(b[it][k2], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
-    }
-    dft<L2, +1, false>(b[it]);
-#pragma unroll
-    for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
-  }
-  cluster.sync();   // every CTA has read buffer 1 before buffer 2 is written
-#pragma unroll
-  for (int it = 0; it < NI; ++it) {
-    const int s = tid + it * NT;
-    const int c2 = s % C, kk = s / C;
-    const int k1 = q * K1Q + kk;
-#pragma unroll
-    for (int dst = 0; dst < Q; ++dst) {
-      cpx<T>* rsm = cluster.map_shared_rank(sm, dst);
-#pragma unroll
-      for (int jj = 0; jj < J2Q; ++jj) rsm[c2 * PCI + jj * PKI + k1] = b[it][dst * J2Q + jj];
-    }
-  }
-  cluster.sync();
-
-  // stage B: this CTA's ja quarter; inverse DFT over k1; rows ja + L2 jb
-  {
-    const int ja = q * J2Q + jl;
-    cpx<T> r[L1];
-#pragma unroll
-    for (int k1 = 0; k1 < L1; ++k1) r[k1] = sm[c * PCI + jl * PKI + k1];
-    dft<L1, +1, false>(r);
-    if (c < colmax) {
-#pragma unroll
-      for (int jb = 0; jb < L1 / 2; ++jb) {
-        const int j = ja + L2 * jb;
-        if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // X and Y passes for the paired-FP32 residual, shared-memory resident (see
 // dfft.cuh): a tile of C lines (X) or C columns (Y) of L points per CTA.
 // ---------------------------------------------------------------------------
@@ -524,7 +400,8 @@ struct LSmem {
 };
 
 template <class T, int L, int C, int SMODE>
-__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a) {
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a0) {
+  const SArgs a = s_for_rhs(a0, blockIdx.y);
   using LS = LSmem<L, C, T>;
   constexpr int NT = LS::NT, S8 = L / 8;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -588,7 +465,8 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a)
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a) {
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a0) {
+  const XArgs a = x_for_rhs(a0, blockIdx.y);
   using LS = LSmem<L, C, T>;
   constexpr int NT = LS::NT, S8 = L / 8;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -627,7 +505,9 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a) {
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xinv_smem(XArgs a, Scalars* sc, int fin) {
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xinv_smem(XArgs a0, Scalars* sc0, int fin) {
+  const XArgs a = x_for_rhs(a0, blockIdx.y);
+  Scalars* sc = sc0 == nullptr ? nullptr : sc0 + blockIdx.y;
   using LS = LSmem<L, C, T>;
   constexpr int NT = LS::NT, S8 = L / 8;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -670,8 +550,9 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xinv_smem(XArgs a, Sc
   acc.x += accD.x;
   acc.y += accD.y;
   if (fin == FIN_NONE) return;
-  block_partial(acc, red, a.partials);
-  if (last_block_arrives(sc, s_last)) finalize(sc, a.partials, gridDim.x, fin, red);
+  double2* parts = a.partials + (long long)blockIdx.y * gridDim.x;
+  block_partial(acc, red, parts);
+  if (last_block_arrives(sc, s_last)) finalize(sc, parts, gridDim.x, fin, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -690,14 +571,14 @@ cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
     using LS = LSmem<L, CS, T>;
     auto kfs = k_xfwd_smem<T, L, CS>;
     if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
-    kfs<<<unsigned((a.nlines + CS - 1) / CS), LS::NT, LS::SMEM_BYTES, s>>>(a);
+    kfs<<<dim3(unsigned((a.nlines + CS - 1) / CS), unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
   }
   constexpr int C = lines_contig<T, L>();
   using TL = Tile<L, C, T>;
   auto kfn = k_xfwd<T, L, C, HALF>;
   if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
-  const unsigned grid = unsigned((a.nlines + C - 1) / C);
+  const dim3 grid(unsigned((a.nlines + C - 1) / C), unsigned(std::max(1, a.nrhs)));
   kfn<<<grid, TL::NT, TL::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
@@ -711,7 +592,7 @@ cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, 
     const unsigned grid = unsigned((a.nlines + CS - 1) / CS);
     if (nblocks) *nblocks = grid;
     if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
-    kfs<<<grid, LS::NT, LS::SMEM_BYTES, s>>>(a, sc, fin);
+    kfs<<<dim3(grid, unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a, sc, fin);
     return cudaGetLastError();
   }
   constexpr int C = lines_contig<T, L>();
@@ -720,7 +601,7 @@ cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, 
   const unsigned grid = unsigned((a.nlines + C - 1) / C);
   if (nblocks) *nblocks = grid;
   if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
-  kfn<<<grid, TL::NT, TL::SMEM_BYTES, s>>>(a, sc, fin);
+  kfn<<<dim3(grid, unsigned(std::max(1, a.nrhs))), TL::NT, TL::SMEM_BYTES, s>>>(a, sc, fin);
   return cudaGetLastError();
 }
 
@@ -737,7 +618,7 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
     auto kfs = k_strided_smem<T, L, CS, SMODE>;
     if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
     a.col_blocks = (a.ncols + CS - 1) / CS;
-    kfs<<<unsigned(a.nouter) * unsigned(a.col_blocks), LS::NT, LS::SMEM_BYTES, s>>>(a);
+    kfs<<<dim3(unsigned(a.nouter) * unsigned(a.col_blocks), unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a);
     return cudaGetLastError();
   }
   constexpr int C = cols_strided<T>();
@@ -745,7 +626,7 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
   auto kfn = k_strided<T, L, C, SMODE, HALF>;
   if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
   a.col_blocks = (a.ncols + C - 1) / C;
-  const unsigned grid = unsigned(a.nouter) * unsigned(a.col_blocks);
+  const dim3 grid(unsigned(a.nouter) * unsigned(a.col_blocks), unsigned(std::max(1, a.nrhs)));
   kfn<<<grid, TL::NT, TL::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
@@ -832,7 +713,8 @@ __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int ky, int 
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a) {
+__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a0) {
+  const SArgs a = s_for_rhs(a0, blockIdx.y);
   using TL = Tile<L, C, T>;
   using ZP = ZPipe<L, C, T>;
   constexpr bool GZ = ZP::GZ;
@@ -941,7 +823,8 @@ struct ZSmem {
 };
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a) {
+__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a0) {
+  const SArgs a = s_for_rhs(a0, blockIdx.y);
   using ZS = ZSmem<L, C, T>;
   constexpr int NT = ZS::NT;
   constexpr int S8 = L / 8;          // span of the first (and last) radix-8 stage
@@ -1020,8 +903,9 @@ cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
   auto kfn = k_zconv_smem<T, L, C>;
   if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZS::SMEM_BYTES));
   const int ntiles = L * (L / C);
-  const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count)));
-  kfn<<<grid, ZS::NT, ZS::SMEM_BYTES, s>>>(a);
+  const int nb = std::max(1, a.nrhs);
+  const unsigned gx = unsigned(std::max(1, std::min(ntiles, std::max(1, sm_count) / nb)));
+  kfn<<<dim3(gx, unsigned(nb)), ZS::NT, ZS::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1056,7 +940,8 @@ __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, cpx<T>*
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT)) k_yfwd_pipe(SArgs a) {
+__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT)) k_yfwd_pipe(SArgs a0) {
+  const SArgs a = s_for_rhs(a0, blockIdx.y);
   using TL = Tile<L, C, T>;
   using YP = YPipe<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
@@ -1129,8 +1014,9 @@ cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
   }
   a.col_blocks = (a.ncols + C - 1) / C;
   const int ntiles = a.nouter * a.col_blocks;
-  const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm)));
-  kfn<<<grid, YP::NT, YP::SMEM_BYTES, s>>>(a);
+  const int nb = std::max(1, a.nrhs);
+  const unsigned gx = unsigned(std::max(1, std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm) / nb)));
+  kfn<<<dim3(gx, unsigned(nb)), YP::NT, YP::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1149,20 +1035,9 @@ cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
     return e;
   }
   const int ntiles = L * (L / C);
-  const unsigned grid = unsigned(std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm)));
-  kfn<<<grid, ZP::NT, ZP::SMEM_BYTES, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <class T, int L>
-cudaError_t launch_zconv_cluster_L(SArgs a, cudaStream_t s, bool setup) {
-  constexpr int C = 32, Q = 4;
-  using ZT = ZTile<L, C, Q, T>;
-  auto kfn = k_zconv_cluster<T, L, C, Q>;
-  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZT::SMEM_BYTES));
-  a.col_blocks = (a.ncols + C - 1) / C;
-  const unsigned grid = unsigned(a.nouter) * unsigned(a.col_blocks) * Q;
-  kfn<<<grid, ZT::NT, ZT::SMEM_BYTES, s>>>(a);
+  const int nb = std::max(1, a.nrhs);
+  const unsigned gx = unsigned(std::max(1, std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm) / nb)));
+  kfn<<<dim3(gx, unsigned(nb)), ZP::NT, ZP::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 

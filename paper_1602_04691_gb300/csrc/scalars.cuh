@@ -23,7 +23,7 @@ enum { FIN_NONE = 0,    // no reduction
 enum { DONE_RUNNING = 0, DONE_CONVERGED = 1, DONE_BREAKDOWN = 2,
        DONE_NONFINITE = 3, DONE_MAXIT = 4 };
 
-constexpr int kHistMax = 4096;
+constexpr int kHistMax = 512;
 
 struct alignas(16) Scalars {
   double2 rho;       // r^T r (unconjugated) of the current residual

@@ -118,18 +118,25 @@ __device__ __forceinline__ void block_partial2(double2 a, double2 b, double2* re
 // every cell costs two complex products.
 __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __restrict__ S,
                       cpx<double>* u0, cpx<double>* b, int n, double d, double ox, double oy,
-                      double oz, double k, double ax, double ay, double az, Scalars* sc,
-                      double2* partials) {
+                      double oz, const double* __restrict__ kvals, const double* __restrict__ dirs,
+                      Scalars* sc0, double2* partials0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<double>* e = reinterpret_cast<cpx<double>*>(smraw);   // [3][n]
   __shared__ double2 red[64];
   __shared__ int s_last;
+  const int rb = blockIdx.y;                                  // right-hand side of the batch
   const long long n3 = (long long)n * n * n;
+  Scalars* sc = sc0 + rb;
+  double2* partials = partials0 + (long long)rb * gridDim.x;
+  if (rhs != nullptr) rhs += rb * n3;
+  u0 += rb * n3;
+  b += rb * n3;
   if (rhs == nullptr) {
+    const double k = kvals[rb];
     for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
       const int axis = t / n, i = t - axis * n;
       const double o = axis == 0 ? ox : (axis == 1 ? oy : oz);
-      const double a = axis == 0 ? ax : (axis == 1 ? ay : az);
+      const double a = dirs[3 * rb + axis];
       double sn, cs;
       sincos(k * a * (o + (i + 0.5) * d), &sn, &cs);
       e[t] = {cs, sn};
@@ -174,10 +181,15 @@ __global__ void k_adj_rhs(const cpx<double>* __restrict__ ec, const cpx<double>*
 // COCG start: x = 0, rho = r^T r, ||r||^2; sets tol/maxit and the flags.
 // Sums in T over 8 elements per thread, then in FP64.
 template <class T>
-__global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n3, Scalars* sc,
-                            double2* partials, double tol, int maxit) {
+__global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n3, Scalars* sc0,
+                            double2* partials0, const double* __restrict__ tols, int maxit) {
   __shared__ double2 red[64];
   __shared__ int s_last;
+  const int rb = blockIdx.y;
+  r += rb * n3;
+  x += rb * n3;
+  Scalars* sc = sc0 + rb;
+  double2* partials = partials0 + 2LL * rb * gridDim.x;
   double2 rho = make_double2(0.0, 0.0);
   double nn = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -202,7 +214,7 @@ __global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n
   block_partial2(rho, make_double2(nn, 0.0), red, partials);
   if (last_block_arrives(sc, s_last)) {
     if (threadIdx.x == 0) {
-      sc->tol = tol;
+      sc->tol = tols[rb];
       sc->maxit = maxit;
     }
     finalize(sc, partials, gridDim.x, FIN_INIT, red);
@@ -226,9 +238,13 @@ struct KahanF {
 template <class T>
 __global__ void k_cocg_update(cpx<T>* __restrict__ x, const cpx<T>* __restrict__ p,
                               cpx<T>* __restrict__ r, const cpx<T>* __restrict__ q, long long n3,
-                              Scalars* sc, double2* partials) {
+                              Scalars* sc0, double2* partials0) {
   __shared__ double2 red[64];
   __shared__ int s_last;
+  const int rb = blockIdx.y;
+  x += rb * n3; p += rb * n3; r += rb * n3; q += rb * n3;
+  Scalars* sc = sc0 + rb;
+  double2* partials = partials0 + 2LL * rb * gridDim.x;
   if (sc->done != 0) return;
   const double2 ad = sc->alpha;
   const cpx<T> al = {T(ad.x), T(ad.y)};
@@ -267,9 +283,13 @@ __global__ void k_cocg_update(cpx<T>* __restrict__ x, const cpx<T>* __restrict__
 template <>
 __global__ void k_cocg_update<float>(cpx<float>* __restrict__ x, const cpx<float>* __restrict__ p,
                                      cpx<float>* __restrict__ r, const cpx<float>* __restrict__ q,
-                                     long long n3, Scalars* sc, double2* partials) {
+                                     long long n3, Scalars* sc0, double2* partials0) {
   __shared__ double2 red[64];
   __shared__ int s_last;
+  const int rb = blockIdx.y;
+  x += rb * n3; p += rb * n3; r += rb * n3; q += rb * n3;
+  Scalars* sc = sc0 + rb;
+  double2* partials = partials0 + 2LL * rb * gridDim.x;
   if (sc->done != 0) return;
   const double2 ad = sc->alpha;
   const float ar = float(ad.x), ai = float(ad.y);
@@ -324,7 +344,11 @@ __global__ void k_cocg_update<float>(cpx<float>* __restrict__ x, const cpx<float
 
 // Mixed refinement: r32 = r64 / ||r64||.
 __global__ void k_normalise_to_f32(const cpx<double>* __restrict__ r64, cpx<float>* r32,
-                                   long long n3, double inv) {
+                                   long long n3, const double* __restrict__ invs) {
+  const int rb = blockIdx.y;
+  const double inv = invs[rb];
+  r64 += rb * n3;
+  r32 += rb * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> v = r64[i];
@@ -334,7 +358,12 @@ __global__ void k_normalise_to_f32(const cpx<double>* __restrict__ r64, cpx<floa
 
 // Mixed refinement: w += scale * d32.
 __global__ void k_accumulate(cpx<double>* w, const cpx<float>* __restrict__ d32, long long n3,
-                             double scale) {
+                             const double* __restrict__ scales) {
+  const int rb = blockIdx.y;
+  const double scale = scales[rb];
+  if (scale == 0.0) return;
+  w += rb * n3;
+  d32 += rb * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<float> dv = d32[i];
@@ -348,6 +377,8 @@ __global__ void k_accumulate(cpx<double>* w, const cpx<float>* __restrict__ d32,
 // u = w / S = w * (1/S) (every S != 0; 1/S is kept by the plan).
 __global__ void k_recover(const cpx<double>* __restrict__ w, const cpx<double>* __restrict__ Sinv,
                           cpx<double>* u, long long n3) {
+  w += blockIdx.y * n3;
+  u += blockIdx.y * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x)
     u[i] = cmul(w[i], Sinv[i]);

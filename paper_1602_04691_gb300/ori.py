@@ -59,13 +59,19 @@ class Plan:
     """Operator for one grid (n^3 cells of a cube), wave number k and medium (h, N).
 
     h: complex128 CUDA tensor of n^3 impedances, N: float64 CUDA tensor of n^3
-    densities, both C-ordered [z][y][x].  c_S defaults to 4 pi (spheres)."""
+    densities, both C-ordered [z][y][x].  c_S defaults to 4 pi (spheres).
+    k may be a sequence of wave numbers: the plan then holds one spectrum per
+    entry, ``solve_batch`` solves for all of them, and the single-system
+    calls use the first."""
 
-    def __init__(self, n: int, k: float, h: torch.Tensor, N: torch.Tensor, side: float = 1.0,
+    def __init__(self, n: int, k, h: torch.Tensor, N: torch.Tensor, side: float = 1.0,
                  origin=(0.0, 0.0, 0.0), c_S: float | None = None, mem_cap: int = 0, stream=None):
         lib = _lib.load()
         self.n = int(n)
-        self.k = float(k)
+        self.ks = [float(v) for v in k] if hasattr(k, "__len__") else [float(k)]
+        if not self.ks:
+            raise ValueError("k must hold at least one wave number")
+        self.k = self.ks[0]
         self.side = float(side)
         self.origin = tuple(float(v) for v in origin)
         self.c_S = 4.0 * math.pi if c_S is None else float(c_S)
@@ -81,6 +87,10 @@ class Plan:
         lib.ori_default_plan_opts(C.byref(po))
         po.c_S = self.c_S
         po.mem_cap = int(mem_cap)
+        ks_arr = (C.c_double * len(self.ks))(*self.ks)
+        if len(self.ks) > 1:
+            po.n_k = len(self.ks)
+            po.ks = C.cast(ks_arr, C.POINTER(C.c_double))
         handle = C.c_void_p()
         with torch.cuda.device(self.device):
             st = lib.ori_plan(self.n, self.k, C.byref(dom), h.data_ptr(), N.data_ptr(), C.byref(po),
@@ -171,6 +181,46 @@ class Plan:
         d = info.as_dict()
         d["returned"] = st
         return u, d
+
+    def solve_batch(self, alphas=None, rhs: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                    raise_on_failure: bool = True, stream=None, **kw):
+        """Solve for every wave number of the plan and every incidence direction at once.
+
+        alphas: sequence of ndir directions (x, y, z) for plane-wave right-hand sides, or
+        None with rhs: complex128 tensor of shape (n_k, ndir, n^3) (or anything of that
+        size).  Returns (u of shape (n_k, ndir, n^3), list of n_k * ndir info dicts with
+        system r = i * ndir + j)."""
+        m = self.n ** 3
+        nk = len(self.ks)
+        if rhs is not None:
+            if rhs.numel() % (nk * m) != 0:
+                raise ValueError(f"rhs must hold n_k * ndir * {m} elements")
+            ndir = rhs.numel() // (nk * m)
+            rhs = _need(rhs, torch.complex128, nk * ndir * m, "rhs")
+            al = None
+        else:
+            if alphas is None:
+                raise ValueError("give alphas or rhs")
+            dirs = [tuple(float(c) for c in a) for a in alphas]
+            if not dirs or any(len(a) != 3 for a in dirs):
+                raise ValueError("alphas must be a non-empty sequence of 3-vectors")
+            ndir = len(dirs)
+            al = (C.c_double * (3 * ndir))(*[c for a in dirs for c in a])
+        u = (torch.empty(nk * ndir * m, dtype=torch.complex128, device=self.device)
+             if out is None else _need(out, torch.complex128, nk * ndir * m, "out"))
+        o = solve_opts(**kw)
+        infos = (_lib.SolveInfo * (nk * ndir))()
+        st = _lib.load().ori_cocg_solve_batch(self.handle, ndir, C.cast(al, C.c_void_p) if al is not None else None,
+                                              rhs.data_ptr() if rhs is not None else None, u.data_ptr(),
+                                              C.byref(o), C.cast(infos, C.c_void_p), _stream_ptr(stream))
+        if raise_on_failure:
+            _lib.check(st, "ori_cocg_solve_batch")
+        out_infos = []
+        for i in range(nk * ndir):
+            d = infos[i].as_dict()
+            d["returned"] = st
+            out_infos.append(d)
+        return u.view(nk, ndir, m), out_infos
 
     def adjoint(self, u: torch.Tensor, econj: torch.Tensor, raise_on_failure: bool = True,
                 stream=None, **kw):

@@ -1,0 +1,170 @@
+"""Batched solves: several wave numbers x several incidence directions in one batch.
+
+Each system of a batch (wave number k_i, direction alpha_j) is the system of
+Eq. 2.19 with the plane wave of Eq. 2.4; the batch must give what separate
+solves give.  Checks: dense LU from the oracle at small n, the oracle's
+direct-sum residual on sampled rows at n = 128 (16 directions x 4 wave
+numbers), agreement with single-system solves, masking of systems that
+converge early, and bitwise repeatability when the batch size changes in
+between (the captured graphs are rebuilt).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1602_04691_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def unit(a):
+    a = np.asarray(a, dtype=np.float64)
+    return a / np.linalg.norm(a)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def make_plan(n, k, h, N, **kw):
+    from paper_1602_04691_gb300 import Plan
+    return Plan(n, k, to_dev(h), to_dev(N), **kw)
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-12, 1e-9), ("mixed", 1e-6, 2e-5)])
+def test_batch_plane_waves_vs_lu(precision, tol, bound):
+    n, ks = 8, [1.0, 2.5]
+    dirs = [(0.0, 0.0, 1.0), (1.0, 1.0, 0.0), (-0.3, 0.5, 0.8)]
+    h, N = inputs.random_h_N(n, 81)
+    plan = make_plan(n, ks, h, N)
+    u, infos = plan.solve_batch(dirs, tol=tol, precision=precision)
+    u = u.cpu().numpy()
+    pos = O.cell_centres(n)
+    for i, k in enumerate(ks):
+        A = O.red_matrix(n, k, h, N)
+        for j, a in enumerate(dirs):
+            info = infos[i * len(dirs) + j]
+            assert info["status"] == 0 and info["relres"] <= tol
+            u_lu = O.solve_dense(A, O.plane_wave(pos, k, unit(a)))
+            assert rel(u[i, j], u_lu) < bound, (i, j)
+
+
+def test_batch_user_rhs_vs_lu():
+    n, k = 10, 2.0
+    h, N = inputs.random_h_N(n, 91)
+    rhs = np.stack([inputs.random_complex(n ** 3, 910 + j) for j in range(3)])
+    plan = make_plan(n, k, h, N)
+    u, infos = plan.solve_batch(rhs=to_dev(rhs), tol=1e-12, precision="fp64")
+    A = O.red_matrix(n, k, h, N)
+    for j in range(3):
+        assert rel(u[0, j].cpu().numpy(), O.solve_dense(A, rhs[j])) < 1e-9
+
+
+def test_batch_matches_single_solves():
+    """Every system of a mixed batch agrees with its own FP64 single solve."""
+    n, ks = 20, [2.0, 5.0]
+    dirs = inputs.fibonacci_directions(4)
+    h, N = inputs.random_h_N(n, 92)
+    plan = make_plan(n, ks, h, N)
+    ub, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+    for i, k in enumerate(ks):
+        single = make_plan(n, k, h, N)
+        for j, a in enumerate(dirs):
+            us, _ = single.solve(tol=1e-10, precision="fp64", alpha=tuple(a))
+            assert infos[i * len(dirs) + j]["relres"] <= 1e-6
+            assert rel(ub[i, j].cpu().numpy(), us.cpu().numpy()) < 1e-5, (i, j)
+        single.close()
+
+
+def test_batch_masks_converged_systems():
+    """A zero right-hand side stops at once (u = 0, no iterations) and systems
+    of different difficulty stop at their own iteration counts, each meeting tol."""
+    n = 16
+    ks = [0.5, 6.0]
+    h, N = inputs.random_h_N(n, 93)
+    pos = O.cell_centres(n)
+    rhs = np.zeros((2, 2, n ** 3), dtype=np.complex128)
+    rhs[0, 0] = O.plane_wave(pos, ks[0])
+    rhs[1, 0] = O.plane_wave(pos, ks[1])
+    rhs[1, 1] = O.plane_wave(pos, ks[1], unit((1.0, 0.0, 0.0)))
+    plan = make_plan(n, ks, h, N)
+    for precision, tol in [("fp64", 1e-10), ("mixed", 1e-6)]:
+        u, infos = plan.solve_batch(rhs=to_dev(rhs), tol=tol, precision=precision)
+        u = u.cpu().numpy()
+        assert infos[1]["iters"] == 0 and np.all(u[0, 1] == 0)
+        iters = [infos[r]["iters"] for r in (0, 2, 3)]
+        assert iters[0] < iters[1], iters
+        for r in (0, 2, 3):
+            assert infos[r]["status"] == 0 and infos[r]["relres"] <= tol
+        A0 = O.red_matrix(n, ks[0], h, N)
+        assert rel(u[0, 0], O.solve_dense(A0, rhs[0, 0])) < (1e-7 if precision == "fp64" else 2e-5)
+
+
+def test_batch_repeatable_across_batch_sizes():
+    n, ks = 12, [1.5, 3.0]
+    dirs = [(0.0, 0.0, 1.0), (0.0, 1.0, 0.0)]
+    h, N = inputs.random_h_N(n, 94)
+    plan = make_plan(n, ks, h, N)
+    u1, _ = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+    u1 = u1.cpu().numpy().copy()
+    plan.solve(tol=1e-6, precision="mixed")
+    plan.solve_batch(dirs[:1], tol=1e-6, precision="mixed")
+    u2, _ = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+    assert np.array_equal(u1, u2.cpu().numpy())
+
+
+def test_batch_graph_and_plain_launches_agree():
+    n, ks = 12, [2.0, 4.0]
+    dirs = inputs.fibonacci_directions(3)
+    h, N = inputs.random_h_N(n, 95)
+    plan = make_plan(n, ks, h, N)
+    ug, ig = plan.solve_batch(dirs, tol=1e-6, precision="mixed", use_graph=True)
+    up, ip = plan.solve_batch(dirs, tol=1e-6, precision="mixed", use_graph=False)
+    assert np.array_equal(ug.cpu().numpy(), up.cpu().numpy())
+    assert [i["iters"] for i in ig] == [i["iters"] for i in ip]
+
+
+def test_batch_16_directions_4_wave_numbers_n128():
+    """n = 128, 16 directions spread on the sphere x k in {1, 2, 4, 8}: one
+    mixed batch of 64 systems, each meeting relres 1e-6.  Sampled rows of
+    Eq. 2.19 by direct summation (oracle) for three systems, and two systems
+    against their own FP64 single solves."""
+    n, ks = 128, [1.0, 2.0, 4.0, 8.0]
+    dirs = inputs.fibonacci_directions(16)
+    h, N = inputs.random_h_N(n, 4)
+    plan = make_plan(n, ks, h, N)
+    u, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+    assert len(infos) == 64
+    for r, info in enumerate(infos):
+        assert info["status"] == 0 and info["relres"] <= 1e-6, (r, info)
+    pos_rows = np.random.default_rng(128).choice(n ** 3, 48, replace=False)
+    centres = O.cell_centres(n)
+    for (i, j) in [(0, 0), (2, 7), (3, 15)]:
+        k = ks[i]
+        ui = u[i, j].cpu().numpy()
+        Au = O.red_matvec_rows(ui, pos_rows, n, k, h, N)
+        u0 = O.plane_wave(centres[pos_rows], k, unit(dirs[j]))
+        assert np.linalg.norm(Au - u0) / np.linalg.norm(u0) < 1e-4, (i, j)
+    for (i, j) in [(1, 3), (3, 9)]:
+        single = make_plan(n, ks[i], h, N)
+        us, _ = single.solve(tol=1e-9, precision="fp64", alpha=tuple(dirs[j]))
+        assert rel(u[i, j].cpu().numpy(), us.cpu().numpy()) < 1e-5, (i, j)
+        single.close()
