@@ -285,6 +285,51 @@ ori_status ori_adjoint_solve(ori_plan_t plan, const double* u_dev,
                              double* grad_N_dev, const ori_solve_opts* opts,
                              ori_solve_info* info, void* stream);
 
+/*
+ * Launch schedules.  The FP32 Y-forward and Z passes (L >= 64) each have two
+ * kernels: a persistent one that streams the next tile into shared memory
+ * with cp.async while it transforms the current one, and one CTA per tile of
+ * columns.  Which is faster depends on n, the batch size and the GPU; so does
+ * the grid of the vector kernels.  The paper has no counterpart (its code is
+ * a CPU FFT library).  Paired-FP32 and FP64 passes have one schedule each.
+ */
+enum { ORI_SCHED_PERSISTENT = 0, ORI_SCHED_TILES = 1 };
+
+typedef struct {
+  int yfwd;             /* FP32 Y forward pass: ORI_SCHED_PERSISTENT (default) or
+                           ORI_SCHED_TILES                                         */
+  int zconv;            /* FP32 Z pass (forward FFT, spectrum product, inverse)   */
+  int ctas_per_sm;      /* persistent kernels: resident CTAs per SM to launch,
+                           0 (default) = as many as fit, else at most this many    */
+  int vec_ctas_per_sm;  /* vector kernels (updates, norms): CTAs per SM, 1..16;
+                           0 -> 8 (default)                                        */
+  int reserved[4];
+} ori_schedule;
+
+/* The plan's current schedule. */
+ori_status ori_plan_get_schedule(ori_plan_t plan, ori_schedule* out);
+
+/* Use schedule *s from now on (drops the plan's captured graphs).  Out-of-range
+ * fields return ORI_ERR_INVALID_ARG.  Synchronises the plan's stream. */
+ori_status ori_plan_set_schedule(ori_plan_t plan, const ori_schedule* s);
+
+/*
+ * ori_plan_autotune - time the candidate schedules on this plan for a batch of
+ * nrhs systems (1..4096) and keep the fastest.  Each candidate pair of FP32
+ * Y-forward / Z kernels (with the persistent CTA cap 0 or 1) is timed over
+ * `reps` (1..100) FP32 operator applications y = B x on the plan's scratch
+ * vectors after one warm-up; then the vector grid (4, 8 or 16 CTAs per SM) is
+ * timed on the FP32 COCG update.  Grows the plan's batch scratch to nrhs like
+ * ori_cocg_solve_batch; overwrites the scratch vectors (not the medium or
+ * spectra); leaves ori_plan_stats unchanged.  *best (may be NULL) receives the
+ * chosen schedule, *best_ms (may be NULL) its operator time for the whole
+ * batch in milliseconds.  Synchronising.  A cache of results keyed by GPU,
+ * n, nrhs and arithmetic belongs to the caller (the Python binding keeps one
+ * as JSON).
+ */
+ori_status ori_plan_autotune(ori_plan_t plan, int nrhs, int reps, ori_schedule* best,
+                             float* best_ms, void* stream);
+
 /* Device-time accounting of a plan's kernels (for profiling and benchmarks). */
 enum {
   ORI_PASS_XFWD = 0,   /* X forward FFT pass with its prologue                  */

@@ -35,8 +35,11 @@ EXPORTS = [
     "ori_plan_destroy", "ori_plan_info", "ori_matvec", "ori_matvec32", "ori_cocg_solve",
     "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
     "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats", "ori_matvec_noalloc",
-    "ori_cocg_solve_batch",
+    "ori_cocg_solve_batch", "ori_plan_get_schedule", "ori_plan_set_schedule", "ori_plan_autotune",
 ]
+
+ORI_SCHED_PERSISTENT = 0
+ORI_SCHED_TILES = 1
 
 PASS_NAMES = ["xfwd", "yfwd", "zconv", "yinv", "xinv", "update", "vector", "unused"]
 PASS_NAMES = ([k + "_f32" for k in PASS_NAMES] + [k + "_f64" for k in PASS_NAMES]
@@ -66,6 +69,24 @@ class SolveInfo(C.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Schedule(C.Structure):
+    _fields_ = [("yfwd", C.c_int), ("zconv", C.c_int), ("ctas_per_sm", C.c_int),
+                ("vec_ctas_per_sm", C.c_int), ("reserved", C.c_int * 4)]
+
+    def as_dict(self):
+        return {"yfwd": int(self.yfwd), "zconv": int(self.zconv), "ctas_per_sm": int(self.ctas_per_sm),
+                "vec_ctas_per_sm": int(self.vec_ctas_per_sm)}
+
+    @classmethod
+    def from_dict(cls, d):
+        s = cls()
+        s.yfwd = int(d["yfwd"])
+        s.zconv = int(d["zconv"])
+        s.ctas_per_sm = int(d["ctas_per_sm"])
+        s.vec_ctas_per_sm = int(d["vec_ctas_per_sm"])
+        return s
 
 
 class PlanStats(C.Structure):
@@ -124,6 +145,12 @@ def load():
     lib.ori_cocg_solve.restype = i
     lib.ori_cocg_solve_batch.argtypes = [vp, i, vp, vp, vp, C.POINTER(SolveOpts), vp, vp]
     lib.ori_cocg_solve_batch.restype = i
+    lib.ori_plan_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    lib.ori_plan_get_schedule.restype = i
+    lib.ori_plan_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
+    lib.ori_plan_set_schedule.restype = i
+    lib.ori_plan_autotune.argtypes = [vp, i, i, C.POINTER(Schedule), C.POINTER(C.c_float), vp]
+    lib.ori_plan_autotune.restype = i
     lib.ori_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.ori_adjoint_solve.restype = i
     lib.ori_plan_set_timing.argtypes = [vp, i]

@@ -123,6 +123,8 @@ struct ori_plan_s {
   int graph_f_len = 0, graph_d_len = 0, graph_f_nrhs = 0, graph_d_nrhs = 0;
   bool graph_f_timed = false, graph_d_timed = false;
   int vec_grid = 0;
+  // launch schedule (ori_schedule): FP32 Y-forward / Z kernels, CTA cap, vector grid
+  int sched_y = SCHED_PERSISTENT, sched_z = SCHED_PERSISTENT, cta_cap = 0, vec_ctas = 8;
   // accounting (ori_plan_stats) and optional per-kernel event timing
   ori_plan_stats stats{};
   bool capturing = false;
@@ -144,6 +146,7 @@ struct ori_plan_s {
 };
 
 static constexpr int kEvPool = 4096;
+static constexpr int kMaxVecCtasPerSm = 16;   // bound of ori_schedule.vec_ctas_per_sm
 
 // Count one kernel launch (graph nodes are counted at each replay instead).
 static inline void launched(ori_plan_s* p) {
@@ -275,7 +278,8 @@ static ori_status ensure_capacity(ori_plan_s* p, int nrhs) {
   ORI_TRY(alloc_n(p, &p->T2d, c * t2_elems(p)));
   ORI_TRY(alloc_n(p, &p->sc, c));
   ORI_CUDA(cudaMemsetAsync(p->sc, 0, c * sizeof(Scalars), p->ps));
-  p->part_per_rhs = std::max<size_t>(size_t(p->xinv_blocks), size_t(2 * p->vec_grid)) + 16;
+  // partials of the X-inverse reductions, or two per block of the widest vector grid
+  p->part_per_rhs = std::max<size_t>(size_t(p->xinv_blocks), size_t(2) * std::max(1, p->sm_count) * kMaxVecCtasPerSm) + 16;
   ORI_TRY(alloc_n(p, &p->partials, c * p->part_per_rhs));
   for (cpx<double>** v : {&p->b64, &p->w, &p->r64, &p->u0, &p->p64, &p->q64}) ORI_TRY(alloc_n(p, v, c * n3));
   for (cpx<float>** v : {&p->x32, &p->r32, &p->p32, &p->q32}) ORI_TRY(alloc_n(p, v, c * n3));
@@ -379,6 +383,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = n; y.n_out = L; y.nouter = n;
   y.twL = tw; y.done = mask.flags; y.done_stride = mask.stride; y.sm_count = p->sm_count;
   y.nrhs = nrhs; y.bs_in = bsT1; y.bs_out = bsT2;
+  y.sched = p->sched_y; y.cta_cap = p->cta_cap;
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + K, e0, e1); e0 = e1;
@@ -394,6 +399,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.bs_ghat = H3 * (long long)sizeof(cpx<T>);
   z.bs_ghatZ = (long long)p->H * p->H * p->L * (long long)sizeof(cpx<float>);
   z.rhs_per_ghat = rhs_per_k;
+  z.sched = p->sched_z; z.cta_cap = p->cta_cap;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + K, e0, e1); e0 = e1;
@@ -614,7 +620,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     p->c_S = o.c_S;
     p->mem_cap = o.mem_cap;
     cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
-    p->vec_grid = std::max(1, p->sm_count) * 8;
+    p->vec_grid = std::max(1, p->sm_count) * p->vec_ctas;
     if (cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->evj, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess) {
@@ -1272,6 +1278,181 @@ ori_status ori_adjoint_solve(ori_plan_t p, const double* u_dev, const double* ec
   if (info.status != ORI_OK)
     return fail(ori_status(info.status), std::string("adjoint solve ended with status ") + ori_status_string(info.status));
   return ORI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch schedules and the autotuner
+// ---------------------------------------------------------------------------
+
+static_assert(ORI_SCHED_PERSISTENT == SCHED_PERSISTENT && ORI_SCHED_TILES == SCHED_TILES,
+              "schedule codes of the ABI and the kernels must agree");
+
+static void apply_schedule(ori_plan_s* p, const ori_schedule& s) {
+  p->sched_y = s.yfwd;
+  p->sched_z = s.zconv;
+  p->cta_cap = s.ctas_per_sm;
+  p->vec_ctas = s.vec_ctas_per_sm > 0 ? s.vec_ctas_per_sm : 8;
+  p->vec_grid = std::max(1, p->sm_count) * p->vec_ctas;
+  drop_graphs(p);   // captured launches carry the old grids
+}
+
+static ori_schedule current_schedule(const ori_plan_s* p) {
+  ori_schedule s{};
+  s.yfwd = p->sched_y;
+  s.zconv = p->sched_z;
+  s.ctas_per_sm = p->cta_cap;
+  s.vec_ctas_per_sm = p->vec_ctas;
+  return s;
+}
+
+// Device time of `reps` FP32 operator applications y = B x over a batch of
+// nrhs systems on the plan's scratch vectors (no masks), per application.
+static ori_status time_fp32_operator(ori_plan_s* p, int nrhs, int reps, float* ms) {
+  const long long bs32 = p->n3 * (long long)sizeof(cpx<float>);
+  const int nk = int(p->ks.size());
+  const int per_k = (nrhs + nk - 1) / nk;
+  XArgs pro{}, epi{};
+  pro.mode = PRO_SCALE;
+  pro.x = p->x32;
+  pro.bs_x = bs32;
+  pro.scale = p->S32;
+  epi.mode = EPI_PLUS_S;
+  epi.xin = p->x32;
+  epi.bs_xin = bs32;
+  epi.out = p->q32;
+  epi.bs_out = bs32;
+  epi.scale = p->S32;
+  ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, Mask{}, nrhs, per_k));   // warm-up
+  ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
+  for (int i = 0; i < reps; ++i) ORI_TRY(run_conv<float>(p, pro, epi, FIN_NONE, p->ps, Mask{}, nrhs, per_k));
+  ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
+  ORI_CUDA(cudaEventSynchronize(p->ev1));
+  float t = 0.f;
+  ORI_CUDA(cudaEventElapsedTime(&t, p->ev0, p->ev1));
+  *ms = t / float(reps);
+  return ORI_OK;
+}
+
+// Device time of one FP32 COCG vector update over the batch (scalars reset
+// before each launch so that no system is flagged as finished).
+static ori_status time_fp32_update(ori_plan_s* p, int nrhs, int reps, float* ms) {
+  const int vg = vgrid(p, nrhs);
+  float total = 0.f;
+  for (int i = 0; i <= reps; ++i) {
+    ORI_CUDA(cudaMemsetAsync(p->sc, 0, size_t(nrhs) * sizeof(Scalars), p->ps));
+    ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
+    k_cocg_update<float><<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->x32, p->p32, p->r32, p->q32, p->n3, p->sc, p->partials);
+    ORI_CUDA(cudaGetLastError());
+    ORI_CUDA(cudaEventRecord(p->ev1, p->ps));
+    ORI_CUDA(cudaEventSynchronize(p->ev1));
+    float t = 0.f;
+    ORI_CUDA(cudaEventElapsedTime(&t, p->ev0, p->ev1));
+    if (i > 0) total += t;   // the first launch is a warm-up
+  }
+  *ms = total / float(reps);
+  return ORI_OK;
+}
+
+static ori_status autotune(ori_plan_s* p, int nrhs, int reps, ori_schedule* best_out, float* best_ms) {
+  ORI_TRY(ensure_capacity(p, nrhs));
+  const size_t n3 = size_t(p->n3) * size_t(nrhs);
+  for (cpx<float>* v : {p->x32, p->p32, p->r32, p->q32})
+    ORI_CUDA(cudaMemsetAsync(v, 0, n3 * sizeof(cpx<float>), p->ps));
+  ori_schedule best = current_schedule(p);
+  float best_t = 0.f;
+  // FFT pass schedules (only the FP32 passes at L >= 64 have alternatives)
+  struct Cand { int y, z, cap; };
+  std::vector<Cand> cands;
+  if (p->L >= 64) {
+    for (int y : {SCHED_PERSISTENT, SCHED_TILES})
+      for (int z : {SCHED_PERSISTENT, SCHED_TILES})
+        for (int cap : {0, 1}) {
+          if (y == SCHED_TILES && z == SCHED_TILES && cap != 0) continue;   // cap unused
+          cands.push_back({y, z, cap});
+        }
+  } else {
+    cands.push_back({SCHED_PERSISTENT, SCHED_PERSISTENT, 0});
+  }
+  bool first = true;
+  for (const Cand& c : cands) {
+    ori_schedule s = best;
+    s.yfwd = c.y;
+    s.zconv = c.z;
+    s.ctas_per_sm = c.cap;
+    apply_schedule(p, s);
+    float t = 0.f;
+    ORI_TRY(time_fp32_operator(p, nrhs, reps, &t));
+    if (first || t < best_t) {
+      best_t = t;
+      best = s;
+      first = false;
+    }
+  }
+  apply_schedule(p, best);
+  // vector-kernel grid
+  float best_v = 0.f;
+  first = true;
+  for (int v : {4, 8, 16}) {
+    ori_schedule s = best;
+    s.vec_ctas_per_sm = v;
+    apply_schedule(p, s);
+    float t = 0.f;
+    ORI_TRY(time_fp32_update(p, nrhs, reps, &t));
+    if (first || t < best_v) {
+      best_v = t;
+      best.vec_ctas_per_sm = v;
+      first = false;
+    }
+  }
+  apply_schedule(p, best);
+  ORI_CUDA(cudaMemsetAsync(p->sc, 0, size_t(nrhs) * sizeof(Scalars), p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (best_out) *best_out = best;
+  if (best_ms) *best_ms = best_t;
+  return ORI_OK;
+}
+
+extern "C" {
+
+ori_status ori_plan_get_schedule(ori_plan_t p, ori_schedule* out) {
+  if (!p || !out) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  *out = current_schedule(p);
+  return ORI_OK;
+}
+
+ori_status ori_plan_set_schedule(ori_plan_t p, const ori_schedule* s) {
+  g_last_error.clear();
+  if (!p || !s) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if ((s->yfwd != ORI_SCHED_PERSISTENT && s->yfwd != ORI_SCHED_TILES) ||
+      (s->zconv != ORI_SCHED_PERSISTENT && s->zconv != ORI_SCHED_TILES))
+    return fail(ORI_ERR_INVALID_ARG, "yfwd and zconv must be ORI_SCHED_PERSISTENT or ORI_SCHED_TILES");
+  if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64) return fail(ORI_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
+  if (s->vec_ctas_per_sm < 0 || s->vec_ctas_per_sm > kMaxVecCtasPerSm)
+    return fail(ORI_ERR_INVALID_ARG, "vec_ctas_per_sm must be in [0, 16]");
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  apply_schedule(p, *s);
+  return ORI_OK;
+}
+
+ori_status ori_plan_autotune(ori_plan_t p, int nrhs, int reps, ori_schedule* best, float* best_ms, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(ORI_ERR_INVALID_ARG, "plan is NULL");
+  if (nrhs < 1 || nrhs > 4096) return fail(ORI_ERR_INVALID_ARG, "nrhs must be in [1, 4096]");
+  if (reps < 1 || reps > 100) return fail(ORI_ERR_INVALID_ARG, "reps must be in [1, 100]");
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(enter(p, user));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->timing) t_harvest(p);
+  const bool timing = p->timing;
+  const ori_plan_stats saved = p->stats;
+  p->timing = false;
+  const ori_status st = autotune(p, nrhs, reps, best, best_ms);
+  p->timing = timing;
+  p->stats = saved;
+  if (st != ORI_OK) return st;
+  return leave(p, user);
 }
 
 }  // extern "C"

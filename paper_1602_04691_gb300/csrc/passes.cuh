@@ -111,7 +111,15 @@ struct SArgs {
   long long bs_in, bs_out, bs_ghat, bs_ghatZ;
   int rhs_per_ghat;
   int done_stride;
+  // launch schedule of the FP32 Y-forward and Z passes (chosen by the plan's
+  // autotuner): SCHED_PERSISTENT = the cp.async-pipelined persistent kernel
+  // with at most cta_cap resident CTAs per SM (0 = as many as fit);
+  // SCHED_TILES = one CTA per tile of columns
+  int sched;
+  int cta_cap;
 };
+
+enum { SCHED_PERSISTENT = 0, SCHED_TILES = 1 };
 
 // Move a pointer by `bytes` (null stays null).
 __device__ __forceinline__ const void* bmove(const void* p, long long bytes) {

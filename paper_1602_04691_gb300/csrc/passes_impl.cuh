@@ -610,8 +610,14 @@ cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
 
 template <class T, int L, int SMODE, bool HALF>
 cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
-  if constexpr (sizeof(T) == 4 && SMODE == SMODE_FWD && HALF && L >= 64)
-    return launch_yfwd_pipe_L<T, L>(a, s, setup, a.sm_count);
+  if constexpr (sizeof(T) == 4 && SMODE == SMODE_FWD && HALF && L >= 64) {
+    if (setup) {   // both schedules are set up; the plan picks one per launch
+      cudaError_t e = launch_yfwd_pipe_L<T, L>(a, s, true, a.sm_count);
+      if (e != cudaSuccess) return e;
+    } else if (a.sched == SCHED_PERSISTENT) {
+      return launch_yfwd_pipe_L<T, L>(a, s, false, a.sm_count);
+    }
+  }
   if constexpr (std::is_same<T, dfl>::value && L >= 64 && ((SMODE == SMODE_FWD && HALF) || SMODE == SMODE_INV)) {
     constexpr int CS = 4;
     using LS = LSmem<L, CS, T>;
@@ -654,6 +660,21 @@ __device__ __forceinline__ int ky_of_slot(int i, int L) {
   return (i & 1) ? L - m : m;
 }
 
+// Persistent passes number the tiles of a batch consecutively: right-hand
+// side r owns tiles [r * per_rhs, (r + 1) * per_rhs).  A CTA visits tiles
+// t, t + step, ...; this returns the first of them at or after t whose
+// right-hand side is still running (ntiles when none is left).
+__device__ __forceinline__ int next_live_tile(const SArgs& a, int t, int step, int per_rhs, int ntiles) {
+  if (a.done == nullptr) return t;
+  while (t < ntiles) {
+    const int r = t / per_rhs;
+    if (*bflag(a.done, a.done_stride, r) == 0) return t;
+    const int first_next = (r + 1) * per_rhs;          // jump past this right-hand side
+    t += ((first_next - t + step - 1) / step) * step;
+  }
+  return t;
+}
+
 template <int L, int C, class T>
 struct ZPipe {
   using TL = Tile<L, C, T>;
@@ -666,13 +687,16 @@ struct ZPipe {
 };
 
 template <class T, int L, int C>
-__device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, cpx<T>* S) {
+__device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
   constexpr int NT = ZPipe<L, C, T>::NT;
   constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;    // 16-byte chunks per row
   const int col_blocks = L / C;
-  const int ky = ky_of_slot(tile / col_blocks, L);
-  const int cb = tile % col_blocks;
-  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + (long long)ky * a.in_outer + (long long)cb * C;
+  const int rhs = tile / per_rhs;
+  const int t = tile - rhs * per_rhs;
+  const int ky = ky_of_slot(t / col_blocks, L);
+  const int cb = t % col_blocks;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(bmove(a.in, a.bs_in * rhs)) + (long long)ky * a.in_outer +
+                      (long long)cb * C;
   const int chunks = a.n_in * PER_ROW;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));             // elements per chunk
   for (int k = threadIdx.x; k < chunks; k += NT) {
@@ -684,13 +708,16 @@ __device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, cpx<T>*
 
 // Stage the n_in input rows of a Z tile (C columns) into S, NT threads.
 template <class T, int L, int C, int NT>
-__device__ __forceinline__ void zpipe_prefetch_rows(const SArgs& a, int tile, cpx<T>* S) {
+__device__ __forceinline__ void zpipe_prefetch_rows(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
   constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));
   const int col_blocks = L / C;
-  const int ky = ky_of_slot(tile / col_blocks, L);
-  const int cb = tile % col_blocks;
-  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + (long long)ky * a.in_outer + (long long)cb * C;
+  const int rhs = tile / per_rhs;
+  const int tl = tile - rhs * per_rhs;
+  const int ky = ky_of_slot(tl / col_blocks, L);
+  const int cb = tl % col_blocks;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(bmove(a.in, a.bs_in * rhs)) + (long long)ky * a.in_outer +
+                      (long long)cb * C;
   const int chunks = a.n_in * PER_ROW;
   for (int k = threadIdx.x; k < chunks; k += NT) {
     const int j = k / PER_ROW, cc = (k - j * PER_ROW) * EPC;
@@ -702,10 +729,12 @@ __device__ __forceinline__ void zpipe_prefetch_rows(const SArgs& a, int tile, cp
 // The spectrum slice of a tile: entries (mz, my(ky), kx) for mz in [0, L/2],
 // kx in the tile, stored contiguously as [mz][C] in the Z-tile order.
 template <class T, int L, int C>
-__device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int ky, int cb, cpx<T>* S) {
+__device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int rhs, int ky, int cb, cpx<T>* S) {
   constexpr int NT = ZPipe<L, C, T>::NT;
   const int my = mirror_index(ky, L);
-  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.ghatZ) + ((long long)my * (L / C) + cb) * (L / 2 + 1) * C;
+  const int g = a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(bmove(a.ghatZ, a.bs_ghatZ * g)) +
+                      ((long long)my * (L / C) + cb) * (L / 2 + 1) * C;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));
   constexpr int chunks = (L / 2 + 1) * C / EPC;
   for (int k = threadIdx.x; k < chunks; k += NT) cp_async16(S + k * EPC, src + k * EPC);
@@ -713,8 +742,7 @@ __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int ky, int 
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a0) {
-  const SArgs a = s_for_rhs(a0, blockIdx.y);
+__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a) {
   using TL = Tile<L, C, T>;
   using ZP = ZPipe<L, C, T>;
   constexpr bool GZ = ZP::GZ;
@@ -724,23 +752,26 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
   cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* S = E + ZP::E_ELEMS;
   cpx<T>* TWS = S + ZP::S_ELEMS;
-  if (a.done != nullptr && *a.done != 0) return;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
   if (GZ) {
     for (int i = threadIdx.x; i < L; i += NT) TWS[i] = twg[i];
   }
   const cpx<T>* tw = GZ ? TWS : twg;
-  const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
   const int col_blocks = L / C;
-  const int ntiles = L * col_blocks;
+  const int per_rhs = L * col_blocks;
+  const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
+  const int step = gridDim.x;
   const int tid = threadIdx.x;
   const int c = tid % C, jl = tid / C;
 
-  int tile = blockIdx.x;
-  if (tile < ntiles) zpipe_prefetch<T, L, C>(a, tile, S);
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int ky = ky_of_slot(tile / col_blocks, L);
-    const int cb = tile % col_blocks;
+  int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
+  if (tile < ntiles) zpipe_prefetch<T, L, C>(a, tile, per_rhs, S);
+  while (tile < ntiles) {
+    const int rhs = tile / per_rhs;
+    const int tl = tile - rhs * per_rhs;
+    const int ky = ky_of_slot(tl / col_blocks, L);
+    const int cb = tl % col_blocks;
+    const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
     cp_async_wait_all();
     __syncthreads();   // staged rows visible; previous tile done with E
     // stage 1: DFT over j1 of rows j1*L2 + j2 (zero padded beyond n_in)
@@ -754,8 +785,8 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
       }
     }
     __syncthreads();   // staging buffer consumed
-    if (GZ) zpipe_prefetch_ghat<T, L, C>(a, ky, cb, S);
-    else if (tile + (int)gridDim.x < ntiles) zpipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
+    if (GZ) zpipe_prefetch_ghat<T, L, C>(a, rhs, ky, cb, S);
+    else if (next < ntiles) zpipe_prefetch<T, L, C>(a, next, per_rhs, S);
     dft<L1, -1, true>(r);
 #pragma unroll
     for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (jl * k1) & (L - 1));
@@ -766,6 +797,8 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
     // stage 2 (DFT over j2), spectrum, inverse stage A (DFT over k2)
     cpx<T> b[NI][L2];
     const int my = mirror_index(ky, L);
+    const cpx<T>* gh = GZ ? nullptr
+                          : reinterpret_cast<const cpx<T>*>(bmove(a.ghat, a.bs_ghat * (a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0)));
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
       const int s = tid + it * NT;
@@ -785,7 +818,7 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
       for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
     }
     __syncthreads();   // forward exchange and the spectrum slice fully read
-    if (GZ && tile + (int)gridDim.x < ntiles) zpipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
+    if (GZ && next < ntiles) zpipe_prefetch<T, L, C>(a, next, per_rhs, S);
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
       const int s = tid + it * NT;
@@ -798,12 +831,13 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) r[k1] = E[c * PCI + jl * PKI + k1];
     dft<L1, +1, false>(r);
-    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)ky * a.out_outer + (long long)cb * C;
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + (long long)ky * a.out_outer + (long long)cb * C;
 #pragma unroll
     for (int jb = 0; jb < L1 / 2; ++jb) {
       const int j = jl + L2 * jb;
       if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
     }
+    tile = next;
   }
   cp_async_wait_all();
 }
@@ -823,8 +857,7 @@ struct ZSmem {
 };
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a0) {
-  const SArgs a = s_for_rhs(a0, blockIdx.y);
+__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a) {
   using ZS = ZSmem<L, C, T>;
   constexpr int NT = ZS::NT;
   constexpr int S8 = L / 8;          // span of the first (and last) radix-8 stage
@@ -832,19 +865,23 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a0) 
   cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* S = X + ZS::X_ELEMS;
   cpx<T>* TW = S + ZS::S_ELEMS;
-  if (a.done != nullptr && *a.done != 0) return;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
   for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
-  const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(a.ghat);
   const int col_blocks = L / C;
-  const int ntiles = L * col_blocks;
+  const int per_rhs = L * col_blocks;
+  const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
+  const int step = gridDim.x;
   const int tid = threadIdx.x;
 
-  int tile = blockIdx.x;
-  if (tile < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, tile, S);
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int ky = ky_of_slot(tile / col_blocks, L);
-    const int cb = tile % col_blocks;
+  int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
+  if (tile < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, tile, per_rhs, S);
+  while (tile < ntiles) {
+    const int rhs = tile / per_rhs;
+    const int tl = tile - rhs * per_rhs;
+    const int ky = ky_of_slot(tl / col_blocks, L);
+    const int cb = tl % col_blocks;
+    const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
+    const cpx<T>* gh = reinterpret_cast<const cpx<T>*>(bmove(a.ghat, a.bs_ghat * (a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0)));
     cp_async_wait_all();
     __syncthreads();
     // first forward stage (M = L): inputs beyond L/2 are the zero padding
@@ -863,7 +900,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a0) 
       for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
     }
     __syncthreads();
-    if (tile + (int)gridDim.x < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, tile + gridDim.x, S);
+    if (next < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, next, per_rhs, S);
     dif_rest<L, C>(X, TW, tid, NT);
     // spectrum: position p holds frequency kz = digit_rev(p)
     const int my = mirror_index(ky, L);
@@ -877,7 +914,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a0) 
     __syncthreads();
     dit_head<L, C>(X, TW, tid, NT);
     // last inverse stage (M = L), keep rows z < n_out
-    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + (long long)ky * a.out_outer + (long long)cb * C;
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + (long long)ky * a.out_outer + (long long)cb * C;
     for (int g = tid; g < C * S8; g += NT) {
       const int c = g % C, j = g / C;
       cpx<T> v[8];
@@ -892,6 +929,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a0) 
         if (z < a.n_out) out[(long long)z * a.out_pt + c] = v[t];
       }
     }
+    tile = next;
   }
   cp_async_wait_all();
 }
@@ -902,10 +940,9 @@ cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
   using ZS = ZSmem<L, C, T>;
   auto kfn = k_zconv_smem<T, L, C>;
   if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZS::SMEM_BYTES));
-  const int ntiles = L * (L / C);
-  const int nb = std::max(1, a.nrhs);
-  const unsigned gx = unsigned(std::max(1, std::min(ntiles, std::max(1, sm_count) / nb)));
-  kfn<<<dim3(gx, unsigned(nb)), ZS::NT, ZS::SMEM_BYTES, s>>>(a);
+  const long long ntiles = (long long)L * (L / C) * std::max(1, a.nrhs);
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count))));
+  kfn<<<gx, ZS::NT, ZS::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -925,12 +962,14 @@ struct YPipe {
 };
 
 template <class T, int L, int C>
-__device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, cpx<T>* S) {
+__device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
   constexpr int NT = YPipe<L, C, T>::NT;
   constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));
-  const int outer = tile / a.col_blocks, cb = tile - outer * a.col_blocks;
-  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(a.in) + outer * a.in_outer + (long long)cb * C;
+  const int rhs = tile / per_rhs;
+  const int tl = tile - rhs * per_rhs;
+  const int outer = tl / a.col_blocks, cb = tl - outer * a.col_blocks;
+  const cpx<T>* src = reinterpret_cast<const cpx<T>*>(bmove(a.in, a.bs_in * rhs)) + outer * a.in_outer + (long long)cb * C;
   const int chunks = a.n_in * PER_ROW;
   for (int k = threadIdx.x; k < chunks; k += NT) {
     const int j = k / PER_ROW, cc = (k - j * PER_ROW) * EPC;
@@ -940,8 +979,7 @@ __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, cpx<T>*
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT)) k_yfwd_pipe(SArgs a0) {
-  const SArgs a = s_for_rhs(a0, blockIdx.y);
+__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT)) k_yfwd_pipe(SArgs a) {
   using TL = Tile<L, C, T>;
   using YP = YPipe<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
@@ -950,16 +988,20 @@ __global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256
   cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* S = E + YP::E_ELEMS;
   cpx<T>* TW = S + YP::S_ELEMS;
-  if (a.done != nullptr && *a.done != 0) return;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
   for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
-  const int ntiles = a.nouter * a.col_blocks;
+  const int per_rhs = a.nouter * a.col_blocks;
+  const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
+  const int step = gridDim.x;
   const int tid = threadIdx.x;
   const int c = tid % C, jl = tid / C;
-  int tile = blockIdx.x;
-  if (tile < ntiles) ypipe_prefetch<T, L, C>(a, tile, S);
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int outer = tile / a.col_blocks, cb = tile - outer * a.col_blocks;
+  int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
+  if (tile < ntiles) ypipe_prefetch<T, L, C>(a, tile, per_rhs, S);
+  while (tile < ntiles) {
+    const int rhs = tile / per_rhs;
+    const int tl = tile - rhs * per_rhs;
+    const int outer = tl / a.col_blocks, cb = tl - outer * a.col_blocks;
+    const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
     cp_async_wait_all();
     __syncthreads();
     cpx<T> r[L1];
@@ -972,14 +1014,14 @@ __global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256
       }
     }
     __syncthreads();
-    if (tile + (int)gridDim.x < ntiles) ypipe_prefetch<T, L, C>(a, tile + gridDim.x, S);
+    if (next < ntiles) ypipe_prefetch<T, L, C>(a, next, per_rhs, S);
     dft<L1, -1, true>(r);
 #pragma unroll
     for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], TW, (jl * k1) & (L - 1));
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
     __syncthreads();
-    cpx<T>* out = reinterpret_cast<cpx<T>*>(a.out) + outer * a.out_outer + (long long)cb * C;
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + outer * a.out_outer + (long long)cb * C;
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
       const int sidx2 = tid + it * NT;
@@ -994,6 +1036,7 @@ __global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256
         if (k < a.n_out) out[(long long)k * a.out_pt + c2] = b[k2];
       }
     }
+    tile = next;
   }
   cp_async_wait_all();
 }
@@ -1013,10 +1056,10 @@ cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
     return e;
   }
   a.col_blocks = (a.ncols + C - 1) / C;
-  const int ntiles = a.nouter * a.col_blocks;
-  const int nb = std::max(1, a.nrhs);
-  const unsigned gx = unsigned(std::max(1, std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm) / nb)));
-  kfn<<<dim3(gx, unsigned(nb)), YP::NT, YP::SMEM_BYTES, s>>>(a);
+  const long long ntiles = (long long)a.nouter * a.col_blocks * std::max(1, a.nrhs);
+  const int resident = a.cta_cap > 0 ? std::min(std::max(1, per_sm), a.cta_cap) : std::max(1, per_sm);
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count) * resident)));
+  kfn<<<gx, YP::NT, YP::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1034,21 +1077,34 @@ cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
     per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
     return e;
   }
-  const int ntiles = L * (L / C);
-  const int nb = std::max(1, a.nrhs);
-  const unsigned gx = unsigned(std::max(1, std::min(ntiles, std::max(1, sm_count) * std::max(1, per_sm) / nb)));
-  kfn<<<dim3(gx, unsigned(nb)), ZP::NT, ZP::SMEM_BYTES, s>>>(a);
+  const long long ntiles = (long long)L * (L / C) * std::max(1, a.nrhs);
+  const int resident = a.cta_cap > 0 ? std::min(std::max(1, per_sm), a.cta_cap) : std::max(1, per_sm);
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count) * resident)));
+  kfn<<<gx, ZP::NT, ZP::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 // Z-pass kernel choice for L >= 64: the shared-memory radix-8 kernel for
-// paired FP32, the pipelined register kernel for FP32 and FP64; the plain
+// paired FP32; for FP32 the pipelined persistent kernel or, by schedule, the
+// one-CTA-per-tile strided kernel; the pipelined kernel for FP64; the plain
 // strided kernel for small L.
 template <class T, int L>
 cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
-  if constexpr (L >= 64 && std::is_same<T, dfl>::value) return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
-  else if constexpr (L >= 64) return launch_zconv_pipe_L<T, L>(a, s, setup, a.sm_count);
-  else return launch_strided_L<T, L, SMODE_ZCONV, true>(a, s, setup);
+  if constexpr (L >= 64 && std::is_same<T, dfl>::value) {
+    return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
+  } else if constexpr (L >= 64 && sizeof(T) == 4) {
+    if (setup) {
+      cudaError_t e = launch_zconv_pipe_L<T, L>(a, s, true, a.sm_count);
+      if (e != cudaSuccess) return e;
+      return launch_strided_L<T, L, SMODE_ZCONV, true>(a, s, true);
+    }
+    if (a.sched == SCHED_TILES) return launch_strided_L<T, L, SMODE_ZCONV, true>(a, s, false);
+    return launch_zconv_pipe_L<T, L>(a, s, false, a.sm_count);
+  } else if constexpr (L >= 64) {
+    return launch_zconv_pipe_L<T, L>(a, s, setup, a.sm_count);
+  } else {
+    return launch_strided_L<T, L, SMODE_ZCONV, true>(a, s, setup);
+  }
 }
 
 #define ORI_FOR_EACH_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)

@@ -139,6 +139,33 @@ class Plan:
     def reset_stats(self):
         _lib.check(_lib.load().ori_plan_reset_stats(self.handle), "ori_plan_reset_stats")
 
+    # -- launch schedule -------------------------------------------------------
+    def schedule(self) -> dict:
+        sc = _lib.Schedule()
+        _lib.check(_lib.load().ori_plan_get_schedule(self.handle, C.byref(sc)), "ori_plan_get_schedule")
+        return sc.as_dict()
+
+    def set_schedule(self, schedule: dict):
+        sc = _lib.Schedule.from_dict(schedule)
+        _lib.check(_lib.load().ori_plan_set_schedule(self.handle, C.byref(sc)), "ori_plan_set_schedule")
+
+    def autotune_now(self, nrhs: int = 1, reps: int = 3, stream=None):
+        """Time the candidate schedules for a batch of nrhs systems and keep the
+        fastest; returns (schedule dict, FP32 operator ms for the batch)."""
+        sc = _lib.Schedule()
+        ms = C.c_float()
+        with torch.cuda.device(self.device):
+            st = _lib.load().ori_plan_autotune(self.handle, int(nrhs), int(reps), C.byref(sc), C.byref(ms),
+                                               _stream_ptr(stream))
+        _lib.check(st, "ori_plan_autotune")
+        return sc.as_dict(), float(ms.value)
+
+    def autotune(self, nrhs: int = 1, path: str | None = None, reps: int = 3, force: bool = False) -> dict:
+        """Schedule for this GPU, n and batch size from the JSON cache, else timed and cached."""
+        from . import autotune as _at
+        name = torch.cuda.get_device_name(self.device)
+        return _at.tune(self, nrhs, name, path=path, reps=reps, force=force)
+
     # -- medium ----------------------------------------------------------------
     def set_medium(self, h: torch.Tensor, N: torch.Tensor, stream=None):
         m = self.n ** 3

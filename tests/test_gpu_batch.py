@@ -168,3 +168,47 @@ def test_batch_16_directions_4_wave_numbers_n128():
         us, _ = single.solve(tol=1e-9, precision="fp64", alpha=tuple(dirs[j]))
         assert rel(u[i, j].cpu().numpy(), us.cpu().numpy()) < 1e-5, (i, j)
         single.close()
+
+
+def test_every_schedule_matches_oracle_and_autotune_caches(tmp_path):
+    """Each launch schedule of the FP32 passes gives the FP32 operator within
+    its tolerance of the oracle's direct sum and a batch that meets tol; the
+    autotuner keeps one of them and a second call reads it from the cache."""
+    n, ks = 24, [2.0, 3.0]                    # L = 64: both kernels exist per pass
+    h, N = inputs.random_h_N(n, 96)
+    x = inputs.random_complex(n ** 3, 97)
+    ref = O.red_matvec_direct(x, n, ks[0], h, N)
+    plan = make_plan(n, ks, h, N)
+    default = plan.schedule()
+    assert default == {"yfwd": 0, "zconv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8}
+    dirs = [(0.0, 0.0, 1.0), (0.6, 0.8, 0.0)]
+    for y in (0, 1):
+        for z in (0, 1):
+            for cap, vec in ((0, 8), (1, 4), (2, 16)):
+                plan.set_schedule({"yfwd": y, "zconv": z, "ctas_per_sm": cap, "vec_ctas_per_sm": vec})
+                y32 = plan.matvec(to_dev(x), form="A", precision="fp32").cpu().numpy()
+                assert rel(y32, ref) < 1e-5, (y, z, cap)
+                _, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+                assert all(i["status"] == 0 and i["relres"] <= 1e-6 for i in infos)
+    path = str(tmp_path / "tune.json")
+    r1 = plan.autotune(nrhs=4, path=path)
+    assert not r1["cached"] and r1["ms"] > 0
+    assert plan.schedule() == r1["schedule"]
+    other = make_plan(n, ks, h, N)
+    r2 = other.autotune(nrhs=4, path=path)
+    assert r2["cached"] and other.schedule() == r1["schedule"]
+    u, infos = other.solve_batch(dirs, tol=1e-6, precision="mixed")
+    assert all(i["relres"] <= 1e-6 for i in infos)
+
+
+def test_set_schedule_rejects_bad_fields():
+    from paper_1602_04691_gb300 import OriError
+    n = 8
+    h, N = inputs.random_h_N(n, 98)
+    plan = make_plan(n, 1.0, h, N)
+    for bad in ({"yfwd": 2, "zconv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8},
+                {"yfwd": 0, "zconv": 0, "ctas_per_sm": -1, "vec_ctas_per_sm": 8},
+                {"yfwd": 0, "zconv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 17}):
+        with pytest.raises(OriError):
+            plan.set_schedule(bad)
+    assert plan.schedule()["vec_ctas_per_sm"] == 8
