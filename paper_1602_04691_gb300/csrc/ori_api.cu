@@ -372,7 +372,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   int e0 = t_rec(p, s), e1;
   pro.n = n; pro.nlines = n * n; pro.n_in = n; pro.line_len_in = n; pro.line_len_out = L;
   pro.fft_out = T1; pro.twL = tw; pro.done = mask.flags; pro.done_stride = mask.stride;
-  pro.nrhs = nrhs; pro.bs_fft = bsT1; pro.bs_beta = sizeof(Scalars);
+  pro.nrhs = nrhs; pro.bs_fft = bsT1; pro.bs_beta = sizeof(Scalars); pro.sm_count = p->sm_count;
   ORI_CUDA(run_xfwd<T>(L, true, pro, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_XFWD + K, e0, e1); e0 = e1;
@@ -416,7 +416,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
 
   epi.n = n; epi.nlines = n * n; epi.line_len_in = L; epi.line_len_out = n;
   epi.in = T1; epi.twL = tw; epi.done = mask.flags; epi.done_stride = mask.stride;
-  epi.partials = p->partials; epi.nrhs = nrhs; epi.bs_fft = bsT1;
+  epi.partials = p->partials; epi.nrhs = nrhs; epi.bs_fft = bsT1; epi.sm_count = p->sm_count;
   ORI_CUDA(run_xinv<T>(L, epi, p->sc, fin, s, false, nullptr));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_XINV + K, e0, e1);
@@ -443,9 +443,10 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
 static int vgrid(const ori_plan_s* p, int nrhs) { return std::max(16, p->vec_grid / std::max(1, nrhs)); }
 
 template <class T>
-static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n) {
+static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n, int sm_count) {
   XArgs a{};
   a.nlines = n * n;
+  a.sm_count = sm_count;
   ORI_CUDA(run_xfwd<T>(L, true, a, nullptr, true));
   ORI_CUDA(run_xfwd<T>(L, false, a, nullptr, true));
   ORI_CUDA(run_xinv<T>(L, a, nullptr, FIN_NONE, nullptr, true, xinv_blocks));
@@ -639,8 +640,9 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
         (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)))
       break;
     unsigned bx32 = 0, bx64 = 0, bxdf = 0;
-    if ((st = setup_kernels<float>(p->L, &bx32, p->n)) || (st = setup_kernels<double>(p->L, &bx64, p->n)) ||
-        (st = setup_kernels<dfl>(p->L, &bxdf, p->n)))
+    if ((st = setup_kernels<float>(p->L, &bx32, p->n, p->sm_count)) ||
+        (st = setup_kernels<double>(p->L, &bx64, p->n, p->sm_count)) ||
+        (st = setup_kernels<dfl>(p->L, &bxdf, p->n, p->sm_count)))
       break;
     p->xinv_blocks = std::max({bx32, bx64, bxdf});
     if ((st = ensure_capacity(p, 1))) break;

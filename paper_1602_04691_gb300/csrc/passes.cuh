@@ -88,6 +88,7 @@ struct XArgs {
   int done_stride;      // bytes between the flags of consecutive RHS
   const double* coefs;  // EPI_RUPDATE: per-RHS coefficient (overrides coef when set)
   int nrhs;             // right-hand sides in the batch (gridDim.y)
+  int sm_count;         // persistent kernels: SMs of the device
 };
 
 struct SArgs {

@@ -11,6 +11,28 @@
 
 namespace ori {
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only) and their group fences.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Lines per CTA of the FP32 contiguous (X) passes: 256 threads of L2 each.
+template <int L>
+constexpr int lines_contig_f32() {
+  constexpr int want = 256 / Split<L>::L2;
+  return want < 1 ? 1 : want;
+}
+
+// Lines per tile of the persistent FP32 X passes: 128 threads of L2 each.
+template <int L>
+constexpr int xpipe_cols() {
+  constexpr int c = lines_contig_f32<L>() / 2;
+  return c < 1 ? 1 : c;
+}
+
 // ---------------------------------------------------------------------------
 // Prologue of the X forward pass: the value of the (zero-padded) field that
 // enters the transform at cell (line, j) with j < n.
@@ -120,6 +142,118 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xfwd
       for (int k2 = 0; k2 < L2; ++k2) o[k1 + L1 * k2] = b[k2];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// X forward pass, persistent and pipelined (FP32; prologues PRO_SCALE,
+// PRO_COCG_FIRST and PRO_COCG, n even).  A tile is C consecutive lines,
+// whose n input points per line form one contiguous block of each streamed
+// vector (x or r, p for PRO_COCG, and the scale s); cp.async stages the
+// blocks in shared memory, and the next tile's blocks are requested as soon
+// as the prologue has read the current ones, so they stream in during the
+// two DFT stages.
+// ---------------------------------------------------------------------------
+
+template <int L, int C>
+struct XFwdPipe {
+  using TL = Tile<L, C, float>;
+  static constexpr int NT = TL::NT;
+  static constexpr int STAGE = 3 * C * (L / 2);     // x or r, p, s: C lines of at most L/2 points each
+  static constexpr size_t SMEM_BYTES = size_t(TL::SMEM_ELEMS + STAGE) * sizeof(cpx<float>);
+};
+
+template <int L, int C>
+__device__ __forceinline__ void xfwd_prefetch(const XArgs& a, int tile, cpx<float>* R, cpx<float>* P, cpx<float>* G) {
+  constexpr int NT = XFwdPipe<L, C>::NT;
+  const long long line0 = (long long)tile * C;
+  const long long left = a.nlines - line0;
+  const int lines = left < C ? int(left) : C;
+  const long long off = line0 * a.n;
+  const int chunks = lines * a.n / 2;             // n even: 16 bytes = two complex values
+  const cpx<float>* xs = reinterpret_cast<const cpx<float>*>(a.x) + off;
+  const cpx<float>* ss = reinterpret_cast<const cpx<float>*>(a.scale) + off;
+  for (int k = threadIdx.x; k < chunks; k += NT) {
+    cp_async16(R + 2 * k, xs + 2 * k);
+    cp_async16(G + 2 * k, ss + 2 * k);
+  }
+  if (a.mode == PRO_COCG) {
+    const cpx<float>* ps = reinterpret_cast<const cpx<float>*>(a.p) + off;
+    for (int k = threadIdx.x; k < chunks; k += NT) cp_async16(P + 2 * k, ps + 2 * k);
+  }
+  cp_async_commit();
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(XFwdPipe<L, C>::NT, 2) k_xfwd_pipe(XArgs a0) {
+  using T = float;
+  const XArgs a = x_for_rhs(a0, blockIdx.y);
+  using TL = Tile<L, C, T>;
+  using XP = XFwdPipe<L, C>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT;
+  constexpr int PK = TL::PK, PC = TL::PC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* R = E + TL::SMEM_ELEMS;
+  cpx<T>* P = R + XP::STAGE / 3;
+  cpx<T>* G = P + XP::STAGE / 3;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const int tid = threadIdx.x;
+  const int ntiles = int((a.nlines + C - 1) / C);
+  const cpx<T> beta = x_beta<T>(a);
+  int c, j2;
+  map_t<LAYOUT_CONTIG, C, L2>(tid, c, j2);
+  cpx<T>* out = reinterpret_cast<cpx<T>*>(a.fft_out);
+  int tile = blockIdx.x;
+  if (tile < ntiles) xfwd_prefetch<L, C>(a, tile, R, P, G);
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_async_wait_all();
+    __syncthreads();
+    const long long line = (long long)tile * C + c;
+    const bool ok = line < a.nlines;
+    cpx<T> r[L1];
+#pragma unroll
+    for (int j1 = 0; j1 < L1; ++j1) {
+      r[j1] = czero<T>();
+      const int j = j1 * L2 + j2;
+      if (j1 < L1 / 2 && ok && j < a.n) {
+        const long long i = line * a.n + j;
+        const cpx<T> s = G[c * a.n + j];
+        cpx<T> v = R[c * a.n + j];
+        if (a.mode == PRO_COCG) {
+          v = v + cmul(beta, P[c * a.n + j]);
+          reinterpret_cast<cpx<T>*>(a.p)[i] = v;
+        } else if (a.mode == PRO_COCG_FIRST) {
+          reinterpret_cast<cpx<T>*>(a.p)[i] = v;
+        }
+        r[j1] = cmul(s, v);
+      }
+    }
+    __syncthreads();   // staged inputs consumed: request the next tile
+    if (tile + (int)gridDim.x < ntiles) xfwd_prefetch<L, C>(a, tile + gridDim.x, R, P, G);
+    dft<L1, -1, true>(r);
+#pragma unroll
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + j2] = r[k1];
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < L1 / L2; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_CONTIG, C, L1>(tid + it * NT, c2, k1);
+      cpx<T> b[L2];
+#pragma unroll
+      for (int j = 0; j < L2; ++j) b[j] = E[c2 * PC + k1 * PK + j];
+      dft<L2, -1, false>(b);
+      const long long l2 = (long long)tile * C + c2;
+      if (l2 < a.nlines) {
+        cpx<T>* o = out + l2 * a.line_len_out;
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) o[k1 + L1 * k2] = b[k2];
+      }
+    }
+  }
+  cp_async_wait_all();
 }
 
 // Operator epilogue at cell i (conv value v): see EPI_* in passes.cuh.
@@ -265,6 +399,173 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv
   }
   double2* parts = a.partials + (long long)blockIdx.y * gridDim.x;
   if (!done_partial) block_partial(acc, red, parts);
+  if (last_block_arrives(sc, s_last)) finalize(sc, parts, gridDim.x, fin, red);
+}
+
+// ---------------------------------------------------------------------------
+// X inverse pass, persistent and pipelined (FP32).  A CTA loops over tiles
+// of C consecutive lines; a tile's L points per line (one contiguous block
+// of C L complex values) are staged in shared memory with cp.async, the
+// exchange between the two DFT stages reuses that buffer in place, and as
+// soon as the second stage has read the exchange the next tile starts
+// streaming in, overlapping the inverse DFT and the epilogue.
+// ---------------------------------------------------------------------------
+template <int L, int C>
+struct XInvPipe {
+  using TL = Tile<L, C, float>;
+  static constexpr int NT = TL::NT;
+  static constexpr int BUF = (C * L > TL::SMEM_ELEMS) ? C * L : TL::SMEM_ELEMS;
+  static constexpr int EPI = 2 * C * (L / 2);       // epilogue inputs: xin and s, C lines of <= L/2
+  static constexpr size_t SMEM_BYTES = size_t(BUF + EPI) * sizeof(cpx<float>);
+};
+
+// The epilogue's complex64 inputs of a tile (xin and the scale s, n points
+// per line) when every epilogue reads exactly those: the FP32 operator forms.
+inline __host__ __device__ bool xinv_stage_epi(int mode) {
+  return mode == EPI_COCG || mode == EPI_PLUS_S;
+}
+
+template <int L, int C>
+__device__ __forceinline__ void xinv_prefetch_epi(const XArgs& a, int tile, cpx<float>* X, cpx<float>* G) {
+  constexpr int NT = XInvPipe<L, C>::NT;
+  if (xinv_stage_epi(a.mode)) {
+    const long long line0 = (long long)tile * C;
+    const long long left = a.nlines - line0;
+    const int lines = left < C ? int(left) : C;
+    const long long off = line0 * a.n;
+    const int chunks = lines * a.n / 2;
+    const cpx<float>* xs = reinterpret_cast<const cpx<float>*>(a.xin) + off;
+    const cpx<float>* ss = reinterpret_cast<const cpx<float>*>(a.scale) + off;
+    for (int k = threadIdx.x; k < chunks; k += NT) {
+      cp_async16(X + 2 * k, xs + 2 * k);
+      cp_async16(G + 2 * k, ss + 2 * k);
+    }
+  }
+  cp_async_commit();   // always one group, so that the group count stays fixed
+}
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+
+template <int L, int C>
+__device__ __forceinline__ void xinv_prefetch(const XArgs& a, int tile, cpx<float>* B) {
+  constexpr int NT = XInvPipe<L, C>::NT;
+  const long long line0 = (long long)tile * C;
+  const long long left = a.nlines - line0;
+  const int lines = left < C ? int(left) : C;
+  const cpx<float>* src = reinterpret_cast<const cpx<float>*>(a.in) + line0 * L;
+  const int chunks = lines * (L / 2);          // 16 bytes = two complex values
+  for (int k = threadIdx.x; k < chunks; k += NT) cp_async16(B + 2 * k, src + 2 * k);
+  cp_async_commit();
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(XInvPipe<L, C>::NT, 3) k_xinv_pipe(XArgs a0, Scalars* sc0, int fin) {
+  using T = float;
+  const XArgs a = x_for_rhs(a0, blockIdx.y);
+  Scalars* sc = sc0 == nullptr ? nullptr : sc0 + blockIdx.y;
+  using TL = Tile<L, C, T>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
+  constexpr int PKI = TL::PKI, PCI = TL::PCI;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* B = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* XI = B + XInvPipe<L, C>::BUF;
+  cpx<T>* GI = XI + XInvPipe<L, C>::EPI / 2;
+  __shared__ double2 red[32];
+  __shared__ int s_last;
+  if (a.done != nullptr && *a.done != 0) return;
+  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  const int tid = threadIdx.x;
+  const int ntiles = int((a.nlines + C - 1) / C);
+  const bool staged = xinv_stage_epi(a.mode) && (a.n % 2 == 0);
+  int c, ja;
+  map_t<LAYOUT_CONTIG, C, L2>(tid, c, ja);
+  double2 acc = make_double2(0.0, 0.0);
+  cpx<T> accT = czero<T>();
+  int tile = blockIdx.x;
+  // groups in flight, oldest first: [T1 of this tile] [epilogue inputs of this tile] [T1 of the next]
+  if (tile < ntiles) {
+    xinv_prefetch<L, C>(a, tile, B);
+    if (staged) xinv_prefetch_epi<L, C>(a, tile, XI, GI);
+    else cp_async_commit();
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_async_wait_1();   // this tile's T1 block has landed
+    __syncthreads();
+    // stage A: DFT over k2 of X[k1 + L1 k2], twiddle
+    cpx<T> b[NI][L2];
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_CONTIG, C, L1>(tid + it * NT, c2, k1);
+      const bool okl = (long long)tile * C + c2 < a.nlines;
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) b[it][k2] = okl ? B[c2 * L + k1 + L1 * k2] : czero<T>();
+      dft<L2, +1, false>(b[it]);
+#pragma unroll
+      for (int j = 1; j < L2; ++j) b[it][j] = twL_mul<+1>(b[it][j], tw, (j * k1) & (L - 1));
+    }
+    __syncthreads();   // raw tile consumed: the exchange reuses the buffer
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_CONTIG, C, L1>(tid + it * NT, c2, k1);
+#pragma unroll
+      for (int j = 0; j < L2; ++j) B[c2 * PCI + j * PKI + k1] = b[it][j];
+    }
+    __syncthreads();
+    // stage B: DFT over k1 -> x = ja + L2 jb
+    cpx<T> r[L1];
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) r[k1] = B[c * PCI + ja * PKI + k1];
+    __syncthreads();   // exchange consumed: the buffer takes the next tile
+    if (tile + (int)gridDim.x < ntiles) xinv_prefetch<L, C>(a, tile + gridDim.x, B);
+    else cp_async_commit();
+    dft<L1, +1, false>(r);
+    cp_async_wait_1();   // this tile's epilogue inputs have landed
+    __syncthreads();
+    const long long line = (long long)tile * C + c;
+    if (line < a.nlines) {
+      if (staged) {
+        cpx<T>* q = reinterpret_cast<cpx<T>*>(a.out);
+#pragma unroll
+        for (int jb = 0; jb < L1 / 2; ++jb) {
+          const int x = ja + L2 * jb;
+          if (x < a.n) {
+            const cpx<T> pv = XI[c * a.n + x];
+            const cpx<T> qv = pv + cmul(GI[c * a.n + x], r[jb]);
+            q[line * a.n + x] = qv;
+            if (a.mode == EPI_COCG) accT = accT + cmul(pv, qv);   // p^T q, no conjugate
+          }
+        }
+      } else {
+#pragma unroll
+        for (int jb = 0; jb < L1 / 2; ++jb) {
+          const int x = ja + L2 * jb;
+          if (x < a.n) x_epilogue<T>(a, line * a.n + x, r[jb], accT, acc);
+        }
+      }
+    }
+    __syncthreads();   // epilogue inputs consumed
+    if (tile + (int)gridDim.x < ntiles) {
+      if (staged) xinv_prefetch_epi<L, C>(a, tile + gridDim.x, XI, GI);
+      else cp_async_commit();
+    }
+  }
+  cp_async_wait_all();
+  if (fin == FIN_NONE) return;
+  double2* parts = a.partials + (long long)blockIdx.y * gridDim.x;
+  if (a.mode == EPI_COCG) {
+    // FP32 sums (p^T q): reduce across the warp in FP32, widen once per warp
+    float ax = accT.x, ay = accT.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ax += __shfl_xor_sync(0xffffffffu, ax, o);
+      ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    block_partial_lane0(make_double2(double(ax), double(ay)), red, parts);
+  } else {
+    block_partial(acc, red, parts);
+  }
   if (last_block_arrives(sc, s_last)) finalize(sc, parts, gridDim.x, fin, red);
 }
 
@@ -564,8 +865,45 @@ template <class T, int L> constexpr int lines_contig() {
   return want < 1 ? 1 : want;
 }
 
+template <int L>
+cudaError_t launch_xfwd_pipe_L(const XArgs& a, cudaStream_t s, bool setup) {
+  constexpr int C = xpipe_cols<L>();
+  using XP = XFwdPipe<L, C>;
+  auto kfn = k_xfwd_pipe<L, C>;
+  static int per_sm = 0;
+  if (setup) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(XP::SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, XP::NT, XP::SMEM_BYTES);
+    per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
+    return e;
+  }
+  const long long ntiles = (a.nlines + C - 1) / C;
+  const int nb = std::max(1, a.nrhs);
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, a.sm_count) * std::max(1, per_sm) / nb)));
+  kfn<<<dim3(gx, unsigned(nb)), XP::NT, XP::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The pipelined kernel serves the solver's prologues on whole contiguous lines
+// of even length; the plan's kernel cube and the mixed-arithmetic prologue
+// take the one-tile-per-CTA kernel.
+inline bool xfwd_pipe_ok(const XArgs& a, int L) {
+  return (a.mode == PRO_SCALE || a.mode == PRO_COCG_FIRST || a.mode == PRO_COCG) && a.n % 2 == 0 &&
+         a.n_in == a.n && a.line_len_in == a.n && a.line_len_out == L && 2 * a.n <= L;
+}
+
 template <class T, int L, bool HALF>
 cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
+  if constexpr (sizeof(T) == 4 && HALF && L >= 64) {
+    if (setup) {
+      cudaError_t e = launch_xfwd_pipe_L<L>(a, s, true);
+      if (e != cudaSuccess) return e;
+    } else if (xfwd_pipe_ok(a, L)) {
+      return launch_xfwd_pipe_L<L>(a, s, false);
+    }
+  }
   if constexpr (std::is_same<T, dfl>::value && HALF && L >= 64) {
     constexpr int CS = 4;
     using LS = LSmem<L, CS, T>;
@@ -583,9 +921,35 @@ cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
   return cudaGetLastError();
 }
 
+template <int L>
+cudaError_t launch_xinv_pipe_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
+  constexpr int C = xpipe_cols<L>();
+  using XP = XInvPipe<L, C>;
+  auto kfn = k_xinv_pipe<L, C>;
+  static int per_sm = 0;   // resident CTAs per SM, measured once at set-up
+  const long long ntiles = (a.nlines + C - 1) / C;
+  if (setup) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(XP::SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, XP::NT, XP::SMEM_BYTES);
+    per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
+    if (nblocks) *nblocks = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, a.sm_count) * per_sm)));
+    return e;
+  }
+  if (a.line_len_in != L) return cudaErrorInvalidValue;   // tiles are contiguous blocks of whole lines
+  const int nb = std::max(1, a.nrhs);
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, a.sm_count) * std::max(1, per_sm) / nb)));
+  if (nblocks) *nblocks = gx;
+  kfn<<<dim3(gx, unsigned(nb)), XP::NT, XP::SMEM_BYTES, s>>>(a, sc, fin);
+  return cudaGetLastError();
+}
+
 template <class T, int L>
 cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
-  if constexpr (std::is_same<T, dfl>::value && L >= 64) {
+  if constexpr (sizeof(T) == 4 && L >= 64) {
+    return launch_xinv_pipe_L<L>(a, sc, fin, s, setup, nblocks);
+  } else if constexpr (std::is_same<T, dfl>::value && L >= 64) {
     constexpr int CS = 4;
     using LS = LSmem<L, CS, T>;
     auto kfs = k_xinv_smem<T, L, CS>;
@@ -594,15 +958,16 @@ cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, 
     if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
     kfs<<<dim3(grid, unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a, sc, fin);
     return cudaGetLastError();
+  } else {
+    constexpr int C = lines_contig<T, L>();
+    using TL = Tile<L, C, T>;
+    auto kfn = k_xinv<T, L, C>;
+    const unsigned grid = unsigned((a.nlines + C - 1) / C);
+    if (nblocks) *nblocks = grid;
+    if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
+    kfn<<<dim3(grid, unsigned(std::max(1, a.nrhs))), TL::NT, TL::SMEM_BYTES, s>>>(a, sc, fin);
+    return cudaGetLastError();
   }
-  constexpr int C = lines_contig<T, L>();
-  using TL = Tile<L, C, T>;
-  auto kfn = k_xinv<T, L, C>;
-  const unsigned grid = unsigned((a.nlines + C - 1) / C);
-  if (nblocks) *nblocks = grid;
-  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TL::SMEM_BYTES));
-  kfn<<<dim3(grid, unsigned(std::max(1, a.nrhs))), TL::NT, TL::SMEM_BYTES, s>>>(a, sc, fin);
-  return cudaGetLastError();
 }
 
 template <class T, int L>
@@ -646,12 +1011,6 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
 // L - ky, which read the same spectrum entries, run at the same time and
 // the second read hits L2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int ky_of_slot(int i, int L) {
   if (i == 0) return 0;
