@@ -286,7 +286,7 @@ ori_status ori_adjoint_solve(ori_plan_t plan, const double* u_dev,
                              ori_solve_info* info, void* stream);
 
 /*
- * Launch schedules.  The FP32 Y-forward and Z passes (L >= 64) each have two
+ * Launch schedules.  The FP32 Y-forward, Z and Y-inverse passes (L >= 64) each have two
  * kernels: a persistent one that streams the next tile into shared memory
  * with cp.async while it transforms the current one, and one CTA per tile of
  * columns.  Which is faster depends on n, the batch size and the GPU; so does
@@ -303,7 +303,8 @@ typedef struct {
                            0 (default) = as many as fit, else at most this many    */
   int vec_ctas_per_sm;  /* vector kernels (updates, norms): CTAs per SM, 1..16;
                            0 -> 8 (default)                                        */
-  int reserved[4];
+  int yinv;             /* FP32 Y inverse pass                                     */
+  int reserved[3];
 } ori_schedule;
 
 /* The plan's current schedule. */
@@ -315,11 +316,12 @@ ori_status ori_plan_set_schedule(ori_plan_t plan, const ori_schedule* s);
 
 /*
  * ori_plan_autotune - time the candidate schedules on this plan for a batch of
- * nrhs systems (1..4096) and keep the fastest.  Each candidate pair of FP32
- * Y-forward / Z kernels (with the persistent CTA cap 0 or 1) is timed over
+ * nrhs systems (1..4096) and keep the fastest.  Starting from the plan's
+ * schedule, each field in turn (Y-forward, Z and Y-inverse kernels, then the
+ * persistent CTA cap 1 or 2) takes the alternative that lowers the time of
  * `reps` (1..100) FP32 operator applications y = B x on the plan's scratch
- * vectors after one warm-up; then the vector grid (4, 8 or 16 CTAs per SM) is
- * timed on the FP32 COCG update.  Grows the plan's batch scratch to nrhs like
+ * vectors (each timing after one warm-up); then the vector grid (4, 8 or 16
+ * CTAs per SM) is timed on the FP32 COCG update.  Grows the plan's batch scratch to nrhs like
  * ori_cocg_solve_batch; overwrites the scratch vectors (not the medium or
  * spectra); leaves ori_plan_stats unchanged.  *best (may be NULL) receives the
  * chosen schedule, *best_ms (may be NULL) its operator time for the whole

@@ -73,11 +73,11 @@ class SolveInfo(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("yfwd", C.c_int), ("zconv", C.c_int), ("ctas_per_sm", C.c_int),
-                ("vec_ctas_per_sm", C.c_int), ("reserved", C.c_int * 4)]
+                ("vec_ctas_per_sm", C.c_int), ("yinv", C.c_int), ("reserved", C.c_int * 3)]
 
     def as_dict(self):
-        return {"yfwd": int(self.yfwd), "zconv": int(self.zconv), "ctas_per_sm": int(self.ctas_per_sm),
-                "vec_ctas_per_sm": int(self.vec_ctas_per_sm)}
+        return {"yfwd": int(self.yfwd), "zconv": int(self.zconv), "yinv": int(self.yinv),
+                "ctas_per_sm": int(self.ctas_per_sm), "vec_ctas_per_sm": int(self.vec_ctas_per_sm)}
 
     @classmethod
     def from_dict(cls, d):
@@ -86,6 +86,7 @@ class Schedule(C.Structure):
         s.zconv = int(d["zconv"])
         s.ctas_per_sm = int(d["ctas_per_sm"])
         s.vec_ctas_per_sm = int(d["vec_ctas_per_sm"])
+        s.yinv = int(d.get("yinv", 0))
         return s
 
 

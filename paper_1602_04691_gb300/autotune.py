@@ -62,7 +62,7 @@ def store(path: str, key: str, schedule: dict, ms: float) -> None:
         raise
 
 
-_FIELDS = ("yfwd", "zconv", "ctas_per_sm", "vec_ctas_per_sm")
+_FIELDS = ("yfwd", "zconv", "yinv", "ctas_per_sm", "vec_ctas_per_sm")
 
 
 def valid_schedule(s) -> bool:

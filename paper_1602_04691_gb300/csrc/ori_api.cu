@@ -124,7 +124,7 @@ struct ori_plan_s {
   bool graph_f_timed = false, graph_d_timed = false;
   int vec_grid = 0;
   // launch schedule (ori_schedule): FP32 Y-forward / Z kernels, CTA cap, vector grid
-  int sched_y = SCHED_PERSISTENT, sched_z = SCHED_PERSISTENT, cta_cap = 0, vec_ctas = 8;
+  int sched_y = SCHED_PERSISTENT, sched_z = SCHED_PERSISTENT, sched_yi = SCHED_PERSISTENT, cta_cap = 0, vec_ctas = 8;
   // accounting (ori_plan_stats) and optional per-kernel event timing
   ori_plan_stats stats{};
   bool capturing = false;
@@ -410,6 +410,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   yi.in_pt = L; yi.out_pt = L; yi.ncols = L; yi.n_in = L; yi.n_out = n; yi.nouter = n;
   yi.twL = tw; yi.done = mask.flags; yi.done_stride = mask.stride;
   yi.nrhs = nrhs; yi.bs_in = bsT2; yi.bs_out = bsT1;
+  yi.sm_count = p->sm_count; yi.sched = p->sched_yi; yi.cta_cap = p->cta_cap;
   ORI_CUDA(run_strided<T>(L, SMODE_INV, false, yi, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + K, e0, e1); e0 = e1;
@@ -1294,6 +1295,7 @@ static_assert(ORI_SCHED_PERSISTENT == SCHED_PERSISTENT && ORI_SCHED_TILES == SCH
 static void apply_schedule(ori_plan_s* p, const ori_schedule& s) {
   p->sched_y = s.yfwd;
   p->sched_z = s.zconv;
+  p->sched_yi = s.yinv;
   p->cta_cap = s.ctas_per_sm;
   p->vec_ctas = s.vec_ctas_per_sm > 0 ? s.vec_ctas_per_sm : 8;
   p->vec_grid = std::max(1, p->sm_count) * p->vec_ctas;
@@ -1304,6 +1306,7 @@ static ori_schedule current_schedule(const ori_plan_s* p) {
   ori_schedule s{};
   s.yfwd = p->sched_y;
   s.zconv = p->sched_z;
+  s.yinv = p->sched_yi;
   s.ctas_per_sm = p->cta_cap;
   s.vec_ctas_per_sm = p->vec_ctas;
   return s;
@@ -1364,38 +1367,31 @@ static ori_status autotune(ori_plan_s* p, int nrhs, int reps, ori_schedule* best
     ORI_CUDA(cudaMemsetAsync(v, 0, n3 * sizeof(cpx<float>), p->ps));
   ori_schedule best = current_schedule(p);
   float best_t = 0.f;
-  // FFT pass schedules (only the FP32 passes at L >= 64 have alternatives)
-  struct Cand { int y, z, cap; };
-  std::vector<Cand> cands;
+  // FFT pass schedules (only the FP32 passes at L >= 64 have alternatives):
+  // one field at a time, keeping the best value of each before the next
+  ORI_TRY(time_fp32_operator(p, nrhs, reps, &best_t));
   if (p->L >= 64) {
-    for (int y : {SCHED_PERSISTENT, SCHED_TILES})
-      for (int z : {SCHED_PERSISTENT, SCHED_TILES})
-        for (int cap : {0, 1}) {
-          if (y == SCHED_TILES && z == SCHED_TILES && cap != 0) continue;   // cap unused
-          cands.push_back({y, z, cap});
+    for (int field = 0; field < 4; ++field) {
+      const int values[2] = {field < 3 ? SCHED_TILES : 1, field < 3 ? SCHED_TILES : 2};
+      for (int vi = 0; vi < (field < 3 ? 1 : 2); ++vi) {
+        ori_schedule s = best;
+        int* f = field == 0 ? &s.yfwd : field == 1 ? &s.zconv : field == 2 ? &s.yinv : &s.ctas_per_sm;
+        *f = values[vi];
+        apply_schedule(p, s);
+        float t = 0.f;
+        ORI_TRY(time_fp32_operator(p, nrhs, reps, &t));
+        if (t < best_t) {
+          best_t = t;
+          best = s;
         }
-  } else {
-    cands.push_back({SCHED_PERSISTENT, SCHED_PERSISTENT, 0});
-  }
-  bool first = true;
-  for (const Cand& c : cands) {
-    ori_schedule s = best;
-    s.yfwd = c.y;
-    s.zconv = c.z;
-    s.ctas_per_sm = c.cap;
-    apply_schedule(p, s);
-    float t = 0.f;
-    ORI_TRY(time_fp32_operator(p, nrhs, reps, &t));
-    if (first || t < best_t) {
-      best_t = t;
-      best = s;
-      first = false;
+        apply_schedule(p, best);
+      }
     }
   }
   apply_schedule(p, best);
   // vector-kernel grid
   float best_v = 0.f;
-  first = true;
+  bool first = true;
   for (int v : {4, 8, 16}) {
     ori_schedule s = best;
     s.vec_ctas_per_sm = v;
@@ -1427,9 +1423,9 @@ ori_status ori_plan_get_schedule(ori_plan_t p, ori_schedule* out) {
 ori_status ori_plan_set_schedule(ori_plan_t p, const ori_schedule* s) {
   g_last_error.clear();
   if (!p || !s) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
-  if ((s->yfwd != ORI_SCHED_PERSISTENT && s->yfwd != ORI_SCHED_TILES) ||
-      (s->zconv != ORI_SCHED_PERSISTENT && s->zconv != ORI_SCHED_TILES))
-    return fail(ORI_ERR_INVALID_ARG, "yfwd and zconv must be ORI_SCHED_PERSISTENT or ORI_SCHED_TILES");
+  auto sched_ok = [](int v) { return v == ORI_SCHED_PERSISTENT || v == ORI_SCHED_TILES; };
+  if (!sched_ok(s->yfwd) || !sched_ok(s->zconv) || !sched_ok(s->yinv))
+    return fail(ORI_ERR_INVALID_ARG, "yfwd, zconv and yinv must be ORI_SCHED_PERSISTENT or ORI_SCHED_TILES");
   if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64) return fail(ORI_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   if (s->vec_ctas_per_sm < 0 || s->vec_ctas_per_sm > kMaxVecCtasPerSm)
     return fail(ORI_ERR_INVALID_ARG, "vec_ctas_per_sm must be in [0, 16]");

@@ -972,6 +972,8 @@ cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, 
 
 template <class T, int L>
 cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count);
+template <int L>
+cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count);
 
 template <class T, int L, int SMODE, bool HALF>
 cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
@@ -981,6 +983,14 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
       if (e != cudaSuccess) return e;
     } else if (a.sched == SCHED_PERSISTENT) {
       return launch_yfwd_pipe_L<T, L>(a, s, false, a.sm_count);
+    }
+  }
+  if constexpr (sizeof(T) == 4 && SMODE == SMODE_INV && L >= 64) {
+    if (setup) {
+      cudaError_t e = launch_yinv_pipe_L<L>(a, s, true, a.sm_count);
+      if (e != cudaSuccess) return e;
+    } else if (a.sched == SCHED_PERSISTENT && a.ncols == L && a.n_in == L) {
+      return launch_yinv_pipe_L<L>(a, s, false, a.sm_count);
     }
   }
   if constexpr (std::is_same<T, dfl>::value && L >= 64 && ((SMODE == SMODE_FWD && HALF) || SMODE == SMODE_INV)) {
@@ -1398,6 +1408,125 @@ __global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256
     tile = next;
   }
   cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------
+// Y inverse pass, persistent and pipelined (FP32): tiles (outer index z, C
+// columns) of every right-hand side numbered together.  A tile's L input
+// rows stream into shared memory with cp.async; the exchange between the
+// two DFT stages reuses that buffer in place, and the next tile is requested
+// as soon as the second stage has read the exchange.
+// ---------------------------------------------------------------------------
+template <int L, int C>
+struct YInvPipe {
+  using TL = Tile<L, C, float>;
+  static constexpr int NT = TL::NT;
+  static constexpr int BUF = (C * L > TL::SMEM_ELEMS) ? C * L : TL::SMEM_ELEMS;
+  static constexpr size_t SMEM_BYTES = size_t(BUF + L) * sizeof(cpx<float>);
+};
+
+template <int L, int C>
+__device__ __forceinline__ void yinv_prefetch(const SArgs& a, int tile, int per_rhs, cpx<float>* B) {
+  constexpr int NT = YInvPipe<L, C>::NT;
+  constexpr int PER_ROW = C * int(sizeof(cpx<float>)) / 16;
+  const int rhs = tile / per_rhs;
+  const int tl = tile - rhs * per_rhs;
+  const int outer = tl / a.col_blocks, cb = tl - outer * a.col_blocks;
+  const cpx<float>* src = reinterpret_cast<const cpx<float>*>(bmove(a.in, a.bs_in * rhs)) + outer * a.in_outer +
+                          (long long)cb * C;
+  for (int k = threadIdx.x; k < L * PER_ROW; k += NT) {
+    const int j = k / PER_ROW, cc = (k - j * PER_ROW) * 2;
+    cp_async16(B + j * C + cc, src + (long long)j * a.in_pt + cc);
+  }
+  cp_async_commit();
+}
+
+template <int L, int C>
+__global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 256 ? 2 : 512 / YInvPipe<L, C>::NT)) k_yinv_pipe(SArgs a) {
+  using T = float;
+  using TL = Tile<L, C, T>;
+  using YP = YInvPipe<L, C>;
+  constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
+  constexpr int PKI = TL::PKI, PCI = TL::PCI;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* B = reinterpret_cast<cpx<T>*>(smraw);
+  cpx<T>* TW = B + YP::BUF;
+  const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
+  for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
+  const int per_rhs = a.nouter * a.col_blocks;
+  const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
+  const int step = gridDim.x;
+  const int tid = threadIdx.x;
+  int c, ja;
+  map_t<LAYOUT_STRIDED, C, L2>(tid, c, ja);
+  int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
+  if (tile < ntiles) yinv_prefetch<L, C>(a, tile, per_rhs, B);
+  while (tile < ntiles) {
+    const int rhs = tile / per_rhs;
+    const int tl = tile - rhs * per_rhs;
+    const int outer = tl / a.col_blocks, cb = tl - outer * a.col_blocks;
+    const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
+    cp_async_wait_all();
+    __syncthreads();
+    // stage A: DFT over k2 of rows k1 + L1 k2, twiddle
+    cpx<T> b[NI][L2];
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+#pragma unroll
+      for (int k2 = 0; k2 < L2; ++k2) b[it][k2] = B[(k1 + L1 * k2) * C + c2];
+      dft<L2, +1, false>(b[it]);
+#pragma unroll
+      for (int j = 1; j < L2; ++j) b[it][j] = twL_mul<+1>(b[it][j], TW, (j * k1) & (L - 1));
+    }
+    __syncthreads();   // raw tile consumed: the exchange reuses the buffer
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+      int c2, k1;
+      map_s<LAYOUT_STRIDED, C, L1>(tid + it * NT, c2, k1);
+#pragma unroll
+      for (int j = 0; j < L2; ++j) B[c2 * PCI + j * PKI + k1] = b[it][j];
+    }
+    __syncthreads();
+    cpx<T> r[L1];
+#pragma unroll
+    for (int k1 = 0; k1 < L1; ++k1) r[k1] = B[c * PCI + ja * PKI + k1];
+    __syncthreads();   // exchange consumed: the buffer takes the next tile
+    if (next < ntiles) yinv_prefetch<L, C>(a, next, per_rhs, B);
+    dft<L1, +1, false>(r);
+    cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + outer * a.out_outer + (long long)cb * C;
+#pragma unroll
+    for (int jb = 0; jb < L1; ++jb) {
+      const int j = ja + L2 * jb;
+      if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
+    }
+    tile = next;
+  }
+  cp_async_wait_all();
+}
+
+template <int L>
+cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = cols_strided<float>();
+  using YP = YInvPipe<L, C>;
+  auto kfn = k_yinv_pipe<L, C>;
+  static int per_sm = 0;
+  if (setup) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(YP::SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, YP::NT, YP::SMEM_BYTES);
+    per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
+    return e;
+  }
+  if (a.ncols != L || a.n_in != L) return cudaErrorInvalidValue;   // whole columns of L rows
+  a.col_blocks = L / C;
+  const long long ntiles = (long long)a.nouter * a.col_blocks * std::max(1, a.nrhs);
+  const int resident = a.cta_cap > 0 ? std::min(std::max(1, per_sm), a.cta_cap) : std::max(1, per_sm);
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count) * resident)));
+  kfn<<<gx, YP::NT, YP::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <class T, int L>

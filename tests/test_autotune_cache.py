@@ -16,7 +16,7 @@ class FakePlan:
 
     def autotune_now(self, nrhs, reps):
         self.tuned += 1
-        return {"yfwd": 1, "zconv": 0, "ctas_per_sm": 1, "vec_ctas_per_sm": 4}, 1.25 * nrhs
+        return {"yfwd": 1, "zconv": 0, "yinv": 1, "ctas_per_sm": 1, "vec_ctas_per_sm": 4}, 1.25 * nrhs
 
 
 def test_key_names_gpu_n_batch_and_arithmetic():

@@ -180,16 +180,17 @@ def test_every_schedule_matches_oracle_and_autotune_caches(tmp_path):
     ref = O.red_matvec_direct(x, n, ks[0], h, N)
     plan = make_plan(n, ks, h, N)
     default = plan.schedule()
-    assert default == {"yfwd": 0, "zconv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8}
+    assert default == {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8}
     dirs = [(0.0, 0.0, 1.0), (0.6, 0.8, 0.0)]
     for y in (0, 1):
         for z in (0, 1):
-            for cap, vec in ((0, 8), (1, 4), (2, 16)):
-                plan.set_schedule({"yfwd": y, "zconv": z, "ctas_per_sm": cap, "vec_ctas_per_sm": vec})
-                y32 = plan.matvec(to_dev(x), form="A", precision="fp32").cpu().numpy()
-                assert rel(y32, ref) < 1e-5, (y, z, cap)
-                _, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
-                assert all(i["status"] == 0 and i["relres"] <= 1e-6 for i in infos)
+            for yi in (0, 1):
+                for cap, vec in ((0, 8), (1, 4), (2, 16)):
+                    plan.set_schedule({"yfwd": y, "zconv": z, "yinv": yi, "ctas_per_sm": cap, "vec_ctas_per_sm": vec})
+                    y32 = plan.matvec(to_dev(x), form="A", precision="fp32").cpu().numpy()
+                    assert rel(y32, ref) < 1e-5, (y, z, yi, cap)
+                    _, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+                    assert all(i["status"] == 0 and i["relres"] <= 1e-6 for i in infos)
     path = str(tmp_path / "tune.json")
     r1 = plan.autotune(nrhs=4, path=path)
     assert not r1["cached"] and r1["ms"] > 0
@@ -206,9 +207,10 @@ def test_set_schedule_rejects_bad_fields():
     n = 8
     h, N = inputs.random_h_N(n, 98)
     plan = make_plan(n, 1.0, h, N)
-    for bad in ({"yfwd": 2, "zconv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8},
-                {"yfwd": 0, "zconv": 0, "ctas_per_sm": -1, "vec_ctas_per_sm": 8},
-                {"yfwd": 0, "zconv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 17}):
+    for bad in ({"yfwd": 2, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8},
+                {"yfwd": 0, "zconv": 0, "yinv": 3, "ctas_per_sm": 0, "vec_ctas_per_sm": 8},
+                {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": -1, "vec_ctas_per_sm": 8},
+                {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 17}):
         with pytest.raises(OriError):
             plan.set_schedule(bad)
     assert plan.schedule()["vec_ctas_per_sm"] == 8
