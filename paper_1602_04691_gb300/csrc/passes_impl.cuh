@@ -19,6 +19,25 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// z * w (SIGN > 0) or z * conj(w) (SIGN < 0) for a twiddle value w already loaded.
+template <int SIGN, class T>
+__device__ __forceinline__ cpx<T> tw_mul_val(cpx<T> z, cpx<T> w) {
+  return cmul(z, cpx<T>{w.x, SIGN > 0 ? w.y : -w.y});
+}
+
+// Two-dimensional twiddle table of a two-stage length-L transform:
+// tab2[k1 * L2 + j] = tab[(j * k1) mod L] for k1 < L1, j < L2 (L entries), so
+// that a thread with fixed j (or fixed k1) finds its twiddles at constant
+// offsets from one base pointer.
+template <int L, class T>
+__device__ __forceinline__ void fill_tw2(cpx<T>* tab2, const cpx<T>* tab, int tid, int nt) {
+  constexpr int L2 = Split<L>::L2;
+  for (int i = tid; i < L; i += nt) {
+    const int k1 = i / L2, j = i - k1 * L2;
+    tab2[i] = tab[(j * k1) & (L - 1)];
+  }
+}
+
 // Lines per CTA of the FP32 contiguous (X) passes: 256 threads of L2 each.
 template <int L>
 constexpr int lines_contig_f32() {
@@ -159,7 +178,7 @@ struct XFwdPipe {
   using TL = Tile<L, C, float>;
   static constexpr int NT = TL::NT;
   static constexpr int STAGE = 3 * C * (L / 2);     // x or r, p, s: C lines of at most L/2 points each
-  static constexpr size_t SMEM_BYTES = size_t(TL::SMEM_ELEMS + STAGE) * sizeof(cpx<float>);
+  static constexpr size_t SMEM_BYTES = size_t(TL::SMEM_ELEMS + STAGE + L) * sizeof(cpx<float>);
 };
 
 template <int L, int C>
@@ -196,8 +215,9 @@ __global__ void __launch_bounds__(XFwdPipe<L, C>::NT, 2) k_xfwd_pipe(XArgs a0) {
   cpx<T>* R = E + TL::SMEM_ELEMS;
   cpx<T>* P = R + XP::STAGE / 3;
   cpx<T>* G = P + XP::STAGE / 3;
+  cpx<T>* TW = G + XP::STAGE / 3;
   if (a.done != nullptr && *a.done != 0) return;
-  const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
+  fill_tw2<L>(TW, reinterpret_cast<const cpx<T>*>(a.twL), threadIdx.x, NT);   // [k1][j] layout
   const int tid = threadIdx.x;
   const int ntiles = int((a.nlines + C - 1) / C);
   const cpx<T> beta = x_beta<T>(a);
@@ -232,8 +252,9 @@ __global__ void __launch_bounds__(XFwdPipe<L, C>::NT, 2) k_xfwd_pipe(XArgs a0) {
     __syncthreads();   // staged inputs consumed: request the next tile
     if (tile + (int)gridDim.x < ntiles) xfwd_prefetch<L, C>(a, tile + gridDim.x, R, P, G);
     dft<L1, -1, true>(r);
+    const cpx<T>* t2 = TW + j2;
 #pragma unroll
-    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = tw_mul_val<-1>(r[k1], t2[k1 * L2]);
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + j2] = r[k1];
     __syncthreads();
@@ -1122,9 +1143,7 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
   cpx<T>* S = E + ZP::E_ELEMS;
   cpx<T>* TWS = S + ZP::S_ELEMS;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
-  if (GZ) {
-    for (int i = threadIdx.x; i < L; i += NT) TWS[i] = twg[i];
-  }
+  if (GZ) fill_tw2<L>(TWS, twg, threadIdx.x, NT);   // [k1][j] layout
   const cpx<T>* tw = GZ ? TWS : twg;
   const int col_blocks = L / C;
   const int per_rhs = L * col_blocks;
@@ -1157,8 +1176,14 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
     if (GZ) zpipe_prefetch_ghat<T, L, C>(a, rhs, ky, cb, S);
     else if (next < ntiles) zpipe_prefetch<T, L, C>(a, next, per_rhs, S);
     dft<L1, -1, true>(r);
+    if (GZ) {
+      const cpx<T>* t2 = tw + jl;
 #pragma unroll
-    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (jl * k1) & (L - 1));
+      for (int k1 = 1; k1 < L1; ++k1) r[k1] = tw_mul_val<-1>(r[k1], t2[k1 * L2]);
+    } else {
+#pragma unroll
+      for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (jl * k1) & (L - 1));
+    }
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
     if (GZ) cp_async_wait_all();
@@ -1175,16 +1200,32 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
 #pragma unroll
       for (int j = 0; j < L2; ++j) b[it][j] = E[c2 * PC + k1 * PK + j];
       dft<L2, -1, false>(b[it]);
-      const int mx = mirror_index(cb * C + c2, L);
+      if (GZ) {
+        // kz = k1 + L1 k2 has mirror index kz below L/2 and L - kz from L/2 on
+        // (k2 >= L2/2), so the slice [mz][C] is read at constant offsets from
+        // two base pointers
+        const cpx<T>* lo = S + k1 * C + c2;
+        const cpx<T>* hi = S + (L - k1) * C + c2;
 #pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) {
-        const int mz = mirror_index(k1 + L1 * k2, L);
-        const cpx<T> g = GZ ? S[mz * C + c2] : ldgc(gh + ((long long)mz * a.H + my) * a.H + mx);
-        b[it][k2] = cmul(b[it][k2], g);
+        for (int k2 = 0; k2 < L2; ++k2)
+          b[it][k2] = cmul(b[it][k2], k2 < L2 / 2 ? lo[k2 * L1 * C] : hi[-k2 * L1 * C]);
+      } else {
+        const int mx = mirror_index(cb * C + c2, L);
+#pragma unroll
+        for (int k2 = 0; k2 < L2; ++k2) {
+          const int mz = mirror_index(k1 + L1 * k2, L);
+          b[it][k2] = cmul(b[it][k2], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
+        }
       }
       dft<L2, +1, false>(b[it]);
+      if (GZ) {
+        const cpx<T>* t2 = tw + k1 * L2;
 #pragma unroll
-      for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
+        for (int ja = 1; ja < L2; ++ja) b[it][ja] = tw_mul_val<+1>(b[it][ja], t2[ja]);
+      } else {
+#pragma unroll
+        for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
+      }
     }
     __syncthreads();   // forward exchange and the spectrum slice fully read
     if (GZ && next < ntiles) zpipe_prefetch<T, L, C>(a, next, per_rhs, S);
@@ -1358,7 +1399,7 @@ __global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256
   cpx<T>* S = E + YP::E_ELEMS;
   cpx<T>* TW = S + YP::S_ELEMS;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
-  for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
+  fill_tw2<L>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
   const int per_rhs = a.nouter * a.col_blocks;
   const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
   const int step = gridDim.x;
@@ -1385,8 +1426,9 @@ __global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256
     __syncthreads();
     if (next < ntiles) ypipe_prefetch<T, L, C>(a, next, per_rhs, S);
     dft<L1, -1, true>(r);
+    const cpx<T>* t2 = TW + jl;
 #pragma unroll
-    for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], TW, (jl * k1) & (L - 1));
+    for (int k1 = 1; k1 < L1; ++k1) r[k1] = tw_mul_val<-1>(r[k1], t2[k1 * L2]);
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
     __syncthreads();
@@ -1452,7 +1494,7 @@ __global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 256
   cpx<T>* B = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* TW = B + YP::BUF;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
-  for (int i = threadIdx.x; i < L; i += NT) TW[i] = twg[i];
+  fill_tw2<L>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
   const int per_rhs = a.nouter * a.col_blocks;
   const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
   const int step = gridDim.x;
@@ -1477,8 +1519,9 @@ __global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 256
 #pragma unroll
       for (int k2 = 0; k2 < L2; ++k2) b[it][k2] = B[(k1 + L1 * k2) * C + c2];
       dft<L2, +1, false>(b[it]);
+      const cpx<T>* t2 = TW + k1 * L2;
 #pragma unroll
-      for (int j = 1; j < L2; ++j) b[it][j] = twL_mul<+1>(b[it][j], TW, (j * k1) & (L - 1));
+      for (int j = 1; j < L2; ++j) b[it][j] = tw_mul_val<+1>(b[it][j], t2[j]);
     }
     __syncthreads();   // raw tile consumed: the exchange reuses the buffer
 #pragma unroll
