@@ -102,7 +102,7 @@ struct SArgs {
   int nouter;
   const void* twL;
   const void* ghat;                // spectrum, H^3 entries (SMODE_ZCONV)
-  const void* ghatZ;               // FP32 spectrum in Z-tile order [my][kx/16][mz][16]
+  const void* ghatZ;               // FP32 spectrum in Z-tile order [my][kx/kZGroup][mz][kZGroup]
   int H;                           // L/2 + 1
   const int* done;
   int sm_count;                    // persistent kernels: CTAs to launch
@@ -121,6 +121,9 @@ struct SArgs {
 };
 
 enum { SCHED_PERSISTENT = 0, SCHED_TILES = 1 };
+
+// Columns per group of the Z-tile-ordered FP32 spectrum [my][kx / kZGroup][mz][kZGroup].
+constexpr int kZGroup = 16;
 
 // Move a pointer by `bytes` (null stays null).
 __device__ __forceinline__ const void* bmove(const void* p, long long bytes) {

@@ -1116,18 +1116,27 @@ __device__ __forceinline__ void zpipe_prefetch_rows(const SArgs& a, int tile, in
   cp_async_commit();
 }
 
-// The spectrum slice of a tile: entries (mz, my(ky), kx) for mz in [0, L/2],
-// kx in the tile, stored contiguously as [mz][C] in the Z-tile order.
+// The spectrum slice of a tile: entries (mz, my(ky), kx) for mz in [0, L/2]
+// and kx in the tile, copied to S as [mz][C].  The Z-tile order stores the
+// FP32 spectrum in groups of kZGroup columns, [my][kx / kZGroup][mz][kZGroup];
+// a tile of C columns (C divides kZGroup) reads C of each group row.
 template <class T, int L, int C>
 __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int rhs, int ky, int cb, cpx<T>* S) {
+  static_assert(kZGroup % C == 0, "tile width must divide the spectrum group");
   constexpr int NT = ZPipe<L, C, T>::NT;
   const int my = mirror_index(ky, L);
   const int g = a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0;
+  const int kx0 = cb * C;
+  const int grp = kx0 / kZGroup, off = kx0 - grp * kZGroup;
   const cpx<T>* src = reinterpret_cast<const cpx<T>*>(bmove(a.ghatZ, a.bs_ghatZ * g)) +
-                      ((long long)my * (L / C) + cb) * (L / 2 + 1) * C;
+                      ((long long)my * (L / kZGroup) + grp) * (L / 2 + 1) * kZGroup + off;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));
-  constexpr int chunks = (L / 2 + 1) * C / EPC;
-  for (int k = threadIdx.x; k < chunks; k += NT) cp_async16(S + k * EPC, src + k * EPC);
+  constexpr int PER_ROW = C / EPC;
+  constexpr int chunks = (L / 2 + 1) * PER_ROW;
+  for (int k = threadIdx.x; k < chunks; k += NT) {
+    const int row = k / PER_ROW, cc = (k - row * PER_ROW) * EPC;
+    cp_async16(S + row * C + cc, src + row * kZGroup + cc);
+  }
   cp_async_commit();
 }
 
@@ -1596,7 +1605,7 @@ cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
 
 template <class T, int L>
 cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = 128 / int(sizeof(cpx<T>));
+  constexpr int C = 128 / int(sizeof(cpx<T>));   // 128-byte rows (measured: 64-byte rows are slower)
   using ZP = ZPipe<L, C, T>;
   auto kfn = k_zconv_pipe<T, L, C>;
   static int per_sm = 0;   // resident CTAs per SM, measured once at set-up

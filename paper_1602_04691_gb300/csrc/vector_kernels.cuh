@@ -75,16 +75,17 @@ __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>
 // slice per Z tile).  gz[((my * (L/16) + cb) * H + mz) * 16 + c] =
 // g32[(mz * H + my) * H + m(cb*16 + c)].
 __global__ void k_build_ghatZ(const cpx<float>* __restrict__ g32, cpx<float>* gz, int L, int H) {
-  const long long total = (long long)H * (L / 16) * H * 16;
+  constexpr int G = kZGroup;
+  const long long total = (long long)H * (L / G) * H * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = int(i % 16);
-    const long long r = i / 16;
+    const int c = int(i % G);
+    const long long r = i / G;
     const int mz = int(r % H);
     const long long t = r / H;
-    const int cb = int(t % (L / 16));
-    const int my = int(t / (L / 16));
-    const int kx = cb * 16 + c;
+    const int cb = int(t % (L / G));
+    const int my = int(t / (L / G));
+    const int kx = cb * G + c;
     const int mx = kx <= L / 2 ? kx : L - kx;
     gz[i] = g32[((long long)mz * H + my) * H + mx];
   }
