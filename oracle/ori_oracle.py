@@ -31,6 +31,8 @@ beyond what the paper states):
 * The refraction recipe of Eq. 2.24-2.26 / Eq. 4.1-4.2.
 * The gradient of J = sum_obs |u_o - t_o|^2 with respect to h and N by the
   dense adjoint (derived from Eq. 2.19; the paper has no gradient).
+* The cell charges of Eq. 2.13, the field off the grid of Eq. 2.10, and the
+  solution-difference metric of Section 4 (Table 4).
 
 Floating point is numpy float64 / complex128 throughout.  numpy's FFT, dense
 LU (``numpy.linalg.solve``) and matrix products serve as library steps.
@@ -53,7 +55,7 @@ __all__ = [
     "cocg", "solve_dense", "solve_red_cocg_fft", "relative_residual",
     "two_particle_solution", "refraction_from_h", "h_from_refraction",
     "branch_sqrt_cut_positive_axis", "adjoint_gradient_dense", "objective",
-    "born_first_order",
+    "born_first_order", "charges", "field", "table4_difference",
 ]
 
 # Surface constant c_S for a sphere: |S_m| = c_S a^2 (Eq. 2.13 and the remark after it).
@@ -440,3 +442,61 @@ def adjoint_gradient_dense(n, k, h, N, obs, target, alpha=(0.0, 0.0, 1.0), side=
     g_h = -Kpsi * N * u
     g_N = -Kpsi * h * u
     return u, objective(u, obs, target), 2.0 * np.conj(g_h), 2.0 * np.real(g_N)
+
+
+# ----------------------------------------------------------------------------
+# Charges, the field off the grid, and the solution-difference metric
+# (Section 2, Section 4)
+# ----------------------------------------------------------------------------
+
+def charges(u, n, h, N, side=1.0, c_S=C_S_SPHERE) -> np.ndarray:
+    """Total charge of the particles of each cell, Eq. 2.13 summed over a cell:
+    every particle of Delta_p carries Q = -c_S a^(2-kappa) h(x_p) u_e(x_p), and
+    a^(2-kappa) * #(Delta_p) = N_p |Delta_p| (Eq. 2.18), so the cell carries
+    -c_S h_p N_p |Delta_p| u_p with u_p the solution of Eq. 2.19."""
+    return -red_weights(h, N, cell_size(n, side), c_S) * np.asarray(u, dtype=np.complex128).ravel()
+
+
+def field(points, u, n, k, h, N, alpha=None, origin=(0.0, 0.0, 0.0), side=1.0,
+          c_S=C_S_SPHERE, chunk=256) -> np.ndarray:
+    """The field of Eq. 2.10, u(x) = u0(x) + sum_m G(x, x_m) Q_m, by direct
+    summation over the n^3 cells (Q from `charges`).  A point that coincides
+    with a cell point x_j leaves out m = j: the sum is then the effective field
+    of Eq. 2.14, which the solution u_j of Eq. 2.19 satisfies.  alpha = None
+    returns the scattered part alone (no u0)."""
+    pts = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    pos = cell_centres(n, origin, side)
+    Q = charges(u, n, h, N, side, c_S)
+    d = cell_size(n, side)
+    out = np.empty(len(pts), dtype=np.complex128)
+    for s in range(0, len(pts), chunk):
+        diff = pts[s:s + chunk, None, :] - pos[None, :, :]
+        r = np.sqrt((diff ** 2).sum(axis=2))
+        G = np.zeros(r.shape, dtype=np.complex128)
+        far = r > 1e-9 * d
+        G[far] = greens_function(r[far], k)
+        out[s:s + chunk] = G @ Q
+    if alpha is not None:
+        out += plane_wave(pts, k, alpha)
+    return out
+
+
+def table4_difference(fine, fine_points, coarse, n_coarse, origin=(0.0, 0.0, 0.0), side=1.0) -> float:
+    """Solution difference of Section 4 (Table 4): the cube [origin, origin +
+    side)^3 is cut into n_coarse^3 sub-cubes Delta_q, the coarse solution holds
+    one value y_q per sub-cube, and the fine solution values x_i sit at the
+    points fine_points[i].  For each Delta_q, average |x_i - y_q| over the fine
+    points lying in Delta_q (sub-cubes are half-open, [q d, (q+1) d) per axis);
+    return the largest average."""
+    pts = np.asarray(fine_points, dtype=np.float64)
+    dc = side / n_coarse
+    # half-open sub-cubes [q dc, (q+1) dc): a point on a face belongs to the
+    # sub-cube above it (the relative 1e-9 absorbs rounding of the coordinates)
+    idx = np.floor((pts - np.asarray(origin, dtype=np.float64)) / dc + 1e-9).astype(np.int64)
+    inside = np.all((idx >= 0) & (idx < n_coarse), axis=1)
+    q = (idx[:, 2] * n_coarse + idx[:, 1]) * n_coarse + idx[:, 0]
+    diff = np.abs(np.asarray(fine, dtype=np.complex128).ravel() - np.asarray(coarse).ravel()[np.where(inside, q, 0)])
+    sums = np.bincount(q[inside], weights=diff[inside], minlength=n_coarse ** 3)
+    counts = np.bincount(q[inside], minlength=n_coarse ** 3)
+    has = counts > 0
+    return float(np.max(sums[has] / counts[has]))

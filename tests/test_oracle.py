@@ -375,3 +375,98 @@ def test_adjoint_gradient_vs_central_differences():
         dN = (J_of(h, N + e) - J_of(h, N - e)) / (2 * step)
         assert abs(gh[p] - complex(dre, dim)) < 1e-7 * max(1.0, abs(gh[p]))
         assert abs(gN[p] - dN) < 1e-7 * max(1.0, abs(gN[p]))
+
+
+# --------------------------------------------------------------------------
+# Charges, the field off the grid (Eq. 2.10, 2.13) and the Table 4 metric
+# --------------------------------------------------------------------------
+
+SECTION4_K = 0.182651
+SECTION4_H = 2.65481e-9 + 5.30961e-6j
+
+
+def test_field_at_cell_points_is_the_solution():
+    """Eq. 2.10 evaluated at the particle points, leaving out each particle's
+    own term, is the effective field of Eq. 2.14; the solution of Eq. 2.19
+    (dense LU) must satisfy it.  A wrong sign or scale of the charges Q_m
+    (Eq. 2.13) breaks the identity."""
+    n, k = 5, 2.0
+    h, N = inputs.random_h_N(n, 404)
+    pos = O.cell_centres(n, (0.1, -0.2, 0.3), 0.9)
+    A = O.red_matrix(n, k, h, N, origin=(0.1, -0.2, 0.3), side=0.9)
+    u0 = O.plane_wave(pos, k, (0.0, 0.6, 0.8))
+    u = O.solve_dense(A, u0)
+    f = O.field(pos, u, n, k, h, N, alpha=(0.0, 0.6, 0.8), origin=(0.1, -0.2, 0.3), side=0.9)
+    assert np.max(np.abs(f - u)) < 1e-13
+    # the scattered part alone is u - u0
+    fs = O.field(pos, u, n, k, h, N, origin=(0.1, -0.2, 0.3), side=0.9)
+    assert np.max(np.abs(fs - (u - u0))) < 1e-13
+
+
+def test_field_of_one_particle_closed_form():
+    """One occupied cell (N = 0 elsewhere): u_1 = u0(x_1), Q_1 = -c_S h N |Delta| u_1,
+    and off the grid u(x) = u0(x) + Q_1 exp(ik r) / (4 pi r), r = |x - x_1|."""
+    n, k, side = 3, 1.7, 1.2
+    h = np.zeros(n ** 3, dtype=np.complex128)
+    N = np.zeros(n ** 3)
+    j = 13                                   # the centre cell
+    h[j], N[j] = 0.8 - 0.3j, 1.5
+    pos = O.cell_centres(n, side=side)
+    u = O.solve_dense(O.red_matrix(n, k, h, N, side=side), O.plane_wave(pos, k))
+    assert abs(u[j] - O.plane_wave(pos[j:j + 1], k)[0]) < 1e-15
+    Q1 = -4 * math.pi * h[j] * N[j] * (side / n) ** 3 * u[j]
+    x = np.array([[0.1, 1.7, -0.4], [2.0, 0.3, 0.9]])
+    r = np.linalg.norm(x - pos[j], axis=1)
+    expect = np.exp(1j * k * x[:, 2]) + Q1 * np.exp(1j * k * r) / (4 * math.pi * r)
+    got = O.field(x, u, n, k, h, N, alpha=(0.0, 0.0, 1.0), side=side)
+    assert np.max(np.abs(got - expect)) < 1e-15
+
+
+def test_table4_metric_by_hand():
+    """One coarse cube holding 8 fine points: the mean of |x_i - y|.  Values
+    chosen so the mean is 0.375 exactly: |diffs| = 0,0,0,0,1,0.5,1.5,0."""
+    fine_pts = O.cell_centres(2)
+    y = 1.0 + 1.0j
+    diffs = np.array([0, 0, 0, 0, 1.0, 0.5j, -1.5, 0])
+    assert O.table4_difference(y + diffs, fine_pts, np.array([y]), 1) == 0.375
+    # two coarse cubes along x (n_coarse = 2 uses 8 cubes; fill only those with points)
+    fine_pts = O.cell_centres(4)
+    coarse = np.arange(8) * (1.0 + 0.5j)
+    q = ((fine_pts[:, 2] // 0.5) * 4 + (fine_pts[:, 1] // 0.5) * 2 + fine_pts[:, 0] // 0.5).astype(int)
+    fine = coarse[q].copy()
+    fine[np.argmax(q == 5)] += 0.8           # one of the 8 points of cube 5
+    assert abs(O.table4_difference(fine, fine_pts, coarse, 2) - 0.1) < 1e-15
+
+
+def test_table4_metric_zero_for_nested_constant_fields():
+    """A fine field equal to the coarse value of its sub-cube differs by 0, also
+    when fine points lie exactly on sub-cube faces (vertex points)."""
+    nc, nf = 3, 6
+    coarse = np.exp(1j * np.arange(nc ** 3))
+    for origin in ((0.0, 0.0, 0.0), (-0.5 / nf,) * 3):      # centres, vertices
+        pts = O.cell_centres(nf, origin)
+        m = np.rint((pts - origin[0]) * nf - 0.5).astype(int)   # fine cell indices
+        qc = m * nc // nf
+        q = (qc[:, 2] * nc + qc[:, 1]) * nc + qc[:, 0]
+        assert O.table4_difference(coarse[q], pts, coarse, nc) == 0.0
+
+
+def test_table4_reproduces_printed_red_vs_ie():
+    """Section 4: (RED) with P = 8000 sub-cubes against (IE) with C = 64000
+    collocation points, the paper's parameters.  Points at the grid vertices
+    d*m (Eq. 3.3.5), each unknown owning the sub-cube [m d, (m+1) d).  The
+    metric matches the printed 0.0022 to one unit of its last digit, and the
+    plane-wave estimate (the scattered part is ~1e-5 here)."""
+    g = _golden("table4_differences.json")
+    sol = {}
+    for n in (g["n_red"], g["n_ie"]):
+        d = 1.0 / n
+        org = (-d / 2,) * 3
+        h = np.full(n ** 3, SECTION4_H)
+        u, it, rr = O.solve_red_cocg_fft(n, SECTION4_K, h, np.ones(n ** 3), alpha=(1.0, 0.0, 0.0),
+                                        origin=org, tol=1e-10)
+        sol[n] = (u, O.cell_centres(n, org))
+    v = O.table4_difference(sol[40][0], sol[40][1], sol[20][0], 20)
+    assert abs(v - g["red_vs_ie"]) <= g["printed_resolution"]
+    est = np.mean([abs(np.exp(1j * SECTION4_K * j / 40) - 1) for j in range(2)])
+    assert abs(v - est) < 1e-6
