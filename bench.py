@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch schedule (no autotuning before the timed region)")
+    ap.add_argument("--experiment", action="store_true",
+                    help="run the Section 4 experiment scaled to one GPU (RED n=20, IE n=40, ORI n=480) "
+                         "and print its JSON line instead of the benchmark")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched leg (n=128, 16 directions x 4 wave numbers)")
     return ap.parse_args()
@@ -514,10 +517,25 @@ def batched_leg(args, dev, n=128, ks=(1.0, 2.0, 4.0, 8.0), ndir=16, reps=3):
             "schedule": tuned["schedule"], "schedule_operator_ms": tuned["ms"]}
 
 
+def experiment_arm(args, rank, local):
+    """Section 4's experiment (Table 4 differences, Eq. 2.10 samples) on one GPU."""
+    import torch
+    from paper_1602_04691_gb300 import experiment
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    out = experiment.run(device=dev)
+    out["experiment"] = "Section 4 scaled: RED n=20, IE n=40, ORI n=480, mixed to relres 1e-6"
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.experiment:
+        experiment_arm(args, rank, local)
+    elif args.impl == "reference":
         reference_arm(args, world, rank)
     else:
         ours_arm(args, world, rank, local)

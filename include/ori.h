@@ -332,6 +332,27 @@ ori_status ori_plan_set_schedule(ori_plan_t plan, const ori_schedule* s);
 ori_status ori_plan_autotune(ori_plan_t plan, int nrhs, int reps, ori_schedule* best,
                              float* best_ms, void* stream);
 
+/*
+ * ori_field - the field away from the grid points, Eq. 2.10:
+ *     out_i = [exp(ik alpha.x_i)] + sum_m G(x_i, x_m) Q_m,
+ *     Q_m   = -c_S h_m N_m |Delta| u_m            (Eq. 2.13 summed over cell m:
+ *             the particles of a cell carry a^(2-kappa) #(Delta_m) = N_m |Delta|)
+ * for a solution u of the plan's system (its first wave number), by direct
+ * summation in FP64: O(npts n^3) work.
+ *   u_dev       n^3 complex128 solution (device).
+ *   npts        number of points, 0 .. 2^30 (0: nothing to do).
+ *   points_dev  3*npts doubles (x, y, z of each point), device.
+ *   alpha_host  incidence direction (normalised here; (0,0,0) -> (0,0,1)) to add
+ *               the incident wave, or NULL for the scattered part alone.
+ *   out_dev     npts complex128, device.
+ * A point within 1e-9 d of a cell point leaves that cell out, so at the cell
+ * points the value is the effective field of Eq. 2.14, which a converged
+ * solution equals.  Overwrites the plan's solver scratch (not the medium or
+ * the spectra).  Asynchronous on `stream`.
+ */
+ori_status ori_field(ori_plan_t plan, const double* u_dev, int64_t npts, const double* points_dev,
+                     const double* alpha_host, double* out_dev, void* stream);
+
 /* Device-time accounting of a plan's kernels (for profiling and benchmarks). */
 enum {
   ORI_PASS_XFWD = 0,   /* X forward FFT pass with its prologue                  */

@@ -36,6 +36,7 @@ EXPORTS = [
     "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
     "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats", "ori_matvec_noalloc",
     "ori_cocg_solve_batch", "ori_plan_get_schedule", "ori_plan_set_schedule", "ori_plan_autotune",
+    "ori_field",
 ]
 
 ORI_SCHED_PERSISTENT = 0
@@ -152,6 +153,8 @@ def load():
     lib.ori_plan_set_schedule.restype = i
     lib.ori_plan_autotune.argtypes = [vp, i, i, C.POINTER(Schedule), C.POINTER(C.c_float), vp]
     lib.ori_plan_autotune.restype = i
+    lib.ori_field.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    lib.ori_field.restype = i
     lib.ori_adjoint_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo), vp]
     lib.ori_adjoint_solve.restype = i
     lib.ori_plan_set_timing.argtypes = [vp, i]

@@ -1454,3 +1454,49 @@ ori_status ori_plan_autotune(ori_plan_t p, int nrhs, int reps, ori_schedule* bes
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The field off the grid (Eq. 2.10)
+// ---------------------------------------------------------------------------
+extern "C" ori_status ori_field(ori_plan_t p, const double* u_dev, int64_t npts, const double* points_dev,
+                                const double* alpha_host, double* out_dev, void* stream) {
+  g_last_error.clear();
+  if (!p || !u_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (npts < 0 || npts > (int64_t(1) << 30)) return fail(ORI_ERR_INVALID_ARG, "npts must be in [0, 2^30]");
+  if (npts == 0) return ORI_OK;
+  if (!points_dev || !out_dev) return fail(ORI_ERR_INVALID_ARG, "points_dev and out_dev must be non-NULL");
+  double a[3] = {0.0, 0.0, 1.0};
+  if (alpha_host) {
+    if (!finite3(alpha_host)) return fail(ORI_ERR_INVALID_ARG, "alpha must be finite");
+    const double an = std::sqrt(alpha_host[0] * alpha_host[0] + alpha_host[1] * alpha_host[1] +
+                                alpha_host[2] * alpha_host[2]);
+    if (an > 0)
+      for (int c = 0; c < 3; ++c) a[c] = alpha_host[c] / an;
+  }
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  ORI_TRY(ensure_capacity(p, 1));
+  ORI_TRY(enter(p, user));
+  const double coef = -p->c_S * p->d * p->d * p->d;
+  ORI_VEC(p, ORI_PASS_VECTOR,
+          (k_charges<<<p->vec_grid, 256, 0, p->ps>>>(reinterpret_cast<const cpx<double>*>(u_dev), p->h, p->N, coef,
+                                                      p->p64, p->n3)));
+  // slices per point: enough blocks to fill the GPU; partials in the FP64 scratch cube
+  const long long cap_entries = (long long)t1_elems(p) * p->cap;
+  int S = int(std::max<long long>(1, std::min<long long>(256, (4LL * p->sm_count + npts - 1) / npts)));
+  S = int(std::min<long long>(S, std::max<long long>(1, p->n3 / 256)));
+  const long long chunk = std::max<long long>(1, std::min<long long>(npts, cap_entries / S));
+  double2* partials = reinterpret_cast<double2*>(p->T1d);
+  for (long long c0 = 0; c0 < npts; c0 += chunk) {
+    const int np = int(std::min<long long>(chunk, npts - c0));
+    const double* pts = points_dev + 3 * c0;
+    const dim3 grid(unsigned(std::min<long long>(np, 65535)), unsigned(S));
+    ORI_VEC(p, ORI_PASS_VECTOR,
+            (k_field_partial<<<grid, 256, 0, p->ps>>>(p->p64, pts, np, p->n, p->d, p->origin[0], p->origin[1],
+                                                       p->origin[2], p->ks[0], partials)));
+    ORI_VEC(p, ORI_PASS_VECTOR,
+            (k_field_finish<<<unsigned((np + 255) / 256), 256, 0, p->ps>>>(
+                partials, S, pts, np, p->ks[0], a[0], a[1], a[2], alpha_host ? 1 : 0,
+                reinterpret_cast<cpx<double>*>(out_dev) + c0)));
+  }
+  return leave(p, user);
+}

@@ -401,6 +401,86 @@ __global__ void k_gradient(const cpx<double>* __restrict__ ec, const cpx<double>
   }
 }
 
+// Cell charges of Eq. 2.13 summed over a cell: Q_m = coef * h_m N_m u_m with
+// coef = -c_S |Delta| (every particle of cell m carries -c_S a^(2-kappa) h u,
+// and a^(2-kappa) times their number is N_m |Delta|).
+__global__ void k_charges(const cpx<double>* __restrict__ u, const cpx<double>* __restrict__ h,
+                          const double* __restrict__ N, double coef, cpx<double>* Q, long long n3) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<double> hu = cmul(h[i], u[i]);
+    const double s = coef * N[i];
+    Q[i] = {s * hu.x, s * hu.y};
+  }
+}
+
+// Field of Eq. 2.10 by direct summation, first stage: block (p, s) adds
+// G(x_p, x_m) Q_m over the cells m of slice s (cells m = s, s + S, ...
+// strided by threads) and writes one partial per (point, slice).  A cell
+// whose point coincides with x_p (r <= 1e-9 d) is left out.
+__global__ void k_field_partial(const cpx<double>* __restrict__ Q, const double* __restrict__ pts, int npts,
+                                int n, double d, double ox, double oy, double oz, double k,
+                                double2* partials) {
+  __shared__ double2 red[32];
+  const long long n3 = (long long)n * n * n;
+  const int S = gridDim.y;
+  const long long per = (n3 + S - 1) / S;
+  const long long m0 = blockIdx.y * per;
+  const long long m1 = m0 + per < n3 ? m0 + per : n3;
+  const double inv4pi = 1.0 / (4.0 * kPi);
+  for (int pi = blockIdx.x; pi < npts; pi += gridDim.x) {
+    const double px = pts[3 * pi], py = pts[3 * pi + 1], pz = pts[3 * pi + 2];
+    double ar = 0.0, ai = 0.0;
+    for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
+      const int ix = int(m % n), iy = int((m / n) % n), iz = int(m / ((long long)n * n));
+      const double dx = px - (ox + (ix + 0.5) * d);
+      const double dy = py - (oy + (iy + 0.5) * d);
+      const double dz = pz - (oz + (iz + 0.5) * d);
+      const double r = sqrt(dx * dx + dy * dy + dz * dz);
+      if (r > 1e-9 * d) {
+        double sn, cs;
+        sincos(k * r, &sn, &cs);
+        const double g = inv4pi / r;
+        const cpx<double> q = Q[m];
+        ar += g * (cs * q.x - sn * q.y);
+        ai += g * (cs * q.y + sn * q.x);
+      }
+    }
+    const double2 v = warp_sum2(make_double2(ar, ai));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double2 t = make_double2(0.0, 0.0);
+      for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) { t.x += red[i].x; t.y += red[i].y; }
+      partials[(long long)pi * S + blockIdx.y] = t;
+    }
+  }
+}
+
+// Second stage: out_p = sum of the S partials of point p in slice order, plus
+// the incident wave exp(i k a . x_p) when add_u0.
+__global__ void k_field_finish(const double2* __restrict__ partials, int S, const double* __restrict__ pts,
+                               int npts, double k, double ax, double ay, double az, int add_u0,
+                               cpx<double>* out) {
+  for (int pi = blockIdx.x * blockDim.x + threadIdx.x; pi < npts; pi += gridDim.x * blockDim.x) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int s = 0; s < S; ++s) {
+      const double2 v = partials[(long long)pi * S + s];
+      t.x += v.x;
+      t.y += v.y;
+    }
+    if (add_u0) {
+      double sn, cs;
+      sincos(k * (ax * pts[3 * pi] + ay * pts[3 * pi + 1] + az * pts[3 * pi + 2]), &sn, &cs);
+      t.x += cs;
+      t.y += sn;
+    }
+    out[pi] = {t.x, t.y};
+  }
+}
+
 // Widen a complex64 vector to complex128 / narrow complex128 to complex64.
 __global__ void k_widen(const cpx<float>* __restrict__ a, cpx<double>* b, long long n3) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;

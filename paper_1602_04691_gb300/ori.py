@@ -249,6 +249,21 @@ class Plan:
             out_infos.append(d)
         return u.view(nk, ndir, m), out_infos
 
+    def field(self, u: torch.Tensor, points: torch.Tensor, alpha=None, stream=None) -> torch.Tensor:
+        """Field of Eq. 2.10 at `points` (float64 CUDA tensor of shape (npts, 3)) for the
+        solution u: the scattered part, plus the incident wave when alpha is given."""
+        u = _need(u, torch.complex128, self.n ** 3, "u")
+        if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float64
+                and points.dim() == 2 and points.shape[1] == 3):
+            raise TypeError("points must be a float64 CUDA tensor of shape (npts, 3)")
+        points = points.contiguous()
+        out = torch.empty(points.shape[0], dtype=torch.complex128, device=self.device)
+        al = None if alpha is None else (C.c_double * 3)(*[float(v) for v in alpha])
+        _lib.check(_lib.load().ori_field(self.handle, u.data_ptr(), int(points.shape[0]), points.data_ptr(),
+                                         C.cast(al, C.c_void_p) if al is not None else None, out.data_ptr(),
+                                         _stream_ptr(stream)), "ori_field")
+        return out
+
     def adjoint(self, u: torch.Tensor, econj: torch.Tensor, raise_on_failure: bool = True,
                 stream=None, **kw):
         """Gradient of J = sum_obs |u_o - t_o|^2 w.r.t. h and N; econj = conj(u - t) on the
