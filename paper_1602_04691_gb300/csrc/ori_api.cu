@@ -471,65 +471,86 @@ static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N
   return ORI_OK;
 }
 
-// Spectrum of every wave number: kernel cube -> FP64 3D FFT -> (L/2+1)^3
-// distinct entries in FP64, FP32 and paired FP32, and the Z-tile-ordered
-// FP32 copy.  The cube is a transient L^3 complex128 buffer.
+// Spectrum of every wave number.  The kernel cube c(x, y, z) = G(d |offset|)
+// (zero at the origin and beyond offsets n - 1) is even along each axis, so
+// its DFT is even too and only the octant kx, ky, kz <= L/2 (H = L/2 + 1 per
+// axis) is kept.  Planes z = 0..H-1 (the others repeat them) are transformed
+// along x and y in batches, keeping kx, ky < H, into an H^3 buffer; the z
+// transform then reads row L - z for z > L/2 (the even extension) and keeps
+// kz < H in place.  FP64 throughout; the octant is stored in FP64, FP32 and
+// paired FP32 with c_S |Delta| / L^3 folded in, plus the Z-tile-ordered FP32
+// copy.  Transient memory: the H^3 octant and a batch of L^2 planes.
 static ori_status build_spectrum(ori_plan_s* p) {
-  const int L = p->L, n = p->n;
+  const int L = p->L, n = p->n, H = p->H;
   const long long L3 = (long long)L * L * L;
-  const long long H3 = (long long)p->H * p->H * p->H;
-  const long long HZ = (long long)p->H * p->H * p->L;
-  cpx<double>* cube = nullptr;
-  {
-    cudaError_t e = cudaMalloc(&cube, size_t(L3) * sizeof(cpx<double>));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(ORI_ERR_OOM, std::string("cudaMalloc (kernel cube): ") + cudaGetErrorString(e));
-    }
+  const long long H3 = (long long)H * H * H;
+  const long long HZ = (long long)H * H * L;
+  const long long plane = (long long)L * L;
+  const int nz = int(std::max<long long>(1, std::min<long long>(H, (1LL << 26) / plane)));   // <= 1 GiB per batch
+  cpx<double>* oct = nullptr;
+  cpx<double>* planes = nullptr;
+  cudaError_t e = cudaMalloc(&oct, size_t(H3) * sizeof(cpx<double>));
+  if (e == cudaSuccess) e = cudaMalloc(&planes, size_t(nz) * size_t(plane) * sizeof(cpx<double>));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (oct) cudaFree(oct);
+    return fail(ORI_ERR_OOM, std::string("cudaMalloc (spectrum build): ") + cudaGetErrorString(e));
   }
   ori_status st = ORI_OK;
+  auto check = [&](cudaError_t err, const char* what) {
+    if (err != cudaSuccess && st == ORI_OK) st = fail(ORI_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
+    return st == ORI_OK;
+  };
   for (size_t ik = 0; ik < p->ks.size() && st == ORI_OK; ++ik) {
-    XArgs a{};
-    a.mode = PRO_KERNEL;
-    a.d = p->d;
-    a.k = p->ks[ik];
-    a.n = n;
-    a.nlines = L * L;
-    a.n_in = L;
-    a.line_len_in = L;
-    a.line_len_out = L;
-    a.lines_per_plane = L;
-    a.fft_out = cube;
-    a.twL = p->tw64;
-    cudaError_t e = run_xfwd<double>(L, false, a, p->ps, false);
-    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan X pass: ") + cudaGetErrorString(e)); break; }
-    SArgs y{};
-    y.in = cube; y.out = cube;
-    y.in_outer = (long long)L * L; y.out_outer = (long long)L * L;
-    y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = L; y.n_out = L; y.nouter = L;
-    y.twL = p->tw64;
-    e = run_strided<double>(L, SMODE_FWD, false, y, p->ps, false);
-    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Y pass: ") + cudaGetErrorString(e)); break; }
+    for (int z0 = 0; z0 < H && st == ORI_OK; z0 += nz) {
+      const int nzb = std::min(nz, H - z0);
+      XArgs a{};
+      a.mode = PRO_KERNEL;
+      a.d = p->d;
+      a.k = p->ks[ik];
+      a.n = n;
+      a.nlines = (long long)nzb * L;
+      a.n_in = L;
+      a.line_len_in = L;
+      a.line_len_out = L;
+      a.lines_per_plane = L;
+      a.plane0 = z0;
+      a.fft_out = planes;
+      a.twL = p->tw64;
+      a.sm_count = p->sm_count;
+      if (!check(run_xfwd<double>(L, false, a, p->ps, false), "plan X pass")) break;
+      SArgs y{};
+      y.in = planes;
+      y.out = oct + (long long)z0 * H * H;
+      y.in_outer = plane; y.out_outer = (long long)H * H;
+      y.in_pt = L; y.out_pt = H; y.ncols = H; y.n_in = L; y.n_out = H; y.nouter = nzb;
+      y.twL = p->tw64;
+      y.sm_count = p->sm_count;
+      check(run_strided<double>(L, SMODE_FWD, false, y, p->ps, false), "plan Y pass");
+    }
+    if (st != ORI_OK) break;
     SArgs z{};
-    z.in = cube; z.out = cube;
-    z.in_outer = L; z.out_outer = L;
-    z.in_pt = (long long)L * L; z.out_pt = (long long)L * L;
-    z.ncols = L; z.n_in = L; z.n_out = L; z.nouter = L;
+    z.in = oct; z.out = oct;
+    z.in_outer = H; z.out_outer = H;
+    z.in_pt = (long long)H * H; z.out_pt = (long long)H * H;
+    z.ncols = H; z.n_in = L; z.n_out = H; z.nouter = H;
+    z.mirror_in = 1;
     z.twL = p->tw64;
-    e = run_strided<double>(L, SMODE_FWD, false, z, p->ps, false);
-    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z pass: ") + cudaGetErrorString(e)); break; }
+    z.sm_count = p->sm_count;
+    if (!check(run_strided<double>(L, SMODE_FWD, false, z, p->ps, false), "plan Z pass")) break;
     const double scale = p->c_S * p->d * p->d * p->d / double(L3);
-    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(cube, p->ghat64 + ik * H3, p->ghat32 + ik * H3,
-                                                   p->ghatdf + ik * H3, L, p->H, scale);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan extract: ") + cudaGetErrorString(e)); break; }
-    k_build_ghatZ<<<p->vec_grid, 256, 0, p->ps>>>(p->ghat32 + ik * H3, p->ghatZ32 + ik * HZ, L, p->H);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan Z spectrum: ") + cudaGetErrorString(e)); break; }
-    e = cudaStreamSynchronize(p->ps);
-    if (e != cudaSuccess) { st = fail(ORI_ERR_CUDA, std::string("plan spectrum: ") + cudaGetErrorString(e)); break; }
+    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(oct, p->ghat64 + ik * H3, p->ghat32 + ik * H3,
+                                                   p->ghatdf + ik * H3, H, H, scale);
+    if (!check(cudaGetLastError(), "plan extract")) break;
+    if (p->ghatZ32) {
+      k_build_ghatZ<<<p->vec_grid, 256, 0, p->ps>>>(p->ghat32 + ik * H3, p->ghatZ32 + ik * HZ, L, H);
+      if (!check(cudaGetLastError(), "plan Z spectrum")) break;
+    }
+    check(cudaStreamSynchronize(p->ps), "plan spectrum");
   }
-  cudaFree(cube);
+  cudaStreamSynchronize(p->ps);
+  cudaFree(planes);
+  cudaFree(oct);
   return st;
 }
 

@@ -78,6 +78,7 @@ struct XArgs {
   int line_len_in;      // elements between lines in the input
   int line_len_out;     // elements between lines in the output
   int lines_per_plane;  // PRO_KERNEL: lines in one z plane (= L)
+  int plane0;           // PRO_KERNEL: z index of the first plane of the launch
   int mode;             // PRO_* or EPI_*
   const void* twL;      // twiddle table for length L
   const int* done;      // solver flag: the pass returns at once if *done != 0
@@ -112,6 +113,8 @@ struct SArgs {
   long long bs_in, bs_out, bs_ghat, bs_ghatZ;
   int rhs_per_ghat;
   int done_stride;
+  int mirror_in;                   // forward transform of an even sequence stored up to L/2:
+                                   // input row j > L/2 is read from row L - j
   // launch schedule of the FP32 Y-forward and Z passes (chosen by the plan's
   // autotuner): SCHED_PERSISTENT = the cp.async-pipelined persistent kernel
   // with at most cta_cap resident CTAs per SM (0 = as many as fit);

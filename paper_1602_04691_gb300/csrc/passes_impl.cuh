@@ -96,7 +96,7 @@ __device__ __forceinline__ cpx<T> x_prologue(const XArgs& a, long long line, int
       return cmul(s, p);
     }
     default: {  // PRO_KERNEL: kernel cube entry at signed offsets (FP64)
-      const int l3 = int(line / a.lines_per_plane), l2 = int(line % a.lines_per_plane);
+      const int l3 = a.plane0 + int(line / a.lines_per_plane), l2 = int(line % a.lines_per_plane);
       const int s1 = signed_offset<T>(j, L), s2 = signed_offset<T>(l2, L), s3 = signed_offset<T>(l3, L);
       if (abs(s1) >= a.n || abs(s2) >= a.n || abs(s3) >= a.n) return czero<T>();
       const long long r2 = (long long)s1 * s1 + (long long)s2 * s2 + (long long)s3 * s3;
@@ -624,7 +624,8 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
       r[j1] = czero<T>();
       if (!HALF || j1 < L1 / 2) {
         const int j = j1 * L2 + j2;
-        if (c < colmax && j < a.n_in) r[j1] = in[(long long)j * a.in_pt + c];
+        const int jr = (!HALF && a.mirror_in && j > L / 2) ? L - j : j;
+        if (c < colmax && j < a.n_in) r[j1] = in[(long long)jr * a.in_pt + c];
       }
     }
     dft<L1, -1, HALF>(r);

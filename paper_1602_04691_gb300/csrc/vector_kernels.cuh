@@ -57,12 +57,12 @@ __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __rest
 // Spectrum of the kernel cube: keep the (L/2+1)^3 distinct entries of the
 // even cube and fold in c_S |Delta| / L^3.
 __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>* g64,
-                               cpx<float>* g32, cpx<dfl>* gdf, int L, int H, double scale) {
+                               cpx<float>* g32, cpx<dfl>* gdf, int ld, int H, double scale) {
   const long long total = (long long)H * H * H;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int m1 = int(i % H), m2 = int((i / H) % H), m3 = int(i / ((long long)H * H));
-    const cpx<double> v = cube[((long long)m3 * L + m2) * L + m1];
+    const cpx<double> v = cube[((long long)m3 * ld + m2) * ld + m1];
     const cpx<double> s = {v.x * scale, v.y * scale};
     g64[i] = s;
     g32[i] = ccast<float>(s);
