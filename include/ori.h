@@ -90,7 +90,11 @@ typedef struct {
                        k; ori_cocg_solve_batch solves for every one of them, the
                        other calls use ks[0]                                      */
   const double* ks; /* n_k host wave numbers (read during ori_plan only)         */
-  int    reserved[4];
+  int    min_L;     /* 0: padded length L = smallest power of two >= 2n.  Else a
+                       power of two in [4, 2048]: L = max(that, min_L) (any
+                       L >= 2n - 1 gives the same operator, R6 of the design
+                       notes; used to exercise long transforms on small grids) */
+  int    reserved[3];
 } ori_plan_opts;
 
 typedef struct {
@@ -135,9 +139,11 @@ void ori_default_plan_opts(ori_plan_opts* o);
 
 /*
  * ori_plan - build the operator for one grid, wave number and medium.
- *   n        cells per axis, 2 <= n <= 512.  The padded FFT length per axis
+ *   n        cells per axis, 2 <= n <= 1024.  The padded FFT length per axis
  *            is L = the smallest power of two >= 2n (the paper pads to 2b-2
- *            by mirroring, Section 3; any L >= 2n-1 gives the same crop).
+ *            by mirroring, Section 3; any L >= 2n-1 gives the same crop), at
+ *            most 2048.  L <= 1024 runs the register-tile and persistent
+ *            pipelined FFT passes; L = 2048 runs shared-memory radix-8 passes.
  *   k        wave number, finite and > 0 (Eq. 2.1).
  *   dom      cube corner and side (Eq. 3.3.5 uses the unit cube at the origin).
  *   h_dev    n^3 complex128 impedance samples h(x_p) (Eq. 2.13), device.

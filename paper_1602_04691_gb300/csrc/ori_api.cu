@@ -602,7 +602,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
   g_last_error.clear();
   if (!out) return fail(ORI_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (n < 2 || n > 512) return fail(ORI_ERR_INVALID_ARG, "n must be in [2, 512]");
+  if (n < 2 || n > 1024) return fail(ORI_ERR_INVALID_ARG, "n must be in [2, 1024]");
   if (!dom) return fail(ORI_ERR_INVALID_ARG, "dom is NULL");
   if (!std::isfinite(dom->side) || dom->side <= 0 || !finite3(dom->origin))
     return fail(ORI_ERR_INVALID_ARG, "domain side must be finite and > 0, origin finite");
@@ -614,6 +614,8 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     if (o.c_S == 0.0) o.c_S = 4.0 * kPi;
   }
   if (!std::isfinite(o.c_S)) return fail(ORI_ERR_INVALID_ARG, "c_S must be finite");
+  if (o.min_L != 0 && (o.min_L < 4 || o.min_L > 2048 || (o.min_L & (o.min_L - 1)) != 0))
+    return fail(ORI_ERR_INVALID_ARG, "min_L must be 0 or a power of two in [4, 2048]");
   std::vector<double> ks;
   if (o.n_k > 0) {
     if (!o.ks) return fail(ORI_ERR_INVALID_ARG, "opts->ks is NULL while opts->n_k > 0");
@@ -634,6 +636,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     p->n = int(n);
     p->L = 4;
     while (p->L < 2 * p->n) p->L *= 2;
+    p->L = std::max(p->L, o.min_L);
     p->H = p->L / 2 + 1;
     p->n3 = (long long)n * n * n;
     p->ks = ks;
@@ -657,7 +660,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
         (st = alloc_n(p, &p->S32, n3)) || (st = alloc_n(p, &p->wdf, n3)) || (st = alloc_n(p, &p->Sdf, n3)) ||
         (st = alloc_n(p, &p->ghat64, nk * H3)) || (st = alloc_n(p, &p->ghat32, nk * H3)) ||
         (st = alloc_n(p, &p->ghatdf, nk * H3)) ||
-        (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L)) ||
+        (p->L <= 1024 && (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L))) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
         (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)))
       break;
@@ -1391,7 +1394,7 @@ static ori_status autotune(ori_plan_s* p, int nrhs, int reps, ori_schedule* best
   // FFT pass schedules (only the FP32 passes at L >= 64 have alternatives):
   // one field at a time, keeping the best value of each before the next
   ORI_TRY(time_fp32_operator(p, nrhs, reps, &best_t));
-  if (p->L >= 64) {
+  if (p->L >= 64 && p->L <= 1024) {   // longer transforms have one schedule
     for (int field = 0; field < 4; ++field) {
       const int values[2] = {field < 3 ? SCHED_TILES : 1, field < 3 ? SCHED_TILES : 2};
       for (int vi = 0; vi < (field < 3 ? 1 : 2); ++vi) {

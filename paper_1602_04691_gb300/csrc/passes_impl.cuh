@@ -722,7 +722,7 @@ struct LSmem {
   static constexpr size_t SMEM_BYTES = (X_ELEMS + size_t(L)) * sizeof(cpx<T>);
 };
 
-template <class T, int L, int C, int SMODE>
+template <class T, int L, int C, int SMODE, bool HALF = true>
 __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a0) {
   const SArgs a = s_for_rhs(a0, blockIdx.y);
   using LS = LSmem<L, C, T>;
@@ -747,9 +747,11 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a0
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         v[t] = czero<T>();
-        if (t < 4 && c < colmax && j + t * S8 < a.n_in) v[t] = in[(long long)(j + t * S8) * a.in_pt + c];
+        const int jj = j + t * S8;
+        const int jr = (!HALF && a.mirror_in && jj > L / 2) ? L - jj : jj;
+        if ((!HALF || t < 4) && c < colmax && jj < a.n_in) v[t] = in[(long long)jr * a.in_pt + c];
       }
-      dft<8, -1, true>(v);
+      dft<8, -1, HALF>(v);
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
@@ -787,7 +789,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a0
   }
 }
 
-template <class T, int L, int C>
+template <class T, int L, int C, bool HALF = true>
 __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a0) {
   const XArgs a = x_for_rhs(a0, blockIdx.y);
   using LS = LSmem<L, C, T>;
@@ -809,9 +811,9 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a0) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       v[t] = czero<T>();
-      if (t < 4 && line < a.nlines && j + t * S8 < a.n_in) v[t] = x_prologue<T>(a, line, j + t * S8, L, beta);
+      if ((!HALF || t < 4) && line < a.nlines && j + t * S8 < a.n_in) v[t] = x_prologue<T>(a, line, j + t * S8, L, beta);
     }
-    dft<8, -1, true>(v);
+    dft<8, -1, HALF>(v);
 #pragma unroll
     for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
@@ -917,7 +919,7 @@ inline bool xfwd_pipe_ok(const XArgs& a, int L) {
 }
 
 template <class T, int L, bool HALF>
-cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
+cudaError_t launch_xfwd_reg_L(const XArgs& a, cudaStream_t s, bool setup) {
   if constexpr (sizeof(T) == 4 && HALF && L >= 64) {
     if (setup) {
       cudaError_t e = launch_xfwd_pipe_L<L>(a, s, true);
@@ -968,7 +970,7 @@ cudaError_t launch_xinv_pipe_L(const XArgs& a, Scalars* sc, int fin, cudaStream_
 }
 
 template <class T, int L>
-cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
+cudaError_t launch_xinv_reg_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
   if constexpr (sizeof(T) == 4 && L >= 64) {
     return launch_xinv_pipe_L<L>(a, sc, fin, s, setup, nblocks);
   } else if constexpr (std::is_same<T, dfl>::value && L >= 64) {
@@ -998,7 +1000,12 @@ template <int L>
 cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count);
 
 template <class T, int L, int SMODE, bool HALF>
-cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
+cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup);
+template <class T, int L>
+cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup);
+
+template <class T, int L, int SMODE, bool HALF>
+cudaError_t launch_strided_reg_L(SArgs a, cudaStream_t s, bool setup) {
   if constexpr (sizeof(T) == 4 && SMODE == SMODE_FWD && HALF && L >= 64) {
     if (setup) {   // both schedules are set up; the plan picks one per launch
       cudaError_t e = launch_yfwd_pipe_L<T, L>(a, s, true, a.sm_count);
@@ -1356,7 +1363,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a) {
 
 template <class T, int L>
 cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = 8;
+  constexpr int C = (L > 1024 && sizeof(cpx<T>) == 16) ? 4 : 8;   // the tile must fit in 227 KB
   using ZS = ZSmem<L, C, T>;
   auto kfn = k_zconv_smem<T, L, C>;
   if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZS::SMEM_BYTES));
@@ -1630,7 +1637,7 @@ cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
 // one-CTA-per-tile strided kernel; the pipelined kernel for FP64; the plain
 // strided kernel for small L.
 template <class T, int L>
-cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
+cudaError_t launch_zconv_reg_L(SArgs a, cudaStream_t s, bool setup) {
   if constexpr (L >= 64 && std::is_same<T, dfl>::value) {
     return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
   } else if constexpr (L >= 64 && sizeof(T) == 4) {
@@ -1648,7 +1655,66 @@ cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
   }
 }
 
-#define ORI_FOR_EACH_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+// Lengths beyond kMaxRegL: every pass uses the shared-memory radix-8 kernels
+// (a register tile of L1 = 64 points per thread does not fit).
+constexpr int kMaxRegL = 1024;
+
+template <class T, int L, bool HALF>
+cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
+  if constexpr (L > kMaxRegL) {
+    constexpr int CS = 4;
+    using LS = LSmem<L, CS, T>;
+    auto kfs = k_xfwd_smem<T, L, CS, HALF>;
+    if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
+    kfs<<<dim3(unsigned((a.nlines + CS - 1) / CS), unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a);
+    return cudaGetLastError();
+  } else {
+    return launch_xfwd_reg_L<T, L, HALF>(a, s, setup);
+  }
+}
+
+template <class T, int L>
+cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
+  if constexpr (L > kMaxRegL) {
+    constexpr int CS = 4;
+    using LS = LSmem<L, CS, T>;
+    auto kfs = k_xinv_smem<T, L, CS>;
+    const unsigned grid = unsigned((a.nlines + CS - 1) / CS);
+    if (nblocks) *nblocks = grid;
+    if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
+    kfs<<<dim3(grid, unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a, sc, fin);
+    return cudaGetLastError();
+  } else {
+    return launch_xinv_reg_L<T, L>(a, sc, fin, s, setup, nblocks);
+  }
+}
+
+template <class T, int L, int SMODE, bool HALF>
+cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
+  if constexpr (L > kMaxRegL) {
+    if constexpr (SMODE == SMODE_ZCONV) {
+      return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
+    } else {
+      constexpr int CS = 4;
+      using LS = LSmem<L, CS, T>;
+      auto kfs = k_strided_smem<T, L, CS, SMODE, (SMODE == SMODE_FWD ? HALF : true)>;
+      if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
+      a.col_blocks = (a.ncols + CS - 1) / CS;
+      kfs<<<dim3(unsigned(a.nouter) * unsigned(a.col_blocks), unsigned(std::max(1, a.nrhs))), LS::NT, LS::SMEM_BYTES, s>>>(a);
+      return cudaGetLastError();
+    }
+  } else {
+    return launch_strided_reg_L<T, L, SMODE, HALF>(a, s, setup);
+  }
+}
+
+template <class T, int L>
+cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
+  if constexpr (L > kMaxRegL) return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
+  else return launch_zconv_reg_L<T, L>(a, s, setup);
+}
+
+#define ORI_FOR_EACH_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
 
 template <class T>
 cudaError_t run_xfwd(int L, bool half, const XArgs& a, cudaStream_t s, bool setup) {

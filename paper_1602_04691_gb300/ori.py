@@ -65,7 +65,8 @@ class Plan:
     calls use the first."""
 
     def __init__(self, n: int, k, h: torch.Tensor, N: torch.Tensor, side: float = 1.0,
-                 origin=(0.0, 0.0, 0.0), c_S: float | None = None, mem_cap: int = 0, stream=None):
+                 origin=(0.0, 0.0, 0.0), c_S: float | None = None, mem_cap: int = 0, min_L: int = 0,
+                 stream=None):
         lib = _lib.load()
         self.n = int(n)
         self.ks = [float(v) for v in k] if hasattr(k, "__len__") else [float(k)]
@@ -87,6 +88,7 @@ class Plan:
         lib.ori_default_plan_opts(C.byref(po))
         po.c_S = self.c_S
         po.mem_cap = int(mem_cap)
+        po.min_L = int(min_L)
         ks_arr = (C.c_double * len(self.ks))(*self.ks)
         if len(self.ks) > 1:
             po.n_k = len(self.ks)

@@ -1,0 +1,100 @@
+"""Padded length L = 2048: the shared-memory radix-8 passes of every arithmetic.
+
+Grids of n >= 513 (up to the paper-scale n = 1000) pad to L = 2048.  The plan
+option min_L forces that length on small grids, where the oracle's direct
+sum and dense LU check every output; a natural n = 520 grid is checked on
+sampled rows.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1602_04691_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def long_plan():
+    from paper_1602_04691_gb300 import Plan
+    n, k = 12, 2.4
+    h, N = inputs.random_h_N(n, 601)
+    plan = Plan(n, k, to_dev(h), to_dev(N), min_L=2048)
+    assert plan.L == 2048
+    yield n, k, h, N, plan
+    plan.close()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("precision,form,bound", [("fp64", "A", 1e-12), ("df", "A", 1e-12), ("fp32", "A", 1e-5),
+                                                  ("fp64", "B", 1e-12), ("fp32", "B", 1e-5)])
+def test_L2048_matvec_vs_direct_sum(long_plan, precision, form, bound):
+    n, k, h, N, plan = long_plan
+    x = inputs.random_complex(n ** 3, 602)
+    y = plan.matvec(to_dev(x), form=form, precision=precision).cpu().numpy()
+    if form == "A":
+        ref = O.red_matvec_direct(x, n, k, h, N)
+    else:
+        ref = O.symmetrised_matvec_direct(x, n, k, h, N)
+    assert rel(y, ref) < bound
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-11, 1e-9), ("mixed", 1e-6, 2e-5)])
+def test_L2048_solve_vs_lu(long_plan, precision, tol, bound):
+    n, k, h, N, plan = long_plan
+    u, info = plan.solve(tol=tol, precision=precision)
+    assert info["status"] == 0 and info["relres"] <= tol
+    u_lu = O.solve_dense(O.red_matrix(n, k, h, N), O.plane_wave(O.cell_centres(n), k))
+    assert rel(u.cpu().numpy(), u_lu) < bound
+
+
+def test_L2048_batch_vs_single(long_plan):
+    n, k, h, N, plan = long_plan
+    dirs = [(0.0, 0.0, 1.0), (1.0, 0.0, 0.0)]
+    ub, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+    for j, a in enumerate(dirs):
+        us, _ = plan.solve(tol=1e-10, precision="fp64", alpha=a)
+        assert infos[j]["relres"] <= 1e-6
+        assert rel(ub[0, j].cpu().numpy(), us.cpu().numpy()) < 1e-5
+
+
+def test_natural_L2048_fp32_matvec_sampled_rows():
+    """n = 520 pads to L = 2048 by itself; the FP32 B-form operator on sampled rows."""
+    from paper_1602_04691_gb300 import Plan
+    n, k = 520, 5.0
+    h, N = inputs.random_h_N(n, 603)
+    x = inputs.random_complex(n ** 3, 604).astype(np.complex64)
+    plan = Plan(n, k, to_dev(h), to_dev(N))
+    assert plan.L == 2048
+    y = plan.matvec32(to_dev(x), form="B").cpu().numpy()
+    rows = np.array([0, n ** 3 - 1, n * n * (n // 2) + n * (n // 2) + n // 2, 123456789])
+    S = O.sqrt_hN(h, N)
+    xs = S * x.astype(np.complex128)
+    d = 1.0 / n
+    Kxs = (O.C_S_SPHERE * d ** 3) * O.offdiag_sum_rows_grid(xs, rows, n, k)
+    ref = x[rows] + S[rows] * Kxs
+    assert rel(y[rows], ref) < 1e-5
+    plan.close()
+    torch.cuda.empty_cache()
