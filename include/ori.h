@@ -94,7 +94,16 @@ typedef struct {
                        power of two in [4, 2048]: L = max(that, min_L) (any
                        L >= 2n - 1 gives the same operator, R6 of the design
                        notes; used to exercise long transforms on small grids) */
-  int    reserved[3];
+  int    lean;      /* 0: full plan.  1: a plan for mixed-precision solves only, for
+                       the largest grids (n = 1000 needs about 246 GB instead of
+                       ~390 GB): it keeps no copy of h and N, no A-form arrays, no
+                       1/S, no FP64 spectrum and no FP64 COCG vectors.  On a lean
+                       plan ori_matvec supports ORI_FORM_B in ORI_FP32 / ORI_DF,
+                       ori_matvec32 ORI_FORM_B, the solves ORI_MIXED with the
+                       ORI_DF residual; the A form, FP64 operations, the adjoint
+                       and ori_field return ORI_ERR_UNSUPPORTED, and h N must be
+                       nonzero in every cell (ORI_ERR_UNSUPPORTED otherwise)  */
+  int    reserved[2];
 } ori_plan_opts;
 
 typedef struct {

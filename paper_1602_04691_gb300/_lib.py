@@ -53,7 +53,7 @@ class Domain(C.Structure):
 
 class PlanOpts(C.Structure):
     _fields_ = [("c_S", C.c_double), ("mem_cap", C.c_size_t), ("n_k", C.c_int),
-                ("ks", C.POINTER(C.c_double)), ("min_L", C.c_int), ("reserved", C.c_int * 3)]
+                ("ks", C.POINTER(C.c_double)), ("min_L", C.c_int), ("lean", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class SolveOpts(C.Structure):

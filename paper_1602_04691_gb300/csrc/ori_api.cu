@@ -64,6 +64,7 @@ struct ori_plan_s {
   long long n3 = 0;
   double d = 0, c_S = 0, side = 0, origin[3] = {0, 0, 0};
   std::vector<double> ks;          // wave numbers; one spectrum each
+  bool lean = false;               // mixed-solve-only plan (ori_plan_opts.lean)
   size_t bytes = 0, mem_cap = 0;
   int sm_count = 0;
   unsigned long long zero_S = 0;
@@ -245,8 +246,8 @@ static size_t t2_elems(const ori_plan_s* p) { return size_t(p->n) * p->L * p->L;
 // Release the batch-sized buffers.
 static void free_capacity(ori_plan_s* p) {
   const size_t c = size_t(p->cap), n3 = size_t(p->n3);
-  free_n(p, p->T1f, c * t1_elems(p));
-  free_n(p, p->T2f, c * t2_elems(p));
+  p->T1f = nullptr;   // the FP32 cubes live inside the FP64-class ones
+  p->T2f = nullptr;
   free_n(p, p->T1d, c * t1_elems(p));
   free_n(p, p->T2d, c * t2_elems(p));
   free_n(p, p->sc, c);
@@ -272,16 +273,21 @@ static ori_status ensure_capacity(ori_plan_s* p, int nrhs) {
   cudaStreamSynchronize(p->ps);
   free_capacity(p);
   const size_t c = size_t(nrhs), n3 = size_t(p->n3);
-  ORI_TRY(alloc_n(p, &p->T1f, c * t1_elems(p)));
-  ORI_TRY(alloc_n(p, &p->T2f, c * t2_elems(p)));
+  // FP32 passes and FP64-class passes never run at the same time (one
+  // stream, one operator application after another), so the FP32 cubes
+  // (half the bytes) share the FP64-class allocations
   ORI_TRY(alloc_n(p, &p->T1d, c * t1_elems(p)));
   ORI_TRY(alloc_n(p, &p->T2d, c * t2_elems(p)));
+  p->T1f = reinterpret_cast<cpx<float>*>(p->T1d);
+  p->T2f = reinterpret_cast<cpx<float>*>(p->T2d);
   ORI_TRY(alloc_n(p, &p->sc, c));
   ORI_CUDA(cudaMemsetAsync(p->sc, 0, c * sizeof(Scalars), p->ps));
   // partials of the X-inverse reductions, or two per block of the widest vector grid
   p->part_per_rhs = std::max<size_t>(size_t(p->xinv_blocks), size_t(2) * std::max(1, p->sm_count) * kMaxVecCtasPerSm) + 16;
   ORI_TRY(alloc_n(p, &p->partials, c * p->part_per_rhs));
-  for (cpx<double>** v : {&p->b64, &p->w, &p->r64, &p->u0, &p->p64, &p->q64}) ORI_TRY(alloc_n(p, v, c * n3));
+  for (cpx<double>** v : {&p->b64, &p->w, &p->r64}) ORI_TRY(alloc_n(p, v, c * n3));
+  if (!p->lean)   // FP64 COCG vectors and the incident field kept for S = 0 cells
+    for (cpx<double>** v : {&p->u0, &p->p64, &p->q64}) ORI_TRY(alloc_n(p, v, c * n3));
   for (cpx<float>** v : {&p->x32, &p->r32, &p->p32, &p->q32}) ORI_TRY(alloc_n(p, v, c * n3));
   for (double** v : {&p->d_tols, &p->d_scl, &p->d_coef, &p->d_kv}) ORI_TRY(alloc_n(p, v, c));
   ORI_TRY(alloc_n(p, &p->d_dir, 3 * c));
@@ -461,13 +467,21 @@ static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n, int sm_coun
 
 static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N_dev) {
   const size_t n3 = size_t(p->n3);
-  ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
-  ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
+  const cpx<double>* h = reinterpret_cast<const cpx<double>*>(h_dev);
+  const double* N = N_dev;
+  if (!p->lean) {   // a lean plan keeps no copy of h and N (no adjoint, no field)
+    ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
+    ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
+    h = p->h;
+    N = p->N;
+  }
   ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
-  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(p->h, p->N, p->w64, p->S64, p->w32, p->S32,
+  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(h, N, p->w64, p->S64, p->w32, p->S32,
                                                                         p->Sinv, p->wdf, p->Sdf, p->n3, p->d_count)));
   ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  if (p->lean && p->zero_S != 0)
+    return fail(ORI_ERR_UNSUPPORTED, "a lean plan needs h N != 0 in every cell (no FP64 recovery of S = 0 cells)");
   return ORI_OK;
 }
 
@@ -539,7 +553,7 @@ static ori_status build_spectrum(ori_plan_s* p) {
     z.sm_count = p->sm_count;
     if (!check(run_strided<double>(L, SMODE_FWD, false, z, p->ps, false), "plan Z pass")) break;
     const double scale = p->c_S * p->d * p->d * p->d / double(L3);
-    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(oct, p->ghat64 + ik * H3, p->ghat32 + ik * H3,
+    k_extract_ghat<<<p->vec_grid, 256, 0, p->ps>>>(oct, p->ghat64 ? p->ghat64 + ik * H3 : nullptr, p->ghat32 + ik * H3,
                                                    p->ghatdf + ik * H3, H, H, scale);
     if (!check(cudaGetLastError(), "plan extract")) break;
     if (p->ghatZ32) {
@@ -645,6 +659,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     for (int i = 0; i < 3; ++i) p->origin[i] = dom->origin[i];
     p->c_S = o.c_S;
     p->mem_cap = o.mem_cap;
+    p->lean = o.lean != 0;
     cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     p->vec_grid = std::max(1, p->sm_count) * p->vec_ctas;
     if (cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking) != cudaSuccess ||
@@ -655,10 +670,12 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     }
     const size_t n3 = size_t(p->n3), nk = ks.size();
     const size_t H3 = size_t(p->H) * p->H * p->H;
-    if ((st = alloc_n(p, &p->h, n3)) || (st = alloc_n(p, &p->N, n3)) || (st = alloc_n(p, &p->w64, n3)) ||
-        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->w32, n3)) ||
-        (st = alloc_n(p, &p->S32, n3)) || (st = alloc_n(p, &p->wdf, n3)) || (st = alloc_n(p, &p->Sdf, n3)) ||
-        (st = alloc_n(p, &p->ghat64, nk * H3)) || (st = alloc_n(p, &p->ghat32, nk * H3)) ||
+    const bool full = !p->lean;   // arrays of the FP64 and A-form operations, the adjoint and the field
+    if ((full && ((st = alloc_n(p, &p->h, n3)) || (st = alloc_n(p, &p->N, n3)) || (st = alloc_n(p, &p->w64, n3)) ||
+                  (st = alloc_n(p, &p->Sinv, n3)) || (st = alloc_n(p, &p->w32, n3)) || (st = alloc_n(p, &p->wdf, n3)) ||
+                  (st = alloc_n(p, &p->ghat64, nk * H3)))) ||
+        (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->S32, n3)) || (st = alloc_n(p, &p->Sdf, n3)) ||
+        (st = alloc_n(p, &p->ghat32, nk * H3)) ||
         (st = alloc_n(p, &p->ghatdf, nk * H3)) ||
         (p->L <= 1024 && (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L))) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
@@ -670,7 +687,6 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
         (st = setup_kernels<dfl>(p->L, &bxdf, p->n, p->sm_count)))
       break;
     p->xinv_blocks = std::max({bx32, bx64, bxdf});
-    if ((st = ensure_capacity(p, 1))) break;
     if ((st = enter(p, user))) break;
     {
       cpx<double>* twd = new cpx<double>[p->L];
@@ -689,6 +705,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     }
     if ((st = set_medium(p, h_dev, N_dev))) break;
     if ((st = build_spectrum(p))) break;
+    if ((st = ensure_capacity(p, 1))) break;   // after the spectrum build: lower peak memory
     if ((st = leave(p, user))) break;
   } while (0);
   if (st != ORI_OK) {
@@ -762,6 +779,8 @@ ori_status ori_matvec(ori_plan_t p, const double* x_dev, double* y_dev, int form
   if (precision != ORI_FP64 && precision != ORI_FP32 && precision != ORI_DF)
     return fail(ORI_ERR_INVALID_ARG, "precision must be ORI_FP64, ORI_FP32 or ORI_DF");
   if (x_dev == y_dev) return fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
+  if (p->lean && (form == ORI_FORM_A || precision == ORI_FP64))
+    return fail(ORI_ERR_UNSUPPORTED, "a lean plan applies only the B form in FP32 or paired FP32");
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
   ORI_TRY(enter(p, user));
   XArgs pro{}, epi{};
@@ -795,6 +814,7 @@ ori_status ori_matvec32(ori_plan_t p, const float* x_dev, float* y_dev, int form
   if (!p || !x_dev || !y_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
   if (form != ORI_FORM_A && form != ORI_FORM_B) return fail(ORI_ERR_INVALID_ARG, "form must be ORI_FORM_A or ORI_FORM_B");
   if (x_dev == y_dev) return fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
+  if (p->lean && form == ORI_FORM_A) return fail(ORI_ERR_UNSUPPORTED, "a lean plan applies only the B form");
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
   ORI_TRY(enter(p, user));
   XArgs pro{}, epi{};
@@ -1172,6 +1192,8 @@ static ori_status check_solve_opts(const ori_solve_opts* in, ori_solve_opts* o) 
 static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs_dev, const double* dirs_host,
                               double* u_dev, const ori_solve_opts& o, ori_solve_info* infos, cudaStream_t user) {
   const int nrhs = nk * ndir;
+  if (p->lean && (o.precision == ORI_FP64 || o.residual == ORI_FP64))
+    return fail(ORI_ERR_UNSUPPORTED, "a lean plan solves in mixed precision with the paired-FP32 residual only");
   ORI_TRY(ensure_capacity(p, nrhs));
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
@@ -1198,7 +1220,8 @@ static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs
   // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
   if (p->zero_S == 0) {
     ORI_VEC(p, ORI_PASS_VECTOR,
-            (k_recover<<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->w, p->Sinv, reinterpret_cast<cpx<double>*>(u_dev), p->n3)));
+            (k_recover<<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->w, p->Sinv, p->S64, reinterpret_cast<cpx<double>*>(u_dev),
+                                                           p->n3)));
   } else {
     const long long bsv = p->n3 * (long long)sizeof(cpx<double>);
     XArgs pro{}, epi{};
@@ -1278,6 +1301,7 @@ ori_status ori_adjoint_solve(ori_plan_t p, const double* u_dev, const double* ec
   g_last_error.clear();
   if (!p || !u_dev || !econj_dev || !grad_h_dev || !grad_N_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
   if (p->zero_S != 0) return fail(ORI_ERR_UNSUPPORTED, "the adjoint needs h N != 0 in every cell");
+  if (p->lean) return fail(ORI_ERR_UNSUPPORTED, "a lean plan has no adjoint (it keeps no copy of h and N)");
   ori_solve_opts o;
   ORI_TRY(check_solve_opts(opts, &o));
   ori_solve_info info{};
@@ -1486,6 +1510,7 @@ extern "C" ori_status ori_field(ori_plan_t p, const double* u_dev, int64_t npts,
                                 const double* alpha_host, double* out_dev, void* stream) {
   g_last_error.clear();
   if (!p || !u_dev) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (p->lean) return fail(ORI_ERR_UNSUPPORTED, "a lean plan has no field evaluation (it keeps no copy of h and N)");
   if (npts < 0 || npts > (int64_t(1) << 30)) return fail(ORI_ERR_INVALID_ARG, "npts must be in [0, 2^30]");
   if (npts == 0) return ORI_OK;
   if (!points_dev || !out_dev) return fail(ORI_ERR_INVALID_ARG, "points_dev and out_dev must be non-NULL");

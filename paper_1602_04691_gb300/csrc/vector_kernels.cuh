@@ -38,18 +38,15 @@ __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __rest
     const double nv = N[i];
     const cpx<double> w = {hv.x * nv, hv.y * nv};
     const cpx<double> s = csqrt_principal(w);
-    w64[i] = w;
     S64[i] = s;
-    w32[i] = ccast<float>(w);
     S32[i] = ccast<float>(s);
-    wdf[i] = c_from_c64<dfl>(w);
     Sdf[i] = c_from_c64<dfl>(s);
-    if (w.x == 0.0 && w.y == 0.0) {
-      ++zs;
-      Sinv[i] = {0.0, 0.0};
-    } else {
-      Sinv[i] = cdivd(cpx<double>{1.0, 0.0}, s);
-    }
+    if (w64) w64[i] = w;                 // the A-form arrays and 1/S are optional
+    if (w32) w32[i] = ccast<float>(w);
+    if (wdf) wdf[i] = c_from_c64<dfl>(w);
+    const bool zero = w.x == 0.0 && w.y == 0.0;
+    if (zero) ++zs;
+    if (Sinv) Sinv[i] = zero ? cpx<double>{0.0, 0.0} : cdivd(cpx<double>{1.0, 0.0}, s);
   }
   if (zs) atomicAdd(zero_count, zs);
 }
@@ -64,7 +61,7 @@ __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>
     const int m1 = int(i % H), m2 = int((i / H) % H), m3 = int(i / ((long long)H * H));
     const cpx<double> v = cube[((long long)m3 * ld + m2) * ld + m1];
     const cpx<double> s = {v.x * scale, v.y * scale};
-    g64[i] = s;
+    if (g64) g64[i] = s;   // a lean plan keeps no FP64 spectrum
     g32[i] = ccast<float>(s);
     gdf[i] = c_from_c64<dfl>(s);
   }
@@ -130,7 +127,7 @@ __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __
   Scalars* sc = sc0 + rb;
   double2* partials = partials0 + (long long)rb * gridDim.x;
   if (rhs != nullptr) rhs += rb * n3;
-  u0 += rb * n3;
+  if (u0 != nullptr) u0 += rb * n3;
   b += rb * n3;
   if (rhs == nullptr) {
     const double k = kvals[rb];
@@ -154,7 +151,7 @@ __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __
       const int ix = int(i % n), iy = int((i / n) % n), iz = int(i / ((long long)n * n));
       u = cmul(cmul(e[ix], e[n + iy]), e[2 * n + iz]);
     }
-    u0[i] = u;
+    if (u0 != nullptr) u0[i] = u;
     const cpx<double> bv = cmul(S[i], u);
     b[i] = bv;
     acc += bv.x * bv.x + bv.y * bv.y;
@@ -377,12 +374,12 @@ __global__ void k_accumulate(cpx<double>* w, const cpx<float>* __restrict__ d32,
 
 // u = w / S = w * (1/S) (every S != 0; 1/S is kept by the plan).
 __global__ void k_recover(const cpx<double>* __restrict__ w, const cpx<double>* __restrict__ Sinv,
-                          cpx<double>* u, long long n3) {
+                          const cpx<double>* __restrict__ S, cpx<double>* u, long long n3) {
   w += blockIdx.y * n3;
   u += blockIdx.y * n3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
        i += (long long)gridDim.x * blockDim.x)
-    u[i] = cmul(w[i], Sinv[i]);
+    u[i] = Sinv != nullptr ? cmul(w[i], Sinv[i]) : cdivd(w[i], S[i]);   // lean plans keep no 1/S
 }
 
 // Adjoint gradient: psi = S z, t = (conj(e) - psi) u,

@@ -66,7 +66,7 @@ class Plan:
 
     def __init__(self, n: int, k, h: torch.Tensor, N: torch.Tensor, side: float = 1.0,
                  origin=(0.0, 0.0, 0.0), c_S: float | None = None, mem_cap: int = 0, min_L: int = 0,
-                 stream=None):
+                 lean: bool = False, stream=None):
         lib = _lib.load()
         self.n = int(n)
         self.ks = [float(v) for v in k] if hasattr(k, "__len__") else [float(k)]
@@ -89,6 +89,7 @@ class Plan:
         po.c_S = self.c_S
         po.mem_cap = int(mem_cap)
         po.min_L = int(min_L)
+        po.lean = 1 if lean else 0
         ks_arr = (C.c_double * len(self.ks))(*self.ks)
         if len(self.ks) > 1:
             po.n_k = len(self.ks)

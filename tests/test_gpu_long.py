@@ -98,3 +98,49 @@ def test_natural_L2048_fp32_matvec_sampled_rows():
     assert rel(y[rows], ref) < 1e-5
     plan.close()
     torch.cuda.empty_cache()
+
+
+def test_lean_plan_matches_full_plan_and_rejects_the_rest():
+    """A lean plan (mixed solves only; the paper-scale memory budget) gives the
+    full plan's solutions, holds less memory, and refuses what it cannot do."""
+    from paper_1602_04691_gb300 import OriError, Plan
+    from paper_1602_04691_gb300._lib import ORI_ERR_UNSUPPORTED
+    n, k = 16, 3.0
+    h, N = inputs.random_h_N(n, 605)
+    full = Plan(n, [k, 1.5], to_dev(h), to_dev(N))
+    lean = Plan(n, [k, 1.5], to_dev(h), to_dev(N), lean=True)
+    assert lean.bytes < full.bytes
+    uf, _ = full.solve(tol=1e-6, precision="mixed")
+    ul, il = lean.solve(tol=1e-6, precision="mixed")
+    assert il["relres"] <= 1e-6
+    assert rel(ul.cpu().numpy(), uf.cpu().numpy()) < 1e-13
+    dirs = [(0.0, 0.0, 1.0), (0.0, 1.0, 1.0)]
+    bf, _ = full.solve_batch(dirs, tol=1e-6, precision="mixed")
+    bl, _ = lean.solve_batch(dirs, tol=1e-6, precision="mixed")
+    assert rel(bl.cpu().numpy(), bf.cpu().numpy()) < 1e-13
+    x = to_dev(inputs.random_complex(n ** 3, 606))
+    for prec in ("fp32", "df"):
+        assert rel(lean.matvec(x, form="B", precision=prec).cpu().numpy(),
+                   full.matvec(x, form="B", precision=prec).cpu().numpy()) < 1e-15
+    calls = [lambda: lean.matvec(x, form="A", precision="fp32"),
+             lambda: lean.matvec(x, form="B", precision="fp64"),
+             lambda: lean.solve(tol=1e-6, precision="fp64"),
+             lambda: lean.solve(tol=1e-6, precision="mixed", residual="fp64"),
+             lambda: lean.field(ul, to_dev(np.zeros((1, 3))))]
+    for call in calls:
+        with pytest.raises(OriError) as e:
+            call()
+        assert e.value.status == ORI_ERR_UNSUPPORTED
+    full.close()
+    lean.close()
+
+
+def test_lean_plan_rejects_zero_impedance_cells():
+    from paper_1602_04691_gb300 import OriError, Plan
+    from paper_1602_04691_gb300._lib import ORI_ERR_UNSUPPORTED
+    n = 8
+    h, N = inputs.random_h_N(n, 607)
+    N[5] = 0.0
+    with pytest.raises(OriError) as e:
+        Plan(n, 1.0, to_dev(h), to_dev(N), lean=True)
+    assert e.value.status == ORI_ERR_UNSUPPORTED
