@@ -1277,14 +1277,15 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
 // ---------------------------------------------------------------------------
 template <int L, int C, class T>
 struct ZSmem {
-  static constexpr int NT = 512;
+  static constexpr int NT = C >= 8 ? 512 : 256;
+  static constexpr int MINB = C >= 8 ? 1 : 2;   // narrow tiles: two CTAs per SM
   static constexpr size_t X_ELEMS = size_t(L) * C;
   static constexpr size_t S_ELEMS = size_t(L / 2) * C;
   static constexpr size_t SMEM_BYTES = (X_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>);
 };
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a) {
+__global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zconv_smem(SArgs a) {
   using ZS = ZSmem<L, C, T>;
   constexpr int NT = ZS::NT;
   constexpr int S8 = L / 8;          // span of the first (and last) radix-8 stage
@@ -1363,12 +1364,20 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, 1) k_zconv_smem(SArgs a) {
 
 template <class T, int L>
 cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = (L > 1024 && sizeof(cpx<T>) == 16) ? 4 : 8;   // the tile must fit in 227 KB
+  constexpr int C = (L > 1024 && sizeof(cpx<T>) == 16) ? 4 : 8;   // the tile must fit in 227 KB (4 columns measured no faster at L = 1024)
   using ZS = ZSmem<L, C, T>;
   auto kfn = k_zconv_smem<T, L, C>;
-  if (setup) return cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZS::SMEM_BYTES));
+  static int per_sm = 0;   // resident CTAs per SM, measured once at set-up
+  if (setup) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZS::SMEM_BYTES));
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kfn, ZS::NT, ZS::SMEM_BYTES);
+    per_sm = (e == cudaSuccess && nb > 0) ? nb : 1;
+    return e;
+  }
   const long long ntiles = (long long)L * (L / C) * std::max(1, a.nrhs);
-  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count))));
+  const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count) * std::max(1, per_sm))));
   kfn<<<gx, ZS::NT, ZS::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
