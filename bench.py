@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--matvec-reps", type=int, default=20)
+    ap.add_argument("--no-cufft", action="store_true",
+                    help="skip the cuFFT comparator (the same matvec through torch.fft on the full padded cube)")
     ap.add_argument("--lean", action="store_true",
                     help="lean plan (mixed solves only; needed for the largest grids, e.g. --n 1000)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -380,6 +382,9 @@ def ours_arm(args, world, rank, local):
         mv_bytes = matvec_alg_bytes(n, L, 8)
         matvec = {"fp32_ms": mv_ms, "alg_bytes": mv_bytes, "alg_GBps": mv_bytes / (mv_ms * 1e-3) / 1e9,
                   "frac_of_hbm": mv_bytes / (mv_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        if not args.no_cufft and rank == 0:
+            _last_ms[:] = [mv_ms]
+            matvec["cufft_comparator"] = cufft_comparator(plan, h_dev, N_dev, x32, y32, n, k, L, dev)
         del x32, y32
 
     # ---- plain FP64 GPU solve (comparator), once -------------------------------
@@ -469,6 +474,62 @@ def ours_arm(args, world, rank, local):
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+_last_ms = []   # our standalone matvec time, for the comparator's ratio
+
+
+def cufft_comparator(plan, h_dev, N_dev, x32, y_ours, n, k, L, dev, reps=5):
+    """The same FP32 B-form matvec y = x + S K (S x) through cuFFT (torch.fft) as a
+    library comparator, the way it is usually written: zero-pad S x into the full
+    L^3 cube, 3D FFT, multiply by the full spectrum, inverse 3D FFT, crop, add x.
+    Its spectrum is the FP64 FFT of the kernel cube, rounded to complex64 once
+    (outside the timing).  Not part of the library."""
+    import torch
+    d = 1.0 / n
+    idx = torch.arange(L, device=dev, dtype=torch.float64)
+    s = torch.where(idx <= L // 2, idx, idx - L)                       # signed offsets
+    s = torch.where(s.abs() <= n - 1, s, torch.full_like(s, float("inf")))
+    r = d * torch.sqrt(s[:, None, None] ** 2 + s[None, :, None] ** 2 + s[None, None, :] ** 2)
+    del s
+    c = torch.zeros(L, L, L, dtype=torch.complex128, device=dev)
+    ok = torch.isfinite(r) & (r > 0)
+    rr = r[ok]
+    c[ok] = (4 * math.pi * d ** 3) * torch.exp(1j * k * rr) / (4 * math.pi * rr)
+    del r, ok, rr
+    ghat = torch.fft.fftn(c).to(torch.complex64)
+    del c
+    torch.cuda.empty_cache()
+    S = torch.sqrt(h_dev * N_dev).to(torch.complex64)
+    pad = torch.zeros(L, L, L, dtype=torch.complex64, device=dev)
+
+    def matvec(x):
+        pad.zero_()
+        pad[:n, :n, :n] = (S * x).view(n, n, n)
+        f = torch.fft.fftn(pad)
+        f *= ghat
+        conv = torch.fft.ifftn(f)
+        return x + S * conv[:n, :n, :n].reshape(-1)
+
+    for _ in range(2):
+        y = matvec(x32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        y = matvec(x32)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    plan.matvec32(x32, "B", out=y_ours)
+    # compare the operator parts y - x (for random x the identity term dominates y)
+    diff = float(torch.linalg.vector_norm(y - y_ours) / torch.linalg.vector_norm(y_ours - x32))
+    del pad, ghat, S, y
+    torch.cuda.empty_cache()
+    return {"ms": ms, "speedup_of_ours": ms / max(1e-9, float(_last_ms[0])) if _last_ms else None,
+            "rel_l2_vs_ours_of_K_part": diff,
+            "how": "torch.fft.fftn/ifftn (cuFFT C2C, complex64) on the zero-padded L^3 cube + elementwise pad, "
+                   "spectrum multiply, crop and axpy"}
 
 
 def batched_leg(args, dev, n=128, ks=(1.0, 2.0, 4.0, 8.0), ndir=16, reps=3):

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define ORI_ABI_VERSION 2
+#define ORI_ABI_VERSION 3
 
 typedef struct ori_plan_s* ori_plan_t;
 
@@ -124,6 +124,12 @@ typedef struct {
                           error bound allows (see ori_solve_info.resid_updates);
                           0 recomputes b - B w every step                           */
   int    reserved[5];
+  const double* x0;    /* NULL (default): start from u = 0.  Else an initial guess of u
+                          on the device, n^3 complex128 per system (ori_cocg_solve_batch:
+                          system r at offset r n^3).  The solve starts from w = S x0
+                          with its true residual (one more FP64-class operator
+                          application, counted in fp64_matvecs); a zero right-hand
+                          side still gives u = 0.  Ignored by ori_adjoint_solve.   */
 } ori_solve_opts;
 
 typedef struct {

@@ -6,11 +6,11 @@ Submodules load lazily so that ``inputs`` (seeded generators) imports
 without CUDA.
 """
 
-__all__ = ["Plan", "OriSolve", "OriError", "solve_autograd", "solve_opts", "inputs"]
+__all__ = ["Plan", "OriSolve", "OriError", "solve", "solve_autograd", "solve_opts", "inputs"]
 
 
 def __getattr__(name):
-    if name in ("Plan", "OriSolve", "OriError", "solve_autograd", "solve_opts"):
+    if name in ("Plan", "OriSolve", "OriError", "solve", "solve_autograd", "solve_opts"):
         from . import ori
         return getattr(ori, name)
     raise AttributeError(name)

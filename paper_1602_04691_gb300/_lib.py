@@ -60,7 +60,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
                 ("alpha", C.c_double * 3), ("use_graph", C.c_int), ("residual", C.c_int),
-                ("resid_update", C.c_int), ("reserved", C.c_int * 5)]
+                ("resid_update", C.c_int), ("reserved", C.c_int * 5), ("x0", C.c_void_p)]
 
 
 class SolveInfo(C.Structure):

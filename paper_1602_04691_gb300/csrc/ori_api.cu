@@ -882,13 +882,14 @@ static ori_status read_heads(ori_plan_s* p, int nrhs) {
 template <class T>
 static ori_status cocg_inner(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, cpx<T>* r, cpx<T>* pp,
                              cpx<T>* q, const cpx<T>* S, const double* tols_host, int maxit, int check_every,
-                             bool use_graph, InnerResult* res) {
+                             bool use_graph, InnerResult* res, bool zero_x = true) {
   double* h_tols = p->h_small;
   for (int i = 0; i < nrhs; ++i) h_tols[i] = tols_host[i];
   ORI_CUDA(cudaMemcpyAsync(p->d_tols, h_tols, nrhs * sizeof(double), cudaMemcpyHostToDevice, p->ps));
   const int vg = vgrid(p, nrhs);
   ORI_VEC(p, ORI_PASS_VECTOR + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64),
-          (k_cocg_init<T><<<dim3(vg, nrhs), 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, p->d_tols, maxit)));
+          (k_cocg_init<T><<<dim3(vg, nrhs), 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, p->d_tols, maxit,
+                                                               zero_x ? 1 : 0)));
   ORI_TRY(read_heads(p, nrhs));
   auto any_running = [&]() {
     for (int i = 0; i < nrhs; ++i)
@@ -1033,7 +1034,7 @@ static ori_status push_doubles(ori_plan_s* p, double* dst, const double* src, in
 
 // Solve B w_r = b64_r for the batch (b64 and bnorm[r] ready); w -> p->w.
 static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* bnorm, const ori_solve_opts& o,
-                          ori_solve_info* info) {
+                          ori_solve_info* info, bool warm = false) {
   const long long n3 = p->n3;
   const size_t bytes64 = size_t(n3) * sizeof(cpx<double>) * nrhs;
   for (int i = 0; i < nrhs; ++i) {
@@ -1042,11 +1043,24 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
   const bool graph = o.use_graph != 0;
   std::vector<InnerResult> ir(nrhs);
   std::vector<double> tin(nrhs);
+  // warm start: w holds S x0; its true residual r0 = b - B w starts the solve
+  std::vector<double> rn0(bnorm, bnorm + nrhs);
+  if (warm) {
+    for (int i = 0; i < nrhs; ++i)   // a zero right-hand side has the solution 0 whatever the guess
+      if (bnorm[i] == 0.0) ORI_CUDA(cudaMemsetAsync(p->w + size_t(i) * size_t(n3), 0, size_t(n3) * sizeof(cpx<double>), p->ps));
+    for (int i = 0; i < nrhs; ++i) p->h_skip[i] = bnorm[i] > 0 ? 0 : 1;
+    ORI_TRY(push_skip(p, nrhs));
+    const bool use_df = o.precision != ORI_FP64 && o.residual == ORI_DF;
+    ORI_TRY(fp64_residual(p, nrhs, rhs_per_k, use_df, rn0.data()));
+    for (int i = 0; i < nrhs; ++i) info[i].fp64_matvecs += bnorm[i] > 0 ? 1 : 0;
+  }
   if (o.precision == ORI_FP64) {
-    ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
-    for (int i = 0; i < nrhs; ++i) tin[i] = bnorm[i] > 0 ? o.tol : 1.0;
+    if (!warm) ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+    // COCG from w (0, or the warm start) to ||r|| <= tol ||b||
+    for (int i = 0; i < nrhs; ++i)
+      tin[i] = bnorm[i] > 0 && rn0[i] > 0 ? std::min(1.0, o.tol * bnorm[i] / rn0[i]) : 1.0;
     ORI_TRY(cocg_inner<double>(p, nrhs, rhs_per_k, p->w, p->r64, p->p64, p->q64, p->S64, tin.data(), o.maxit,
-                               o.check_every, graph, ir.data()));
+                               o.check_every, graph, ir.data(), !warm));
     for (int i = 0; i < nrhs; ++i) p->h_skip[i] = bnorm[i] > 0 ? 0 : 1;
     ORI_TRY(push_skip(p, nrhs));
     std::vector<double> rn(nrhs, 0.0);
@@ -1055,7 +1069,7 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
       info[i].iters = ir[i].iters;
       info[i].outer_iters = 1;
       info[i].relres_recur = ir[i].relres_recur;
-      info[i].fp64_matvecs = 1;
+      info[i].fp64_matvecs += 1;
       info[i].relres = bnorm[i] > 0 ? rn[i] / bnorm[i] : 0.0;
       info[i].relres_bound = 1e-14;
       if (bnorm[i] == 0) info[i].status = ORI_OK;
@@ -1066,11 +1080,15 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
     return ORI_OK;
   }
   // mixed: FP32 COCG on the normalised residual, FP64-class refinement
-  ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
-  ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
-  std::vector<double> rn(bnorm, bnorm + nrhs), err(nrhs, 0.0), recur(nrhs, 0.0);
+  if (!warm) {
+    ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
+    ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+  }
+  std::vector<double> rn(rn0), err(nrhs, 0.0), recur(nrhs, 0.0);
+  if (warm)
+    for (int i = 0; i < nrhs; ++i) err[i] = (o.residual == ORI_DF ? kDfOperatorRelErr : 1e-14) * bnorm[i];
   std::vector<int> active(nrhs), last_done(nrhs, DONE_CONVERGED), total(nrhs, 0), outer(nrhs, 0);
-  for (int i = 0; i < nrhs; ++i) active[i] = bnorm[i] > 0 && rn[i] > o.tol * bnorm[i];
+  for (int i = 0; i < nrhs; ++i) active[i] = bnorm[i] > 0 && rn[i] + err[i] > o.tol * bnorm[i];
   for (int step = 0; step < o.max_outer; ++step) {
     bool any = false;
     for (int i = 0; i < nrhs; ++i) any = any || active[i];
@@ -1216,7 +1234,10 @@ static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs
   ORI_TRY(read_heads(p, nrhs));
   std::vector<double> bnorm(nrhs);
   for (int i = 0; i < nrhs; ++i) bnorm[i] = std::sqrt(p->h_sc[i].sum.x);
-  ORI_TRY(solve_B(p, nrhs, ndir, bnorm.data(), o, infos));
+  if (o.x0 != nullptr)
+    ORI_VEC(p, ORI_PASS_VECTOR, (k_scale_guess<<<dim3(vg, nrhs), 256, 0, p->ps>>>(
+                                    reinterpret_cast<const cpx<double>*>(o.x0), p->S64, p->w, p->n3)));
+  ORI_TRY(solve_B(p, nrhs, ndir, bnorm.data(), o, infos, o.x0 != nullptr));
   // u = w / S; cells with S = 0 take u = u0 - K (S w) (one more FP64 application)
   if (p->zero_S == 0) {
     ORI_VEC(p, ORI_PASS_VECTOR,

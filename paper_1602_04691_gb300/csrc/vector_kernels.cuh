@@ -180,7 +180,7 @@ __global__ void k_adj_rhs(const cpx<double>* __restrict__ ec, const cpx<double>*
 // Sums in T over 8 elements per thread, then in FP64.
 template <class T>
 __global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n3, Scalars* sc0,
-                            double2* partials0, const double* __restrict__ tols, int maxit) {
+                            double2* partials0, const double* __restrict__ tols, int maxit, int zero_x) {
   __shared__ double2 red[64];
   __shared__ int s_last;
   const int rb = blockIdx.y;
@@ -200,7 +200,7 @@ __global__ void k_cocg_init(const cpx<T>* __restrict__ r, cpx<T>* x, long long n
       const long long i = base + u * stride;
       if (i < n3) {
         const cpx<T> rv = r[i];
-        x[i] = czero<T>();
+        if (zero_x) x[i] = czero<T>();   // else x holds an initial guess whose residual is r
         rs = rs + cmul(rv, rv);
         ns += rv.x * rv.x + rv.y * rv.y;
       }
@@ -476,6 +476,16 @@ __global__ void k_field_finish(const double2* __restrict__ partials, int S, cons
     }
     out[pi] = {t.x, t.y};
   }
+}
+
+// Initial guess of the symmetrised system from a guess of u: w = S x0, per system.
+__global__ void k_scale_guess(const cpx<double>* __restrict__ x0, const cpx<double>* __restrict__ S,
+                              cpx<double>* w, long long n3) {
+  x0 += blockIdx.y * n3;
+  w += blockIdx.y * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
+       i += (long long)gridDim.x * blockDim.x)
+    w[i] = cmul(S[i], x0[i]);
 }
 
 // Widen a complex64 vector to complex128 / narrow complex128 to complex64.

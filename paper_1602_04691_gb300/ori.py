@@ -37,7 +37,7 @@ def _need(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
 
 def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_outer=8,
                check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True, residual="df",
-               resid_update=True) -> _lib.SolveOpts:
+               resid_update=True, x0=None) -> _lib.SolveOpts:
     lib = _lib.load()
     o = _lib.SolveOpts()
     lib.ori_default_solve_opts(C.byref(o))
@@ -52,6 +52,11 @@ def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_oute
     o.use_graph = 1 if use_graph else 0
     o.residual = _PREC[residual]
     o.resid_update = 1 if resid_update else 0
+    if x0 is not None:
+        if not (isinstance(x0, torch.Tensor) and x0.is_cuda and x0.dtype == torch.complex128
+                and x0.is_contiguous()):
+            raise TypeError("x0 must be a contiguous complex128 CUDA tensor")
+        o.x0 = x0.data_ptr()
     return o
 
 
@@ -201,6 +206,8 @@ class Plan:
         m = self.n ** 3
         if rhs is not None:
             rhs = _need(rhs, torch.complex128, m, "rhs")
+        if kw.get("x0") is not None:
+            kw["x0"] = _need(kw["x0"], torch.complex128, m, "x0")
         u = torch.empty(m, dtype=torch.complex128, device=self.device) if out is None else out
         o = solve_opts(**kw)
         info = _lib.SolveInfo()
@@ -238,6 +245,8 @@ class Plan:
             al = (C.c_double * (3 * ndir))(*[c for a in dirs for c in a])
         u = (torch.empty(nk * ndir * m, dtype=torch.complex128, device=self.device)
              if out is None else _need(out, torch.complex128, nk * ndir * m, "out"))
+        if kw.get("x0") is not None:
+            kw["x0"] = _need(kw["x0"], torch.complex128, nk * ndir * m, "x0")
         o = solve_opts(**kw)
         infos = (_lib.SolveInfo * (nk * ndir))()
         st = _lib.load().ori_cocg_solve_batch(self.handle, ndir, C.cast(al, C.c_void_p) if al is not None else None,
@@ -285,6 +294,18 @@ class Plan:
         d = info.as_dict()
         d["returned"] = st
         return gh, gN, d
+
+
+def solve(h: torch.Tensor, N: torch.Tensor, k, side: float = 1.0, origin=(0.0, 0.0, 0.0), rhs=None,
+          c_S: float | None = None, lean: bool = False, **kw):
+    """One call: build a plan for the n^3 grid of h (complex128) and N (float64), solve
+    Eq. 2.19 (rhs None: the plane wave of direction `alpha`), free the plan.  Returns
+    (u, info).  Keep a Plan instead when solving repeatedly on one medium."""
+    n = int(round(h.numel() ** (1.0 / 3.0)))
+    if n ** 3 != h.numel():
+        raise ValueError("h must hold n^3 values")
+    with Plan(n, k, h, N, side=side, origin=origin, c_S=c_S, lean=lean) as plan:
+        return plan.solve(rhs=rhs, **kw)
 
 
 class OriSolve(torch.autograd.Function):

@@ -214,3 +214,40 @@ def test_set_schedule_rejects_bad_fields():
         with pytest.raises(OriError):
             plan.set_schedule(bad)
     assert plan.schedule()["vec_ctas_per_sm"] == 8
+
+
+def test_warm_start_from_solution_and_from_a_perturbed_guess():
+    """x0 (initial guess of u): the exact solution needs no refinement step;
+    a perturbed solution converges to the same u in fewer iterations than a
+    cold start; a zero right-hand side still gives u = 0."""
+    n, k = 20, 4.0
+    h, N = inputs.random_h_N(n, 97)
+    plan = make_plan(n, k, h, N)
+    for precision, tol in (("mixed", 1e-6), ("fp64", 1e-10)):
+        uc, ic = plan.solve(tol=tol, precision=precision)
+        ue, ie = plan.solve(tol=tol, precision=precision, x0=uc.clone())
+        assert ie["relres"] <= tol and ie["fp64_matvecs"] >= 1
+        if precision == "mixed":
+            assert ie["iters"] == 0
+        assert rel(ue.cpu().numpy(), uc.cpu().numpy()) < 10 * tol
+        noise = torch.from_numpy(inputs.random_complex(n ** 3, 98)).to(DEV) * 1e-3
+        up, ip = plan.solve(tol=tol, precision=precision, x0=uc + noise * uc.abs().mean())
+        assert ip["relres"] <= tol and ip["iters"] < ic["iters"]
+        assert rel(up.cpu().numpy(), uc.cpu().numpy()) < 100 * tol
+    zero = torch.zeros(n ** 3, dtype=torch.complex128, device=DEV)
+    uz, iz = plan.solve(rhs=zero, tol=1e-6, x0=torch.ones_like(zero))
+    assert float(uz.abs().max()) == 0.0
+
+
+def test_batch_warm_start_and_one_call_solve():
+    from paper_1602_04691_gb300 import solve
+    n, ks = 12, [1.5, 3.0]
+    dirs = [(0.0, 0.0, 1.0), (1.0, 0.0, 0.0)]
+    h, N = inputs.random_h_N(n, 99)
+    plan = make_plan(n, ks, h, N)
+    ub, ib = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
+    uw, iw = plan.solve_batch(dirs, tol=1e-6, precision="mixed", x0=ub.reshape(-1).clone())
+    assert all(i["iters"] == 0 and i["relres"] <= 1e-6 for i in iw)
+    assert rel(uw.cpu().numpy(), ub.cpu().numpy()) < 1e-5
+    u1, i1 = solve(to_dev(h), to_dev(N), ks[0], tol=1e-6, alpha=dirs[1])
+    assert rel(u1.cpu().numpy(), ub[0, 1].cpu().numpy()) < 1e-5
