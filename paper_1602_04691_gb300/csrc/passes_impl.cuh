@@ -1415,7 +1415,7 @@ __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, int per
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT)) k_yfwd_pipe(SArgs a) {
+__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 512 ? 1 : (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT))) k_yfwd_pipe(SArgs a) {
   using TL = Tile<L, C, T>;
   using YP = YPipe<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
@@ -1510,7 +1510,7 @@ __device__ __forceinline__ void yinv_prefetch(const SArgs& a, int tile, int per_
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 256 ? 2 : 512 / YInvPipe<L, C>::NT)) k_yinv_pipe(SArgs a) {
+__global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 512 ? 1 : (YInvPipe<L, C>::NT >= 256 ? 2 : 512 / YInvPipe<L, C>::NT))) k_yinv_pipe(SArgs a) {
   using T = float;
   using TL = Tile<L, C, T>;
   using YP = YInvPipe<L, C>;
@@ -1577,7 +1577,7 @@ __global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 256
 
 template <int L>
 cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = cols_strided<float>();
+  constexpr int C = 16;   // 128-byte rows (8 columns: 1.42 ms, 16: 1.24 ms at n = 512)
   using YP = YInvPipe<L, C>;
   auto kfn = k_yinv_pipe<L, C>;
   static int per_sm = 0;
@@ -1600,7 +1600,7 @@ cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
 
 template <class T, int L>
 cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = cols_strided<T>();
+  constexpr int C = 16;   // 128-byte rows (8 columns: 1.37 ms, 16: 1.30 ms at n = 512)
   using YP = YPipe<L, C, T>;
   auto kfn = k_yfwd_pipe<T, L, C>;
   static int per_sm = 0;
