@@ -1277,8 +1277,8 @@ __global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256
 // ---------------------------------------------------------------------------
 template <int L, int C, class T>
 struct ZSmem {
-  static constexpr int NT = C >= 8 ? 512 : 256;
-  static constexpr int MINB = C >= 8 ? 1 : 2;   // narrow tiles: two CTAs per SM
+  static constexpr int NT = 512;
+  static constexpr int MINB = 1;   // (256 threads, two CTAs per SM measured 9% slower at L = 2048)
   static constexpr size_t X_ELEMS = size_t(L) * C;
   static constexpr size_t S_ELEMS = size_t(L / 2) * C;
   static constexpr size_t SMEM_BYTES = (X_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>);
@@ -1364,7 +1364,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
 
 template <class T, int L>
 cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = (L > 1024 && sizeof(cpx<T>) == 16) ? 4 : 8;   // the tile must fit in 227 KB (4 columns measured no faster at L = 1024)
+  constexpr int C = (L > 1024 && sizeof(cpx<T>) == 16) ? 4 : 8;   // the tile must fit in 227 KB
   using ZS = ZSmem<L, C, T>;
   auto kfn = k_zconv_smem<T, L, C>;
   static int per_sm = 0;   // resident CTAs per SM, measured once at set-up
@@ -1704,7 +1704,7 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
     if constexpr (SMODE == SMODE_ZCONV) {
       return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
     } else {
-      constexpr int CS = 4;
+      constexpr int CS = 4;   // (8 columns measured slower at L = 2048: fewer resident CTAs)
       using LS = LSmem<L, CS, T>;
       auto kfs = k_strided_smem<T, L, CS, SMODE, (SMODE == SMODE_FWD ? HALF : true)>;
       if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
