@@ -242,6 +242,17 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def reference_arm(args, world, rank):
     if rank != 0:
         return
@@ -331,10 +342,7 @@ def ours_arm(args, world, rank, local):
     ms_total = e0.elapsed_time(e1)
     stats = plan.stats()
     plan.set_timing(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, dev)
     ms_per_step = ms_total / args.steps
     value = ms_total / 1e3 / (args.steps * world)
 
