@@ -2,6 +2,7 @@
 // (FP64, and mixed FP32 / FP64-class refinement), batched solves over several
 // incidence directions and wave numbers, and the adjoint gradient.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -26,6 +27,15 @@ template <class T> cudaError_t run_strided(int, int, bool, const SArgs&, cudaStr
 }  // namespace ori
 
 using namespace ori;
+
+// NVTX range for profilers (nsys, ncu --nvtx): pushed on construction, popped
+// on scope exit.  Host-side only; costs nothing when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // Errors
@@ -366,6 +376,7 @@ template <class T>
 static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s, Mask mask,
                            int nrhs = 1, int rhs_per_k = 1) {
   constexpr int K = ArithOf<T>::kind;
+  NvtxRange nvtx(K == 0 ? "ori operator fp32" : (K == ORI_PASS_FP64 ? "ori operator fp64" : "ori operator df"));
   const bool f32 = K == 0;
   cpx<T>* T1 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T1f : (void*)p->T1d);
   cpx<T>* T2 = reinterpret_cast<cpx<T>*>(f32 ? (void*)p->T2f : (void*)p->T2d);
@@ -495,6 +506,7 @@ static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N
 // paired FP32 with c_S |Delta| / L^3 folded in, plus the Z-tile-ordered FP32
 // copy.  Transient memory: the H^3 octant and a batch of L^2 planes.
 static ori_status build_spectrum(ori_plan_s* p) {
+  NvtxRange nvtx("ori plan spectrum");
   const int L = p->L, n = p->n, H = p->H;
   const long long L3 = (long long)L * L * L;
   const long long H3 = (long long)H * H * H;
@@ -883,6 +895,7 @@ template <class T>
 static ori_status cocg_inner(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, cpx<T>* r, cpx<T>* pp,
                              cpx<T>* q, const cpx<T>* S, const double* tols_host, int maxit, int check_every,
                              bool use_graph, InnerResult* res, bool zero_x = true) {
+  NvtxRange nvtx(sizeof(T) == 4 ? "ori cocg fp32" : "ori cocg fp64");
   double* h_tols = p->h_small;
   for (int i = 0; i < nrhs; ++i) h_tols[i] = tols_host[i];
   ORI_CUDA(cudaMemcpyAsync(p->d_tols, h_tols, nrhs * sizeof(double), cudaMemcpyHostToDevice, p->ps));
@@ -981,6 +994,7 @@ static ori_status cocg_inner(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, 
 // r64_r = b64_r - B w_r for the RHS whose skip flag is 0 (complex128 vectors;
 // FFT passes in paired FP32 or native FP64).  Fills rn[r] = ||r64_r||.
 static ori_status fp64_residual(ori_plan_s* p, int nrhs, int rhs_per_k, bool use_df, double* rn) {
+  NvtxRange nvtx("ori refinement residual");
   const long long bsv = p->n3 * (long long)sizeof(cpx<double>);
   XArgs pro{}, epi{};
   pro.mode = use_df ? PRO_SCALE_D : PRO_SCALE;
@@ -1043,6 +1057,9 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
   const bool graph = o.use_graph != 0;
   std::vector<InnerResult> ir(nrhs);
   std::vector<double> tin(nrhs);
+  // a non-finite right-hand side (NaN/Inf in rhs, h or N) is reported, not solved
+  std::vector<char> bad(nrhs);
+  for (int i = 0; i < nrhs; ++i) bad[i] = !std::isfinite(bnorm[i]);
   // warm start: w holds S x0; its true residual r0 = b - B w starts the solve
   std::vector<double> rn0(bnorm, bnorm + nrhs);
   if (warm) {
@@ -1072,7 +1089,8 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
       info[i].fp64_matvecs += 1;
       info[i].relres = bnorm[i] > 0 ? rn[i] / bnorm[i] : 0.0;
       info[i].relres_bound = 1e-14;
-      if (bnorm[i] == 0) info[i].status = ORI_OK;
+      if (bad[i]) info[i].status = ORI_ERR_NONFINITE;
+      else if (bnorm[i] == 0) info[i].status = ORI_OK;
       else info[i].status = ir[i].done == DONE_CONVERGED
                                 ? (info[i].relres <= 10 * o.tol ? ORI_OK : ORI_ERR_NOT_CONVERGED)
                                 : status_of(ir[i].done);
@@ -1088,7 +1106,7 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
   if (warm)
     for (int i = 0; i < nrhs; ++i) err[i] = (o.residual == ORI_DF ? kDfOperatorRelErr : 1e-14) * bnorm[i];
   std::vector<int> active(nrhs), last_done(nrhs, DONE_CONVERGED), total(nrhs, 0), outer(nrhs, 0);
-  for (int i = 0; i < nrhs; ++i) active[i] = bnorm[i] > 0 && rn[i] + err[i] > o.tol * bnorm[i];
+  for (int i = 0; i < nrhs; ++i) active[i] = !bad[i] && bnorm[i] > 0 && rn[i] + err[i] > o.tol * bnorm[i];
   for (int step = 0; step < o.max_outer; ++step) {
     bool any = false;
     for (int i = 0; i < nrhs; ++i) any = any || active[i];
@@ -1180,7 +1198,8 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
     info[i].relres = bnorm[i] > 0 ? rn[i] / bnorm[i] : 0.0;
     info[i].relres_bound = bnorm[i] > 0 ? err[i] / bnorm[i] : 0.0;
     info[i].relres_recur = recur[i];
-    if (bnorm[i] == 0 || info[i].relres + info[i].relres_bound <= o.tol) info[i].status = ORI_OK;
+    if (bad[i] || !std::isfinite(rn[i])) info[i].status = ORI_ERR_NONFINITE;
+    else if (bnorm[i] == 0 || info[i].relres + info[i].relres_bound <= o.tol) info[i].status = ORI_OK;
     else if (last_done[i] == DONE_NONFINITE) info[i].status = ORI_ERR_NONFINITE;
     else if (last_done[i] == DONE_BREAKDOWN) info[i].status = ORI_ERR_BREAKDOWN;
     else info[i].status = ORI_ERR_NOT_CONVERGED;
@@ -1209,6 +1228,7 @@ static ori_status check_solve_opts(const ori_solve_opts* in, ori_solve_opts* o) 
 // plan's wave numbers) and direction id.  rhs_dev == NULL: plane waves.
 static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs_dev, const double* dirs_host,
                               double* u_dev, const ori_solve_opts& o, ori_solve_info* infos, cudaStream_t user) {
+  NvtxRange nvtx("ori solve");
   const int nrhs = nk * ndir;
   if (p->lean && (o.precision == ORI_FP64 || o.residual == ORI_FP64))
     return fail(ORI_ERR_UNSUPPORTED, "a lean plan solves in mixed precision with the paired-FP32 residual only");
@@ -1430,6 +1450,7 @@ static ori_status time_fp32_update(ori_plan_s* p, int nrhs, int reps, float* ms)
 }
 
 static ori_status autotune(ori_plan_s* p, int nrhs, int reps, ori_schedule* best_out, float* best_ms) {
+  NvtxRange nvtx("ori autotune");
   ORI_TRY(ensure_capacity(p, nrhs));
   const size_t n3 = size_t(p->n3) * size_t(nrhs);
   for (cpx<float>* v : {p->x32, p->p32, p->r32, p->q32})
