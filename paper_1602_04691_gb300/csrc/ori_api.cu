@@ -122,6 +122,7 @@ struct ori_plan_s {
   double* d_scl = nullptr;         // scale factors (normalise / accumulate)
   double* d_coef = nullptr;        // residual-update coefficients
   double* d_kv = nullptr;          // wave number of each RHS (plane waves)
+  cpx<double>* d_phase = nullptr;  // 3n plane-wave phase factors per RHS
   double* d_dir = nullptr;         // 3 per RHS (plane waves)
   int* d_skip = nullptr;           // 1 = this RHS takes no part in a pass
   double* h_small = nullptr;       // pinned: 7 * cap doubles
@@ -266,6 +267,7 @@ static void free_capacity(ori_plan_s* p) {
   for (cpx<float>** v : {&p->x32, &p->r32, &p->p32, &p->q32}) free_n(p, *v, c * n3);
   for (double** v : {&p->d_tols, &p->d_scl, &p->d_coef, &p->d_kv}) free_n(p, *v, c);
   free_n(p, p->d_dir, 3 * c);
+  free_n(p, p->d_phase, 3 * size_t(p->n) * c);
   free_n(p, p->d_skip, c);
   if (p->h_sc) cudaFreeHost(p->h_sc);
   if (p->h_small) cudaFreeHost(p->h_small);
@@ -301,6 +303,7 @@ static ori_status ensure_capacity(ori_plan_s* p, int nrhs) {
   for (cpx<float>** v : {&p->x32, &p->r32, &p->p32, &p->q32}) ORI_TRY(alloc_n(p, v, c * n3));
   for (double** v : {&p->d_tols, &p->d_scl, &p->d_coef, &p->d_kv}) ORI_TRY(alloc_n(p, v, c));
   ORI_TRY(alloc_n(p, &p->d_dir, 3 * c));
+  ORI_TRY(alloc_n(p, &p->d_phase, 3 * size_t(p->n) * c));
   ORI_TRY(alloc_n(p, &p->d_skip, c));
   if (cudaMallocHost(&p->h_sc, c * sizeof(Scalars)) != cudaSuccess ||
       cudaMallocHost(&p->h_small, 7 * c * sizeof(double)) != cudaSuccess ||
@@ -1248,9 +1251,13 @@ static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs
   ORI_TRY(push_doubles(p, p->d_dir, dv.data(), 3 * nrhs));
   const int vg = vgrid(p, nrhs);
   ORI_VEC(p, ORI_PASS_VECTOR,
+          (k_phases<<<dim3(unsigned((3 * p->n + 255) / 256), nrhs), 256, 0, p->ps>>>(
+              p->d_kv, p->d_dir, p->n, p->d, p->origin[0], p->origin[1], p->origin[2], p->d_phase)));
+  // u0 is kept only where S = 0 cells need it for the recovery
+  ORI_VEC(p, ORI_PASS_VECTOR,
           (k_rhs<<<dim3(vg, nrhs), 256, rhs_dev ? 0 : 3 * size_t(p->n) * sizeof(cpx<double>), p->ps>>>(
-              reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->u0, p->b64, p->n, p->d, p->origin[0],
-              p->origin[1], p->origin[2], p->d_kv, p->d_dir, p->sc, p->partials)));
+              reinterpret_cast<const cpx<double>*>(rhs_dev), p->S64, p->zero_S ? p->u0 : nullptr, p->b64, p->n,
+              p->d_phase, p->sc, p->partials)));
   ORI_TRY(read_heads(p, nrhs));
   std::vector<double> bnorm(nrhs);
   for (int i = 0; i < nrhs; ++i) bnorm[i] = std::sqrt(p->h_sc[i].sum.x);

@@ -114,9 +114,22 @@ __device__ __forceinline__ void block_partial2(double2 a, double2 b, double2* re
 // factors over the axes, exp(ik(a_x x + a_y y + a_z z)) = e_x(ix) e_y(iy)
 // e_z(iz), so each block evaluates 3n FP64 phases into shared memory and
 // every cell costs two complex products.
+// Phase factors of the separable plane wave, once per right-hand side:
+// out[rb][axis * n + i] = exp(i k_rb a_rb,axis (o_axis + (i + 1/2) d)).
+__global__ void k_phases(const double* __restrict__ kvals, const double* __restrict__ dirs, int n, double d,
+                         double ox, double oy, double oz, cpx<double>* out) {
+  const int rb = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int axis = t / n, i = t - axis * n;
+  const double o = axis == 0 ? ox : (axis == 1 ? oy : oz);
+  double sn, cs;
+  sincos(kvals[rb] * dirs[3 * rb + axis] * (o + (i + 0.5) * d), &sn, &cs);
+  out[(long long)rb * 3 * n + t] = {cs, sn};
+}
+
 __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __restrict__ S,
-                      cpx<double>* u0, cpx<double>* b, int n, double d, double ox, double oy,
-                      double oz, const double* __restrict__ kvals, const double* __restrict__ dirs,
+                      cpx<double>* u0, cpx<double>* b, int n, const cpx<double>* __restrict__ phases,
                       Scalars* sc0, double2* partials0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<double>* e = reinterpret_cast<cpx<double>*>(smraw);   // [3][n]
@@ -129,16 +142,9 @@ __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __
   if (rhs != nullptr) rhs += rb * n3;
   if (u0 != nullptr) u0 += rb * n3;
   b += rb * n3;
-  if (rhs == nullptr) {
-    const double k = kvals[rb];
-    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
-      const int axis = t / n, i = t - axis * n;
-      const double o = axis == 0 ? ox : (axis == 1 ? oy : oz);
-      const double a = dirs[3 * rb + axis];
-      double sn, cs;
-      sincos(k * a * (o + (i + 0.5) * d), &sn, &cs);
-      e[t] = {cs, sn};
-    }
+  if (rhs == nullptr) {   // the 3n phase factors of this right-hand side (k_phases)
+    const cpx<double>* ph = phases + (long long)rb * 3 * n;
+    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) e[t] = ph[t];
     __syncthreads();
   }
   double acc = 0.0;
