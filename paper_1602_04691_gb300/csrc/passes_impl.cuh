@@ -717,13 +717,14 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
 // ---------------------------------------------------------------------------
 template <int L, int C, class T>
 struct LSmem {
-  static constexpr int NT = 256;
+  static constexpr int NT = C >= 4 ? 256 : 64 * C;
+  static constexpr int MINB = C >= 4 ? 2 : 4;       // narrow tiles: more independent CTAs per SM
   static constexpr size_t X_ELEMS = size_t(L) * C;
   static constexpr size_t SMEM_BYTES = (X_ELEMS + size_t(L)) * sizeof(cpx<T>);
 };
 
 template <class T, int L, int C, int SMODE, bool HALF = true>
-__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a0) {
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_strided_smem(SArgs a0) {
   const SArgs a = s_for_rhs(a0, blockIdx.y);
   using LS = LSmem<L, C, T>;
   constexpr int NT = LS::NT, S8 = L / 8;
@@ -790,7 +791,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_strided_smem(SArgs a0
 }
 
 template <class T, int L, int C, bool HALF = true>
-__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a0) {
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xfwd_smem(XArgs a0) {
   const XArgs a = x_for_rhs(a0, blockIdx.y);
   using LS = LSmem<L, C, T>;
   constexpr int NT = LS::NT, S8 = L / 8;
@@ -830,7 +831,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xfwd_smem(XArgs a0) {
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(LSmem<L, C, T>::NT, 2) k_xinv_smem(XArgs a0, Scalars* sc0, int fin) {
+__global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xinv_smem(XArgs a0, Scalars* sc0, int fin) {
   const XArgs a = x_for_rhs(a0, blockIdx.y);
   Scalars* sc = sc0 == nullptr ? nullptr : sc0 + blockIdx.y;
   using LS = LSmem<L, C, T>;
@@ -929,7 +930,7 @@ cudaError_t launch_xfwd_reg_L(const XArgs& a, cudaStream_t s, bool setup) {
     }
   }
   if constexpr (std::is_same<T, dfl>::value && HALF && L >= 64) {
-    constexpr int CS = 4;
+    constexpr int CS = 2;   // two lines per CTA, four CTAs per SM
     using LS = LSmem<L, CS, T>;
     auto kfs = k_xfwd_smem<T, L, CS>;
     if (setup) return cudaFuncSetAttribute(kfs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LS::SMEM_BYTES));
@@ -974,7 +975,7 @@ cudaError_t launch_xinv_reg_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t
   if constexpr (sizeof(T) == 4 && L >= 64) {
     return launch_xinv_pipe_L<L>(a, sc, fin, s, setup, nblocks);
   } else if constexpr (std::is_same<T, dfl>::value && L >= 64) {
-    constexpr int CS = 4;
+    constexpr int CS = 2;   // two lines per CTA, four CTAs per SM
     using LS = LSmem<L, CS, T>;
     auto kfs = k_xinv_smem<T, L, CS>;
     const unsigned grid = unsigned((a.nlines + CS - 1) / CS);
