@@ -25,14 +25,37 @@ def _stream_ptr(stream=None) -> int:
     return int(s.cuda_stream)
 
 
+def _plain(t: torch.Tensor) -> torch.Tensor:
+    """A dense tensor whose memory holds its values.  torch.conj() and negation
+    can return lazy views (a conjugate or negative bit over the original
+    memory) that stay lazy under .contiguous(); C reads the memory, so the bits
+    are resolved first."""
+    return t.resolve_conj().resolve_neg().contiguous()
+
+
 def _need(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
+    """An input argument: checked, then made plain (see _plain)."""
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if t.numel() != numel:
         raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
-    return t.contiguous()
+    return _plain(t)
+
+
+def _out(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
+    """An output argument: written in place, so it must already be dense memory
+    of the right type and size (a copy would leave the caller's tensor unwritten)."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    if not t.is_contiguous() or t.is_conj() or t.is_neg():
+        raise ValueError(f"{name} must be contiguous, without a lazy conjugate or negative bit")
+    return t
 
 
 def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_outer=8,
@@ -54,8 +77,8 @@ def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_oute
     o.resid_update = 1 if resid_update else 0
     if x0 is not None:
         if not (isinstance(x0, torch.Tensor) and x0.is_cuda and x0.dtype == torch.complex128
-                and x0.is_contiguous()):
-            raise TypeError("x0 must be a contiguous complex128 CUDA tensor")
+                and x0.is_contiguous() and not x0.is_conj() and not x0.is_neg()):
+            raise TypeError("x0 must be a contiguous complex128 CUDA tensor without a lazy conjugate or negative bit")
         o.x0 = x0.data_ptr()
     return o
 
@@ -194,7 +217,7 @@ class Plan:
     def matvec32(self, x: torch.Tensor, form: str = "B", out: torch.Tensor | None = None, stream=None):
         """The FP32 operator on complex64 vectors (what the mixed solver iterates with)."""
         x = _need(x, torch.complex64, self.n ** 3, "x")
-        y = torch.empty_like(x) if out is None else out
+        y = torch.empty_like(x) if out is None else _out(out, torch.complex64, self.n ** 3, "out")
         _lib.check(_lib.load().ori_matvec32(self.handle, x.data_ptr(), y.data_ptr(), _FORMS[form],
                                             _stream_ptr(stream)), "ori_matvec32")
         return y
@@ -208,7 +231,7 @@ class Plan:
             rhs = _need(rhs, torch.complex128, m, "rhs")
         if kw.get("x0") is not None:
             kw["x0"] = _need(kw["x0"], torch.complex128, m, "x0")
-        u = torch.empty(m, dtype=torch.complex128, device=self.device) if out is None else out
+        u = torch.empty(m, dtype=torch.complex128, device=self.device) if out is None else _out(out, torch.complex128, m, "out")
         o = solve_opts(**kw)
         info = _lib.SolveInfo()
         st = _lib.load().ori_cocg_solve(self.handle, rhs.data_ptr() if rhs is not None else None,
@@ -244,7 +267,7 @@ class Plan:
             ndir = len(dirs)
             al = (C.c_double * (3 * ndir))(*[c for a in dirs for c in a])
         u = (torch.empty(nk * ndir * m, dtype=torch.complex128, device=self.device)
-             if out is None else _need(out, torch.complex128, nk * ndir * m, "out"))
+             if out is None else _out(out, torch.complex128, nk * ndir * m, "out"))
         if kw.get("x0") is not None:
             kw["x0"] = _need(kw["x0"], torch.complex128, nk * ndir * m, "x0")
         o = solve_opts(**kw)
@@ -268,7 +291,7 @@ class Plan:
         if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float64
                 and points.dim() == 2 and points.shape[1] == 3):
             raise TypeError("points must be a float64 CUDA tensor of shape (npts, 3)")
-        points = points.contiguous()
+        points = _plain(points)
         out = torch.empty(points.shape[0], dtype=torch.complex128, device=self.device)
         al = None if alpha is None else (C.c_double * 3)(*[float(v) for v in alpha])
         _lib.check(_lib.load().ori_field(self.handle, u.data_ptr(), int(points.shape[0]), points.data_ptr(),

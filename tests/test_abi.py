@@ -76,3 +76,21 @@ def test_invalid_arguments_rejected_before_device_work(libpath):
     assert st == _lib.ORI_ERR_INVALID_ARG
     assert lib.ori_matvec(None, 1, 2, 0, 0, None) == _lib.ORI_ERR_INVALID_ARG
     assert lib.ori_cocg_solve(None, None, 1, None, None, None) == _lib.ORI_ERR_INVALID_ARG
+
+
+def test_binding_resolves_lazy_conjugate_and_negative_views():
+    """torch.conj() and negation can return views whose memory still holds the
+    original values (a conjugate or negative bit), and .contiguous() keeps
+    them lazy.  The binding hands raw pointers to C, so every input must be
+    made plain first and no output may carry such a bit."""
+    import torch
+    from paper_1602_04691_gb300.ori import _plain
+    x = torch.tensor([1 + 2j, 3 - 4j, -0.5 + 0.25j], dtype=torch.complex128)
+    c = x.conj()
+    assert c.contiguous().is_conj()                  # the trap: memory still holds x
+    p = _plain(c)
+    assert not p.is_conj() and not p.is_neg()
+    assert torch.equal(torch.view_as_real(p), torch.view_as_real(x).mul(torch.tensor([1.0, -1.0], dtype=torch.float64)))
+    q = _plain(torch._neg_view(c))
+    assert not q.is_conj() and not q.is_neg()
+    assert torch.equal(torch.view_as_real(q), torch.view_as_real(x).mul(torch.tensor([-1.0, 1.0], dtype=torch.float64)))

@@ -351,6 +351,31 @@ def test_adjoint_gradient_vs_dense_oracle(precision, bound):
     assert rel(gN.cpu().numpy(), gN_ref) < bound
 
 
+def test_adjoint_and_solve_take_lazy_conjugate_views():
+    """Plan.adjoint with econj = e.conj() (a lazy view over e's memory) and
+    Plan.solve with rhs = v.conj() give the results of materialised inputs."""
+    n, k = 5, 1.6
+    h, N = inputs.random_h_N(n, 71)
+    obs = inputs.observation_cells(n, 12, 5)
+    target = O.plane_wave(O.cell_centres(n), k)[obs]
+    u_ref, J, gh_ref, gN_ref = O.adjoint_gradient_dense(n, k, h, N, obs, target)
+    plan = make_plan(n, k, h, N)
+    u, _ = plan.solve(tol=1e-12, precision="fp64")
+    e = torch.zeros_like(u)
+    e[torch.from_numpy(obs).to(DEV)] = u[torch.from_numpy(obs).to(DEV)] - to_dev(target)
+    lazy = e.conj()
+    assert lazy.is_conj()
+    gh, gN, _ = plan.adjoint(u, lazy, tol=1e-12, precision="fp64")
+    assert rel(gh.cpu().numpy(), gh_ref) < 1e-8
+    assert rel(gN.cpu().numpy(), gN_ref) < 1e-8
+    v = to_dev(np.random.default_rng(8).standard_normal(n ** 3) + 1j)
+    a, _ = plan.solve(rhs=v.conj(), tol=1e-12, precision="fp64")
+    b, _ = plan.solve(rhs=v.conj().resolve_conj(), tol=1e-12, precision="fp64")
+    assert torch.equal(a, b)
+    with pytest.raises(ValueError):
+        plan.solve(out=torch.empty(n ** 3, dtype=torch.complex128, device=DEV).conj())
+
+
 def test_autograd_function_matches_oracle():
     from paper_1602_04691_gb300 import solve_autograd
     n, k = 4, 2.0
