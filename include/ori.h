@@ -95,8 +95,8 @@ typedef struct {
                        L >= 2n - 1 gives the same operator, R6 of the design
                        notes; used to exercise long transforms on small grids) */
   int    lean;      /* 0: full plan.  1: a plan for mixed-precision solves only, for
-                       the largest grids (n = 1000 needs about 246 GB instead of
-                       ~390 GB): it keeps no copy of h and N, no A-form arrays, no
+                       the largest grids (n = 1000 needs about 263 GB instead of
+                       ~410 GB): it keeps no copy of h and N, no A-form arrays, no
                        1/S, no FP64 spectrum and no FP64 COCG vectors.  On a lean
                        plan ori_matvec supports ORI_FORM_B in ORI_FP32 / ORI_DF,
                        ori_matvec32 ORI_FORM_B, the solves ORI_MIXED with the
@@ -158,7 +158,9 @@ void ori_default_plan_opts(ori_plan_opts* o);
  *            is L = the smallest power of two >= 2n (the paper pads to 2b-2
  *            by mirroring, Section 3; any L >= 2n-1 gives the same crop), at
  *            most 2048.  L <= 1024 runs the register-tile and persistent
- *            pipelined FFT passes; L = 2048 runs shared-memory radix-8 passes.
+ *            pipelined FFT passes; L = 2048 runs shared-memory radix-8 passes
+ *            except for the FP32 Z pass, which stays pipelined (its TILES
+ *            schedule selects the radix-8 kernel).
  *   k        wave number, finite and > 0 (Eq. 2.1).
  *   dom      cube corner and side (Eq. 3.3.5 uses the unit cube at the origin).
  *   h_dev    n^3 complex128 impedance samples h(x_p) (Eq. 2.13), device.

@@ -692,7 +692,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
         (st = alloc_n(p, &p->S64, n3)) || (st = alloc_n(p, &p->S32, n3)) || (st = alloc_n(p, &p->Sdf, n3)) ||
         (st = alloc_n(p, &p->ghat32, nk * H3)) ||
         (st = alloc_n(p, &p->ghatdf, nk * H3)) ||
-        (p->L <= 1024 && (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L))) ||
+        (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L)) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
         (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)))
       break;

@@ -1150,7 +1150,8 @@ __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int rhs, int
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4) ? 2 : 1) k_zconv_pipe(SArgs a) {
+__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4 && L <= 1024) ? 2 : 1)
+k_zconv_pipe(SArgs a) {
   using TL = Tile<L, C, T>;
   using ZP = ZPipe<L, C, T>;
   constexpr bool GZ = ZP::GZ;
@@ -1623,7 +1624,10 @@ cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
 
 template <class T, int L>
 cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = 128 / int(sizeof(cpx<T>));   // 128-byte rows (measured: 64-byte rows are slower)
+  // 128-byte rows (measured: 64-byte rows are slower at L <= 1024); at L = 2048
+  // a 16-column tile's exchange buffer alone exceeds shared memory, so 8 columns
+  // (256 threads, one CTA per SM with up to 255 registers a thread)
+  constexpr int C = (L > 1024 && sizeof(T) == 4) ? 8 : 128 / int(sizeof(cpx<T>));
   using ZP = ZPipe<L, C, T>;
   auto kfn = k_zconv_pipe<T, L, C>;
   static int per_sm = 0;   // resident CTAs per SM, measured once at set-up
@@ -1665,7 +1669,7 @@ cudaError_t launch_zconv_reg_L(SArgs a, cudaStream_t s, bool setup) {
   }
 }
 
-// Lengths beyond kMaxRegL: every pass uses the shared-memory radix-8 kernels
+// Lengths beyond kMaxRegL: every pass but the FP32 Z pass uses the shared-memory radix-8 kernels
 // (a register tile of L1 = 64 points per thread does not fit).
 constexpr int kMaxRegL = 1024;
 
@@ -1718,10 +1722,26 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
   }
 }
 
+// The Z pass beyond kMaxRegL: for FP32 the pipelined kernel still fits, since
+// its first stage holds 32 nonzero inputs of the 64-point DFT (dft<64> with
+// the zero-padded half) and its last keeps 32 of 64 outputs; it reads the
+// Z-tile-ordered spectrum.  The radix-8 shared-memory kernel is the TILES
+// schedule and the kernel of the other arithmetics.
 template <class T, int L>
 cudaError_t launch_zconv_L(SArgs a, cudaStream_t s, bool setup) {
-  if constexpr (L > kMaxRegL) return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
-  else return launch_zconv_reg_L<T, L>(a, s, setup);
+  if constexpr (L > kMaxRegL) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (setup) {
+        cudaError_t e = launch_zconv_pipe_L<T, L>(a, s, true, a.sm_count);
+        if (e != cudaSuccess) return e;
+        return launch_zconv_smem_L<T, L>(a, s, true, a.sm_count);
+      }
+      if (a.ghatZ != nullptr && a.sched != SCHED_TILES) return launch_zconv_pipe_L<T, L>(a, s, false, a.sm_count);
+    }
+    return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
+  } else {
+    return launch_zconv_reg_L<T, L>(a, s, setup);
+  }
 }
 
 #define ORI_FOR_EACH_L(X) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
