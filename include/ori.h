@@ -159,8 +159,8 @@ void ori_default_plan_opts(ori_plan_opts* o);
  *            by mirroring, Section 3; any L >= 2n-1 gives the same crop), at
  *            most 2048.  L <= 1024 runs the register-tile and persistent
  *            pipelined FFT passes; L = 2048 runs shared-memory radix-8 passes
- *            except for the FP32 Z pass, which stays pipelined (its TILES
- *            schedule selects the radix-8 kernel).
+ *            except for the FP32 Y and Z passes, which stay pipelined (their
+ *            TILES schedules select the radix-8 kernels).
  *   k        wave number, finite and > 0 (Eq. 2.1).
  *   dom      cube corner and side (Eq. 3.3.5 uses the unit cube at the origin).
  *   h_dev    n^3 complex128 impedance samples h(x_p) (Eq. 2.13), device.

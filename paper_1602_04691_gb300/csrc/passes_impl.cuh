@@ -1417,7 +1417,8 @@ __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, int per
 }
 
 template <class T, int L, int C>
-__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (YPipe<L, C, T>::NT >= 512 ? 1 : (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT))) k_yfwd_pipe(SArgs a) {
+__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (L > 1024 || YPipe<L, C, T>::NT >= 512) ? 1 : (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT))
+k_yfwd_pipe(SArgs a) {
   using TL = Tile<L, C, T>;
   using YP = YPipe<L, C, T>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
@@ -1512,7 +1513,8 @@ __device__ __forceinline__ void yinv_prefetch(const SArgs& a, int tile, int per_
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 512 ? 1 : (YInvPipe<L, C>::NT >= 256 ? 2 : 512 / YInvPipe<L, C>::NT))) k_yinv_pipe(SArgs a) {
+__global__ void __launch_bounds__(YInvPipe<L, C>::NT, (L > 1024 || YInvPipe<L, C>::NT >= 512) ? 1 : (YInvPipe<L, C>::NT >= 256 ? 2 : 512 / YInvPipe<L, C>::NT))
+k_yinv_pipe(SArgs a) {
   using T = float;
   using TL = Tile<L, C, T>;
   using YP = YInvPipe<L, C>;
@@ -1579,7 +1581,9 @@ __global__ void __launch_bounds__(YInvPipe<L, C>::NT, (YInvPipe<L, C>::NT >= 512
 
 template <int L>
 cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = 16;   // 128-byte rows (8 columns: 1.42 ms, 16: 1.24 ms at n = 512)
+  // 128-byte rows (8 columns: 1.42 ms, 16: 1.24 ms at n = 512); at L = 2048 the
+  // 16-column exchange buffer exceeds shared memory: 8 columns, one CTA per SM
+  constexpr int C = L > 1024 ? 8 : 16;
   using YP = YInvPipe<L, C>;
   auto kfn = k_yinv_pipe<L, C>;
   static int per_sm = 0;
@@ -1602,7 +1606,9 @@ cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
 
 template <class T, int L>
 cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  constexpr int C = 16;   // 128-byte rows (8 columns: 1.37 ms, 16: 1.30 ms at n = 512)
+  // 128-byte rows (8 columns: 1.37 ms, 16: 1.30 ms at n = 512); 8 at L = 2048
+  // as for the inverse
+  constexpr int C = L > 1024 ? 8 : 16;
   using YP = YPipe<L, C, T>;
   auto kfn = k_yfwd_pipe<T, L, C>;
   static int per_sm = 0;
@@ -1669,8 +1675,9 @@ cudaError_t launch_zconv_reg_L(SArgs a, cudaStream_t s, bool setup) {
   }
 }
 
-// Lengths beyond kMaxRegL: every pass but the FP32 Z pass uses the shared-memory radix-8 kernels
-// (a register tile of L1 = 64 points per thread does not fit).
+// Lengths beyond kMaxRegL: the X passes and the FP64 and paired-FP32 passes use
+// the shared-memory radix-8 kernels (a register tile of L1 = 64 points per
+// thread does not fit); the FP32 Y and Z passes stay pipelined.
 constexpr int kMaxRegL = 1024;
 
 template <class T, int L, bool HALF>
@@ -1709,6 +1716,25 @@ cudaError_t launch_strided_L(SArgs a, cudaStream_t s, bool setup) {
     if constexpr (SMODE == SMODE_ZCONV) {
       return launch_zconv_smem_L<T, L>(a, s, setup, a.sm_count);
     } else {
+      // FP32 Y passes: the pipelined kernels fit for the reason the Z kernel does
+      // (a 64-point stage with a zero half on input, or with half its outputs
+      // kept); the TILES schedule keeps the radix-8 kernels below
+      if constexpr (std::is_same<T, float>::value && SMODE == SMODE_FWD && HALF) {
+        if (setup) {
+          cudaError_t e = launch_yfwd_pipe_L<T, L>(a, s, true, a.sm_count);
+          if (e != cudaSuccess) return e;
+        } else if (a.sched == SCHED_PERSISTENT) {
+          return launch_yfwd_pipe_L<T, L>(a, s, false, a.sm_count);
+        }
+      }
+      if constexpr (std::is_same<T, float>::value && SMODE == SMODE_INV) {
+        if (setup) {
+          cudaError_t e = launch_yinv_pipe_L<L>(a, s, true, a.sm_count);
+          if (e != cudaSuccess) return e;
+        } else if (a.sched == SCHED_PERSISTENT && a.ncols == L && a.n_in == L) {
+          return launch_yinv_pipe_L<L>(a, s, false, a.sm_count);
+        }
+      }
       constexpr int CS = 4;   // (8 columns measured slower at L = 2048: fewer resident CTAs)
       using LS = LSmem<L, CS, T>;
       auto kfs = k_strided_smem<T, L, CS, SMODE, (SMODE == SMODE_FWD ? HALF : true)>;

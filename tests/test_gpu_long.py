@@ -1,5 +1,5 @@
 """Padded length L = 2048: the shared-memory radix-8 passes of every arithmetic
-and the pipelined FP32 Z pass.
+and the pipelined FP32 Y and Z passes.
 
 Grids of n >= 513 (up to the paper-scale n = 1000) pad to L = 2048.  The plan
 option min_L forces that length on small grids, where the oracle's direct
@@ -81,11 +81,11 @@ def test_L2048_batch_vs_single(long_plan):
         assert rel(ub[0, j].cpu().numpy(), us.cpu().numpy()) < 1e-5
 
 
-def test_L2048_fp32_z_kernels_agree(long_plan):
-    """At L = 2048 the FP32 Z pass runs the pipelined kernel (64-point first
-    stage with the zero-padded half, 8-column tiles); the TILES schedule keeps
-    the radix-8 shared-memory kernel.  Both against the direct sum, and the
-    default schedule restored afterwards."""
+def test_L2048_fp32_pipelined_and_radix8_kernels_agree(long_plan):
+    """At L = 2048 the FP32 Y forward, Z and Y inverse passes run the pipelined
+    kernels (a 64-point stage with a zero-padded half or half its outputs kept,
+    8-column tiles); the TILES schedule keeps the radix-8 shared-memory kernels.
+    Both against the direct sum, and the default schedule restored afterwards."""
     from paper_1602_04691_gb300._lib import ORI_SCHED_TILES
     n, k, h, N, plan = long_plan
     x = inputs.random_complex(n ** 3, 606)
@@ -93,7 +93,7 @@ def test_L2048_fp32_z_kernels_agree(long_plan):
     xd = to_dev(x.astype(np.complex64))
     default = plan.schedule()
     y_pipe = plan.matvec32(xd, form="B").cpu().numpy()
-    plan.set_schedule(dict(default, zconv=ORI_SCHED_TILES))
+    plan.set_schedule(dict(default, yfwd=ORI_SCHED_TILES, zconv=ORI_SCHED_TILES, yinv=ORI_SCHED_TILES))
     try:
         y_tiles = plan.matvec32(xd, form="B").cpu().numpy()
     finally:
