@@ -1,0 +1,79 @@
+"""Host-side logic of bench.py (no GPU): the algorithmic byte model of the
+five passes, the kernel each pass runs, and when ncu traffic is reported."""
+
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_byte_model_at_n512():
+    """n = 512, L = 1024: T1 = n^2 L = 2N and T2 = n L^2 = 4N complex64 values.
+    One B-form matvec: X fwd reads x, S and writes T1 (4N), Y fwd 6N, Z 8N plus
+    the (L/2+1)^3 spectrum entries, Y inv 6N, X inv reads T1, x, S and writes y
+    (5N): 29N + spectrum, 32.2 GB.  One COCG iteration: the X fwd prologue also
+    reads r and writes p (6N), the X inv epilogue reads p (5N), the update moves
+    6N: 37N + spectrum, 40.8 GB."""
+    n, L, cb = 512, 1024, 8
+    N, H3 = n ** 3, (L // 2 + 1) ** 3
+    assert bench.matvec_alg_bytes(n, L, cb) == (29 * N + H3) * cb
+    assert abs(bench.matvec_alg_bytes(n, L, cb) / 1e9 - 32.2) < 0.05
+    it = sum(bench.alg_bytes(k, n, L, cb) for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv", "update"))
+    assert it == (37 * N + H3) * cb
+    assert abs(it / 1e9 - 40.8) < 0.05
+    assert abs(bench.alg_bytes("zconv", n, L, cb) / 1e9 - 9.67) < 0.01
+
+
+def test_kernel_names_follow_length_and_schedule():
+    pers = {"yfwd": 0, "zconv": 0, "yinv": 0}
+    tiles = {"yfwd": 1, "zconv": 1, "yinv": 1}
+    assert bench.fp32_kernel_name("zconv", 1024, pers) == "k_zconv_pipe<float, 1024, 16>"
+    assert bench.fp32_kernel_name("zconv", 1024, tiles) == "k_strided<float, 1024>(ZCONV)"
+    assert bench.fp32_kernel_name("zconv", 2048, pers) == "k_zconv_pipe<float, 2048, 8>"
+    assert bench.fp32_kernel_name("zconv", 2048, tiles) == "k_zconv_smem<float, 2048, 8>"
+    assert bench.fp32_kernel_name("yinv", 2048, pers) == "k_yinv_pipe<2048, 8>"
+    assert bench.fp32_kernel_name("yfwd", 2048, tiles) == "k_strided_smem<float, 2048, 4>(FWD)"
+    # the X passes have one kernel per length whatever the schedule
+    assert bench.fp32_kernel_name("xfwd", 2048, pers) == bench.fp32_kernel_name("xfwd", 2048, tiles)
+    assert bench.fp32_kernel_name("update", 1024, pers) == "k_cocg_update<float>"
+
+
+def _write_traffic(tmp_path, monkeypatch, source_hash, n):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({
+        "source_hash": source_hash,
+        "kernels": {"zconv": {"n": n, "dram_bytes_per_launch": 1.0e10}}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+
+
+def test_traffic_reported_only_for_current_sources_and_same_grid(tmp_path, monkeypatch):
+    current = bench.source_hash()                    # of the real kernel sources
+    monkeypatch.setattr(bench, "source_hash", lambda: current)
+    _write_traffic(tmp_path, monkeypatch, current, 512)
+    assert bench.traffic_from_profiles("zconv", 512) == 1.0e10
+    assert bench.traffic_from_profiles("zconv", 1000) is None     # another L, other kernels
+    assert bench.traffic_from_profiles("xfwd", 512) is None       # not captured
+
+
+def test_traffic_dropped_once_sources_change(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "source_hash", lambda: "0123456789abcdef")
+    _write_traffic(tmp_path, monkeypatch, "fedcba9876543210", 512)
+    assert bench.traffic_from_profiles("zconv", 512) is None
+
+
+def test_committed_traffic_matches_the_kernel_sources():
+    """profiles/traffic.json was taken from the kernel sources in the tree."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        pytest.skip("no committed traffic capture")
+    with open(path) as f:
+        d = json.load(f)
+    assert d["source_hash"] == bench.source_hash()
