@@ -137,7 +137,7 @@ def fp32_kernel_name(kind: str, L: int, sched: dict) -> str:
                 "yfwd": f"k_strided<float, {L}>(FWD)" if tiles["yfwd"] else f"k_yfwd_pipe<float, {L}, 16>",
                 "zconv": f"k_strided<float, {L}>(ZCONV)" if tiles["zconv"] else f"k_zconv_pipe<float, {L}, 16>",
                 "yinv": f"k_strided<float, {L}>(INV)" if tiles["yinv"] else f"k_yinv_pipe<{L}, 16>"}[kind]
-    return {"xfwd": f"k_xfwd_smem<float, {L}, 4>", "xinv": f"k_xinv_smem<float, {L}, 4>",
+    return {"xfwd": f"k_xfwd_pipe<{L}, 4>", "xinv": f"k_xinv_pipe<{L}, 4>",
             "yfwd": f"k_strided_smem<float, {L}, 4>(FWD)" if tiles["yfwd"] else f"k_yfwd_pipe<float, {L}, 8>",
             "zconv": f"k_zconv_smem<float, {L}, 8>" if tiles["zconv"] else f"k_zconv_pipe<float, {L}, 8>",
             "yinv": f"k_strided_smem<float, {L}, 4>(INV)" if tiles["yinv"] else f"k_yinv_pipe<{L}, 8>"}[kind]

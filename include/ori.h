@@ -158,9 +158,10 @@ void ori_default_plan_opts(ori_plan_opts* o);
  *            is L = the smallest power of two >= 2n (the paper pads to 2b-2
  *            by mirroring, Section 3; any L >= 2n-1 gives the same crop), at
  *            most 2048.  L <= 1024 runs the register-tile and persistent
- *            pipelined FFT passes; L = 2048 runs shared-memory radix-8 passes
- *            except for the FP32 Y and Z passes, which stay pipelined (their
- *            TILES schedules select the radix-8 kernels).
+ *            pipelined FFT passes; at L = 2048 the FP32 passes stay pipelined
+ *            (the TILES schedules of the Y and Z passes select shared-memory
+ *            radix-8 kernels) and the FP64 and paired-FP32 passes run
+ *            shared-memory radix-8 kernels.
  *   k        wave number, finite and > 0 (Eq. 2.1).
  *   dom      cube corner and side (Eq. 3.3.5 uses the unit cube at the origin).
  *   h_dev    n^3 complex128 impedance samples h(x_p) (Eq. 2.13), device.

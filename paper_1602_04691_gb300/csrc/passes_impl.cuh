@@ -203,7 +203,7 @@ __device__ __forceinline__ void xfwd_prefetch(const XArgs& a, int tile, cpx<floa
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(XFwdPipe<L, C>::NT, 2) k_xfwd_pipe(XArgs a0) {
+__global__ void __launch_bounds__(XFwdPipe<L, C>::NT, L > 1024 ? 1 : 2) k_xfwd_pipe(XArgs a0) {
   using T = float;
   const XArgs a = x_for_rhs(a0, blockIdx.y);
   using TL = Tile<L, C, T>;
@@ -480,7 +480,7 @@ __device__ __forceinline__ void xinv_prefetch(const XArgs& a, int tile, cpx<floa
 }
 
 template <int L, int C>
-__global__ void __launch_bounds__(XInvPipe<L, C>::NT, 3) k_xinv_pipe(XArgs a0, Scalars* sc0, int fin) {
+__global__ void __launch_bounds__(XInvPipe<L, C>::NT, L > 1024 ? 1 : 3) k_xinv_pipe(XArgs a0, Scalars* sc0, int fin) {
   using T = float;
   const XArgs a = x_for_rhs(a0, blockIdx.y);
   Scalars* sc = sc0 == nullptr ? nullptr : sc0 + blockIdx.y;
@@ -1675,14 +1675,24 @@ cudaError_t launch_zconv_reg_L(SArgs a, cudaStream_t s, bool setup) {
   }
 }
 
-// Lengths beyond kMaxRegL: the X passes and the FP64 and paired-FP32 passes use
-// the shared-memory radix-8 kernels (a register tile of L1 = 64 points per
-// thread does not fit); the FP32 Y and Z passes stay pipelined.
+// Lengths beyond kMaxRegL: the FP64 and paired-FP32 passes use the
+// shared-memory radix-8 kernels (a register tile of L1 = 64 of their points
+// per thread does not fit).  The FP32 passes stay pipelined: each 64-point
+// stage either has a zero-padded half on input or keeps half its outputs.
 constexpr int kMaxRegL = 1024;
 
 template <class T, int L, bool HALF>
 cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
   if constexpr (L > kMaxRegL) {
+    // FP32 solver prologues: the pipelined kernel (4-line tiles, one CTA per SM)
+    if constexpr (std::is_same<T, float>::value && HALF) {
+      if (setup) {
+        cudaError_t e = launch_xfwd_pipe_L<L>(a, s, true);
+        if (e != cudaSuccess) return e;
+      } else if (xfwd_pipe_ok(a, L)) {
+        return launch_xfwd_pipe_L<L>(a, s, false);
+      }
+    }
     constexpr int CS = 4;
     using LS = LSmem<L, CS, T>;
     auto kfs = k_xfwd_smem<T, L, CS, HALF>;
@@ -1696,7 +1706,9 @@ cudaError_t launch_xfwd_L(const XArgs& a, cudaStream_t s, bool setup) {
 
 template <class T, int L>
 cudaError_t launch_xinv_L(const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup, unsigned* nblocks) {
-  if constexpr (L > kMaxRegL) {
+  if constexpr (L > kMaxRegL && std::is_same<T, float>::value) {
+    return launch_xinv_pipe_L<L>(a, sc, fin, s, setup, nblocks);   // as for L <= kMaxRegL
+  } else if constexpr (L > kMaxRegL) {
     constexpr int CS = 4;
     using LS = LSmem<L, CS, T>;
     auto kfs = k_xinv_smem<T, L, CS>;

@@ -42,6 +42,7 @@ def test_kernel_names_follow_length_and_schedule():
     assert bench.fp32_kernel_name("yfwd", 2048, tiles) == "k_strided_smem<float, 2048, 4>(FWD)"
     # the X passes have one kernel per length whatever the schedule
     assert bench.fp32_kernel_name("xfwd", 2048, pers) == bench.fp32_kernel_name("xfwd", 2048, tiles)
+    assert bench.fp32_kernel_name("xinv", 2048, pers) == "k_xinv_pipe<2048, 4>"
     assert bench.fp32_kernel_name("update", 1024, pers) == "k_cocg_update<float>"
 
 

@@ -1,5 +1,5 @@
-"""Padded length L = 2048: the shared-memory radix-8 passes of every arithmetic
-and the pipelined FP32 Y and Z passes.
+"""Padded length L = 2048: the pipelined FP32 passes, the shared-memory radix-8
+passes of FP64 and paired FP32, and the radix-8 TILES schedules of FP32 Y and Z.
 
 Grids of n >= 513 (up to the paper-scale n = 1000) pad to L = 2048.  The plan
 option min_L forces that length on small grids, where the oracle's direct
