@@ -87,3 +87,33 @@ def test_committed_traffic_agrees_with_the_byte_model():
         ent = d["kernels"][kind]
         ratio = ent["dram_bytes_per_launch"] / bench.alg_bytes(kind, ent["n"], 2 * ent["n"], 8)
         assert 0.9 < ratio < 1.3, (kind, ratio)
+
+
+def test_committed_bench_line_keeps_the_output_contract():
+    """The committed n = 512 bench line carries every key of the output
+    contract, and its derived figures agree with their inputs."""
+    path = os.path.join(ROOT, "profiles", "bench_solve_n512_latest.json")
+    with open(path) as f:
+        d = json.loads(f.readline())
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e",
+                "gpu_launches", "clocks"):
+        assert key in d, key
+    assert d["metric"] == bench.METRIC and d["unit"] == "s" and d["higher_is_better"] is False
+    assert d["warmup"] >= 3 and d["n_gpus"] == 1 and "workload" in d["config"]
+    assert abs(d["ms_per_step"] / 1e3 - d["value"]) < 1e-9 * d["value"]
+    roof = d["roofline"]
+    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
+    assert abs(roof["achieved"] - roof["alg_bytes_per_launch"] / (roof["ms_per_launch"] * 1e-3) / 1e9) < 1e-6 * roof["achieved"]
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):
+        with open(peaks) as f:
+            assert roof["peak"] == float(json.load(f)["hbm_gbs"])
+    cpu = d["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["sample"]
+    e2e = d["e2e"]
+    assert e2e["unit"] == d["unit"] and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
+    assert e2e["value"] > d["value"]                   # the copies are inside its timed region
+    assert d["gpu_launches"] > 0
+    assert not set(d["clocks"]["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
