@@ -49,6 +49,7 @@ import numpy as np
 __all__ = [
     "C_S_SPHERE", "cell_size", "cell_centres", "plane_wave", "greens_function",
     "red_weights", "red_matrix", "red_matvec_direct", "red_matvec_rows", "offdiag_sum_rows_grid",
+    "kernel_octant", "offdiag_sum_rows_octant",
     "symmetrised_matrix", "symmetrised_matvec_direct", "sqrt_hN",
     "pad_kernel_mirror", "pad_field_zero", "kernel_cube",
     "fft_convolution", "red_matvec_fft", "symmetrised_matvec_fft",
@@ -186,6 +187,54 @@ def offdiag_sum_rows_grid(v, rows, n, k, side=1.0, planes_per_chunk=32):
             nz = r > 0
             G[nz] = greens_function(r[nz], k)
             acc += np.sum(G * vv[z0:z0 + planes_per_chunk])
+        out[t] = acc
+    return out
+
+
+def kernel_octant(n, k, side=1.0) -> np.ndarray:
+    """G(d |(a, b, c)|) for cell offsets 0 <= a, b, c < n, indexed [a][b][c], and 0
+    at the origin (the sum of Eq. 2.19 / Eq. 3.3.7 excludes p = q).  Cell points
+    differ by d times integer offsets (Eq. 3.3.5), so these n^3 values are every
+    value G takes in the off-diagonal sum; G depends on |offset| only."""
+    d = side / n
+    b2 = (np.arange(n, dtype=np.float64) * d) ** 2
+    out = np.empty((n, n, n), dtype=np.complex128)
+    for a in range(n):
+        r = np.sqrt((a * d) ** 2 + b2[:, None] + b2[None, :])
+        plane = np.zeros((n, n), dtype=np.complex128)
+        nz = r > 0
+        plane[nz] = greens_function(r[nz], k)
+        out[a] = plane
+    return out
+
+
+def _axis_pieces(q: int, n: int):
+    """Cover the cells 0..n-1 of one axis by two runs: cells q..n-1 sit at offsets
+    0..n-1-q from q, cells q-1..0 (taken downwards) at offsets 1..q."""
+    pieces = [(slice(0, n - q), slice(q, n))]
+    if q > 0:
+        pieces.append((slice(1, q + 1), slice(q - 1, None, -1)))
+    return pieces
+
+
+def offdiag_sum_rows_octant(v, rows, n, k, side=1.0, octant=None):
+    """sum_{p != q} G(|x_q - x_p|) v_p for the cells q in `rows` (the same sums as
+    offdiag_sum_rows_grid): every cell p of the grid, taken as a product of one run
+    per axis (_axis_pieces), multiplies v_p by the table value G(d |offset|) of
+    kernel_octant.  No evaluation of G per row, so large grids (n = 512) take well
+    under a second per row.  `octant` may pass a kernel_octant(n, k, side) table."""
+    G = kernel_octant(n, k, side) if octant is None else octant
+    vv = np.asarray(v, dtype=np.complex128).reshape(n, n, n)
+    rows = np.asarray(rows, dtype=np.int64).ravel()
+    out = np.empty(rows.size, dtype=np.complex128)
+    for t, q in enumerate(rows):
+        qz, rem = divmod(int(q), n * n)
+        qy, qx = divmod(rem, n)
+        acc = 0j
+        for gz, vz in _axis_pieces(qz, n):
+            for gy, vy in _axis_pieces(qy, n):
+                for gx, vx in _axis_pieces(qx, n):
+                    acc += np.einsum("ijk,ijk->", G[gz, gy, gx], vv[vz, vy, vx])
         out[t] = acc
     return out
 

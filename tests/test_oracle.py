@@ -194,6 +194,39 @@ def test_grid_row_sums_equal_dense_rows():
     assert rel(got, (A @ x)[rows]) < 1e-14
 
 
+def test_octant_row_sums_equal_dense_rows_everywhere():
+    """The table-driven row sums (used at n = 512) against the dense matrix on
+    every row of an n = 6 grid (corners, edges, faces, interior), and against
+    the per-row direct evaluation on an odd n = 9 grid."""
+    n, k, side = 6, 2.7, 1.4
+    h, N = inputs.random_h_N(n, 5)
+    x = inputs.random_complex(n ** 3, 6)
+    w = O.red_weights(h, N, side / n)
+    A = O.red_matrix(n, k, h, N, side=side)
+    rows = np.arange(n ** 3)
+    got = x + O.offdiag_sum_rows_octant(w * x, rows, n, k, side)
+    assert rel(got, A @ x) < 1e-14
+    n = 9
+    v = inputs.random_complex(n ** 3, 7)
+    rows = np.array([0, n - 1, n * n - 1, n ** 3 - 1, n ** 3 - n, 4 * n * n + 4 * n + 4, 123, 500])
+    a = O.offdiag_sum_rows_octant(v, rows, n, 4.1, 0.9)
+    b = O.offdiag_sum_rows_grid(v, rows, n, 4.1, 0.9, planes_per_chunk=2)
+    assert rel(a, b) < 1e-14
+
+
+def test_kernel_octant_values():
+    """The table holds G(d |offset|) with the origin left out (p = q excluded)."""
+    n, k, side = 5, 3.3, 2.0
+    G = O.kernel_octant(n, k, side)
+    d = side / n
+    assert G[0, 0, 0] == 0
+    for a, b, c in [(0, 0, 1), (1, 2, 3), (4, 4, 4), (3, 0, 2)]:
+        r = d * math.sqrt(a * a + b * b + c * c)
+        assert abs(G[a, b, c] - np.exp(1j * k * r) / (4 * math.pi * r)) < 1e-15
+    # G depends on |offset| only: any permutation of the three axes gives the same table
+    assert np.array_equal(G, G.transpose(1, 0, 2)) and np.array_equal(G, G.transpose(2, 1, 0))
+
+
 def test_brute_force_tiny_grid():
     """n = 2 (8 cells) summed pair by pair in plain Python."""
     n, k, side = 2, 3.1, 0.7
