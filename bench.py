@@ -154,11 +154,11 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"ori_clocks_rank{index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -186,6 +186,10 @@ class ClockSampler:
                                  "hw": parts[6], "hwt": parts[7], "swt": parts[8], "pcap": parts[9]})
                 except ValueError:
                     continue
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return None
         load = [r for r in rows if r["util"] >= 50] or rows

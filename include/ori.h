@@ -91,9 +91,11 @@ typedef struct {
                        other calls use ks[0]                                      */
   const double* ks; /* n_k host wave numbers (read during ori_plan only)         */
   int    min_L;     /* 0: padded length L = smallest power of two >= 2n.  Else a
-                       power of two in [4, 2048]: L = max(that, min_L) (any
-                       L >= 2n - 1 gives the same operator, R6 of the design
-                       notes; used to exercise long transforms on small grids) */
+                       power of two in [4, 2048]: L = max(that, min_L).  Any
+                       L >= 2n - 1 gives the same operator, because offsets
+                       between cells span -(n-1)..n-1 and the cyclic
+                       convolution then never wraps onto a kept output; used
+                       to exercise long transforms on small grids             */
   int    lean;      /* 0: full plan.  1: a plan for mixed-precision solves only, for
                        the largest grids (n = 1000 needs about 263 GB instead of
                        ~410 GB): it keeps no copy of h and N, no A-form arrays, no
@@ -111,7 +113,7 @@ typedef struct {
   int    maxit;        /* cap on COCG iterations summed over refinements, def 1000  */
   int    precision;    /* ORI_FP64 or ORI_MIXED (default ORI_MIXED)                  */
   double inner_tol;    /* ORI_MIXED: floor of the FP32 inner target, default 1e-5    */
-  int    max_outer;    /* ORI_MIXED: cap on refinement steps, default 8              */
+  int    max_outer;    /* cap on refinement steps (ORI_FP64: on COCG runs), def 8    */
   int    check_every;  /* iterations between host reads of the convergence flag (8)  */
   double alpha[3];     /* incidence direction when rhs_dev == NULL; (0,0,0)->(0,0,1) */
   int    use_graph;    /* 1 (default): replay the check_every-iteration block as a
@@ -134,7 +136,9 @@ typedef struct {
 
 typedef struct {
   int    iters;         /* COCG iterations, all refinement steps together            */
-  int    outer_iters;   /* refinement steps (1 for ORI_FP64)                         */
+  int    outer_iters;   /* ORI_MIXED: refinement steps.  ORI_FP64: COCG runs (a run
+                           restarts from the true residual b - B w when the
+                           recursive one met tol but the true one did not)        */
   int    fp64_matvecs;  /* FP64 operator applications (residuals, recovery)          */
   double relres;        /* true residual of the symmetrised system COCG solves,
                            ||S rhs - B w|| / ||S rhs|| with u = w / S, in FP64      */
@@ -221,13 +225,15 @@ ori_status ori_matvec32(ori_plan_t plan, const float* x_dev, float* y_dev,
  *   n, k, dom  as for ori_plan, with 2 <= n <= ORI_NOALLOC_MAX_N.
  *   c_S        surface constant (0 -> 4 pi).
  *   h_dev, N_dev, x_dev  n^3 complex128 / float64 / complex128 device inputs.
- *   y_dev      n^3 complex128 device output; must not overlap x_dev.
+ *   y_dev      n^3 complex128 device output; its 16 n^3 bytes must not
+ *              overlap those of x_dev (ORI_ERR_INVALID_ARG otherwise).
  * Every intermediate (twiddles, h N, the kernel cube and its spectrum, the FFT
  * work cubes) lives in one static device array of ORI_NOALLOC_SCRATCH_BYTES
  * bytes that each GPU loading the library holds until the process exits.
- * The first call on a device (with that device current) looks up the array's
- * device address and sets kernel attributes; make that first call before
- * any stream capture.  Each call recomputes the spectrum (cheap at these
+ * Every call looks up the array's device address on the current device (a
+ * host-side query; a context made anew after cudaDeviceReset may move it);
+ * the first call on a device, and the first after the address moved, also
+ * sets kernel attributes: make those calls before any stream capture.  Each call recomputes the spectrum (cheap at these
  * sizes) and writes every scratch element it reads, so the array keeps the
  * last call's contents without harm.  All calls share the one array: calls
  * that overlap on the GPU (different streams, or threads on one device) race;
@@ -247,9 +253,12 @@ ori_status ori_matvec_noalloc(int64_t n, double k, const ori_domain* dom, double
  *   u_dev    n^3 complex128 output (also the best iterate on failure).
  * COCG runs on the complex-symmetric B w = S rhs, and u = w / S; cells with
  * S = 0 get u = rhs - K (S w) (one more FP64 operator application).
- * ORI_FP64 runs COCG in FP64.  ORI_MIXED runs FP32 COCG with FP64 scalars on
- * the normalised FP64 residual and refines w in FP64 until the FP64 residual
- * meets tol.  Synchronising: returns after the solve has finished; info (may
+ * ORI_FP64 runs COCG in FP64 and checks the true residual b - B w at the end;
+ * if the recursive residual met tol but the true one did not, COCG restarts
+ * from w (at most max_outer runs).  ORI_MIXED runs FP32 COCG with FP64
+ * scalars on the normalised FP64 residual and refines w in FP64 until the
+ * FP64-class residual meets tol.  Either way ORI_OK means info->relres <= tol
+ * (ORI_MIXED: relres + relres_bound <= tol).  Synchronising: returns after the solve has finished; info (may
  * be NULL) is filled.  Returns ORI_ERR_NOT_CONVERGED / _BREAKDOWN /
  * _NONFINITE with the best iterate in u_dev.
  */

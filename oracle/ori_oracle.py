@@ -34,8 +34,11 @@ beyond what the paper states):
 * The cell charges of Eq. 2.13, the field off the grid of Eq. 2.10, and the
   solution-difference metric of Section 4 (Table 4).
 
-Floating point is numpy float64 / complex128 throughout.  numpy's FFT, dense
-LU (``numpy.linalg.solve``) and matrix products serve as library steps.
+Floating point is numpy float64 / complex128 throughout, except that the
+timed CPU solver (solve_cocg_fft_cpu, the paper's algorithm as Section 4 ran
+it on CPU cores) can also run in complex64, the paper's arithmetic.  numpy's
+and scipy's FFTs, dense LU (``numpy.linalg.solve``) and matrix products serve
+as library steps.
 
 This module is test infrastructure.  Only tests, the package smoke check and
 the CPU-baseline leg of the benchmark may call it.
@@ -54,6 +57,7 @@ __all__ = [
     "pad_kernel_mirror", "pad_field_zero", "kernel_cube",
     "fft_convolution", "red_matvec_fft", "symmetrised_matvec_fft",
     "cocg", "solve_dense", "solve_red_cocg_fft", "relative_residual",
+    "kernel_spectrum_zero", "symmetrised_matvec_spectrum", "solve_cocg_fft_cpu",
     "two_particle_solution", "refraction_from_h", "h_from_refraction",
     "branch_sqrt_cut_positive_axis", "adjoint_gradient_dense", "objective",
     "born_first_order", "charges", "field", "table4_difference",
@@ -360,13 +364,16 @@ def relative_residual(apply_A, u, rhs) -> float:
     return float(np.linalg.norm(r) / np.linalg.norm(rhs))
 
 
-def cocg(apply_A, b, tol=1e-12, maxit=1000, x0=None):
+def cocg(apply_A, b, tol=1e-12, maxit=1000, x0=None, dtype=np.complex128, callback=None):
     """Conjugate orthogonal conjugate gradient (van der Vorst & Melissen), the
     solver named in Section 1 and Section 3, for complex-symmetric A.
 
-    Returns (x, iterations, recursive relative residual)."""
-    b = np.asarray(b, dtype=np.complex128)
-    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    Vectors and scalars are kept in `dtype` (complex128; complex64 is the
+    arithmetic of the paper's runs, Section 4).  `callback(it)`, if given, is
+    called after each iteration.  Returns (x, iterations, recursive relative
+    residual)."""
+    b = np.asarray(b, dtype=dtype)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=dtype)
     r = b - apply_A(x) if x0 is not None else b.copy()
     nb = np.linalg.norm(b)
     if nb == 0.0:
@@ -387,6 +394,8 @@ def cocg(apply_A, b, tol=1e-12, maxit=1000, x0=None):
         p = r + beta * p
         it += 1
         relres = np.linalg.norm(r) / nb
+        if callback is not None:
+            callback(it)
     return x, it, float(relres)
 
 
@@ -416,6 +425,71 @@ def solve_red_cocg_fft(n, k, h, N, alpha=(0.0, 0.0, 1.0), side=1.0, origin=(0.0,
         Kw = (c_S * d ** 3) * fft_convolution((S * w).reshape(n, n, n), c).ravel()
         u[~nz] = rhs[~nz] - Kw[~nz]
     return u, it, rr
+
+
+# ----------------------------------------------------------------------------
+# The paper's algorithm on CPU cores (the timed CPU baseline): Section 3's FFT
+# convolution inside COCG, as Section 4 ran it with FFTW on CPU cores.  The
+# FFTs are scipy.fft's, on `workers` threads; the spectrum F(G) is computed
+# once (Eq. 3.3.9 counts it per matvec: the result is the same).
+# ----------------------------------------------------------------------------
+
+def kernel_spectrum_zero(n, k, side=1.0, c_S=C_S_SPHERE, L=None, dtype=np.complex128, workers=None):
+    """F(c) for the kernel cube c = c_S |Delta| G_off zero-embedded in L^3 (the
+    zero embedding of kernel_cube; L >= 2n - 1, default the smallest power of
+    two >= 2n), filled plane by plane from kernel_octant so that no L^3
+    complex128 temporary is needed, then transformed in place in `dtype`."""
+    import scipy.fft as sfft
+    if L is None:
+        L = 1
+        while L < 2 * n:
+            L *= 2
+    if L < 2 * n - 1:
+        raise ValueError("zero embedding needs L >= 2n - 1")
+    d = cell_size(n, side)
+    G = kernel_octant(n, k, side)
+    # wrapped index j of one axis holds |signed offset| = j for j < n, L - j for j > L - n
+    wrapped = np.concatenate([np.arange(n), np.arange(L - n + 1, L)])
+    offset = np.concatenate([np.arange(n), np.arange(n - 1, 0, -1)])
+    c = np.zeros((L, L, L), dtype=dtype)
+    scale = c_S * d ** 3
+    for jz, az in zip(wrapped, offset):
+        c[jz][np.ix_(wrapped, wrapped)] = (scale * G[az][np.ix_(offset, offset)]).astype(dtype)
+    return sfft.fftn(c, overwrite_x=True, workers=workers)
+
+
+def symmetrised_matvec_spectrum(x, S, spec, n, workers=None):
+    """B x = x + S (c_S |Delta| G_off * (S x)) with the kernel's spectrum `spec`
+    (kernel_spectrum_zero): zero-pad S x to L^3, FFT, multiply, inverse FFT,
+    keep the first n entries per axis (Eq. 3.3.8, Section 3).  Arithmetic in
+    the spectrum's dtype."""
+    import scipy.fft as sfft
+    L = spec.shape[0]
+    pad = np.zeros((L, L, L), dtype=spec.dtype)
+    pad[:n, :n, :n] = (S * x).reshape(n, n, n)
+    f = sfft.fftn(pad, overwrite_x=True, workers=workers)
+    f *= spec
+    conv = sfft.ifftn(f, overwrite_x=True, workers=workers)
+    return x + S * conv[:n, :n, :n].ravel()
+
+
+def solve_cocg_fft_cpu(n, k, h, N, alpha=(0.0, 0.0, 1.0), side=1.0, origin=(0.0, 0.0, 0.0),
+                       c_S=C_S_SPHERE, tol=1e-6, maxit=2000, dtype=np.complex64, workers=None,
+                       spec=None, callback=None):
+    """COCG on B w = S u0 with the FFT matvec of symmetrised_matvec_spectrum in
+    `dtype`, then u = w / S; every cell needs S != 0.  `spec` may pass a
+    kernel_spectrum_zero of the same dtype.  Returns (u, iterations, recursive
+    relres)."""
+    S = sqrt_hN(h, N)
+    if np.any(S == 0):
+        raise ValueError("solve_cocg_fft_cpu needs h N != 0 in every cell")
+    if spec is None:
+        spec = kernel_spectrum_zero(n, k, side, c_S, dtype=dtype, workers=workers)
+    S_t = S.astype(dtype)
+    rhs = plane_wave(cell_centres(n, origin, side), k, alpha)
+    apply_B = lambda v: symmetrised_matvec_spectrum(v, S_t, spec, n, workers)  # noqa: E731
+    w, it, rr = cocg(apply_B, (S * rhs).astype(dtype), tol=tol, maxit=maxit, dtype=dtype, callback=callback)
+    return w.astype(np.complex128) / S, it, rr
 
 
 def two_particle_solution(u01, u02, g, w1, w2):

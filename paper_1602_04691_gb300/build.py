@@ -7,6 +7,7 @@ of the sources and flags skips the build when nothing changed.
 
 from __future__ import annotations
 
+import glob
 import hashlib
 import os
 import subprocess
@@ -20,7 +21,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libori.so")
 
 SOURCES = ["ori_api.cu", "ori_noalloc.cu", "passes_f32.cu", "passes_f64.cu", "passes_df.cu"]
-HEADERS = ["common.cuh", "dfloat.cuh", "passes.cuh", "passes_impl.cuh", "scalars.cuh", "vector_kernels.cuh"]
+# Every header next to the sources is part of the stamp, so an edit to any of them rebuilds.
+HEADERS = sorted(os.path.basename(f) for f in glob.glob(os.path.join(CSRC, "*.cuh")))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include")]
@@ -31,13 +33,16 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+def stamped_files() -> list[str]:
+    """Absolute paths of every file whose contents enter the build stamp."""
+    return [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "ori.h")]
+
+
 def _stamp() -> str:
     h = hashlib.sha256()
-    for f in SOURCES + HEADERS:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
-    with open(os.path.join(ROOT, "include", "ori.h"), "rb") as fh:
-        h.update(fh.read())
+    for path in stamped_files():
+        with open(path, "rb") as fh:
+            h.update(os.path.basename(path).encode() + fh.read())
     h.update(" ".join(ARCH + FLAGS).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()

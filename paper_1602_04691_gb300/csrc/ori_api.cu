@@ -1075,28 +1075,56 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
     for (int i = 0; i < nrhs; ++i) info[i].fp64_matvecs += bnorm[i] > 0 ? 1 : 0;
   }
   if (o.precision == ORI_FP64) {
-    if (!warm) ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
-    // COCG from w (0, or the warm start) to ||r|| <= tol ||b||
-    for (int i = 0; i < nrhs; ++i)
-      tin[i] = bnorm[i] > 0 && rn0[i] > 0 ? std::min(1.0, o.tol * bnorm[i] / rn0[i]) : 1.0;
-    ORI_TRY(cocg_inner<double>(p, nrhs, rhs_per_k, p->w, p->r64, p->p64, p->q64, p->S64, tin.data(), o.maxit,
-                               o.check_every, graph, ir.data(), !warm));
-    for (int i = 0; i < nrhs; ++i) p->h_skip[i] = bnorm[i] > 0 ? 0 : 1;
-    ORI_TRY(push_skip(p, nrhs));
-    std::vector<double> rn(nrhs, 0.0);
-    ORI_TRY(fp64_residual(p, nrhs, rhs_per_k, false, rn.data()));
+    if (!warm) {
+      ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
+      ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+    }
+    // COCG from w (0, or the warm start) to ||r|| <= tol ||b||.  The recursive
+    // residual can drift from the true one b - B w; when the true residual
+    // misses tol, COCG restarts from w with the true residual (at most
+    // max_outer runs), so ORI_OK always means the true relres <= tol.
+    std::vector<double> rn(rn0);
+    std::vector<int> active(nrhs), total(nrhs, 0), last_done(nrhs, DONE_CONVERGED), runs(nrhs, 0);
+    for (int i = 0; i < nrhs; ++i) active[i] = !bad[i] && bnorm[i] > 0 && rn[i] > o.tol * bnorm[i];
+    for (int run = 0; run < o.max_outer; ++run) {
+      bool any = false;
+      int budget = o.maxit;
+      for (int i = 0; i < nrhs; ++i) {
+        if (!active[i]) continue;
+        any = true;
+        budget = std::min(budget, o.maxit - total[i]);
+      }
+      if (!any || budget <= 0) break;
+      // tolerance 1 marks a system that takes no part in this run
+      for (int i = 0; i < nrhs; ++i) tin[i] = active[i] ? std::min(1.0, o.tol * bnorm[i] / rn[i]) : 1.0;
+      ORI_TRY(cocg_inner<double>(p, nrhs, rhs_per_k, p->w, p->r64, p->p64, p->q64, p->S64, tin.data(), budget,
+                                 o.check_every, graph, ir.data(), false));
+      for (int i = 0; i < nrhs; ++i) p->h_skip[i] = active[i] ? 0 : 1;
+      ORI_TRY(push_skip(p, nrhs));
+      std::vector<double> rn_new(rn);
+      ORI_TRY(fp64_residual(p, nrhs, rhs_per_k, false, rn_new.data()));   // r64 = b - B w
+      for (int i = 0; i < nrhs; ++i) {
+        if (!active[i]) continue;
+        total[i] += ir[i].iters;
+        last_done[i] = ir[i].done;
+        ++runs[i];
+        info[i].fp64_matvecs += 1;
+        info[i].relres_recur = ir[i].relres_recur;
+        const bool progress = rn_new[i] < 0.9 * rn[i];
+        rn[i] = rn_new[i];
+        if (rn[i] <= o.tol * bnorm[i] || ir[i].done != DONE_CONVERGED || !progress || total[i] >= o.maxit)
+          active[i] = 0;
+      }
+    }
     for (int i = 0; i < nrhs; ++i) {
-      info[i].iters = ir[i].iters;
-      info[i].outer_iters = 1;
-      info[i].relres_recur = ir[i].relres_recur;
-      info[i].fp64_matvecs += 1;
+      info[i].iters = total[i];
+      info[i].outer_iters = std::max(1, runs[i]);
       info[i].relres = bnorm[i] > 0 ? rn[i] / bnorm[i] : 0.0;
       info[i].relres_bound = 1e-14;
-      if (bad[i]) info[i].status = ORI_ERR_NONFINITE;
-      else if (bnorm[i] == 0) info[i].status = ORI_OK;
-      else info[i].status = ir[i].done == DONE_CONVERGED
-                                ? (info[i].relres <= 10 * o.tol ? ORI_OK : ORI_ERR_NOT_CONVERGED)
-                                : status_of(ir[i].done);
+      if (bad[i] || !std::isfinite(rn[i])) info[i].status = ORI_ERR_NONFINITE;
+      else if (bnorm[i] == 0 || info[i].relres <= o.tol) info[i].status = ORI_OK;
+      else if (last_done[i] != DONE_CONVERGED) info[i].status = status_of(last_done[i]);
+      else info[i].status = ORI_ERR_NOT_CONVERGED;
     }
     return ORI_OK;
   }

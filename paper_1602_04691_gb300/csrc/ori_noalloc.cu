@@ -92,14 +92,18 @@ __global__ void k_na_extract(const cpx<double>* __restrict__ cube, cpx<double>* 
   }
 }
 
+// The symbol's address is looked up on every call (a host-side query, no
+// allocation): a context created anew on the device (after cudaDeviceReset)
+// may place the array elsewhere, and the cached address would then be stale.
+// The kernel attributes are set again whenever the address changes.
 ori_status setup_device(int dev, void** base) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
   if (dev < 0 || dev >= kMaxDevices) return na_fail(ORI_ERR_UNSUPPORTED, "device index out of range");
-  if (g_scratch_dev[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr)
-      return na_fail(ORI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return na_fail(ORI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  if (g_scratch_dev[dev] != p) {
     for (int L = 4; L <= kMaxL; L *= 2) {
       XArgs xa{};
       SArgs sa{};
@@ -138,7 +142,12 @@ extern "C" ori_status ori_matvec_noalloc(int64_t n64, double k, const ori_domain
   if (c_S == 0.0) c_S = 4.0 * kPi;
   if (!std::isfinite(c_S)) return na_fail(ORI_ERR_INVALID_ARG, "c_S must be finite");
   if (!h_dev || !N_dev || !x_dev || !y_dev) return na_fail(ORI_ERR_INVALID_ARG, "NULL pointer");
-  if (x_dev == y_dev) return na_fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
+  {
+    // [x, x + 16 n^3) and [y, y + 16 n^3) must be disjoint: the last pass reads x while other blocks write y
+    const uintptr_t xb = reinterpret_cast<uintptr_t>(x_dev), yb = reinterpret_cast<uintptr_t>(y_dev);
+    const uintptr_t bytes = uintptr_t(n64) * uintptr_t(n64) * uintptr_t(n64) * sizeof(cpx<double>);
+    if (xb < yb + bytes && yb < xb + bytes) return na_fail(ORI_ERR_INVALID_ARG, "x_dev and y_dev must not overlap");
+  }
 
   int dev = 0;
   NA_CUDA(cudaGetDevice(&dev));

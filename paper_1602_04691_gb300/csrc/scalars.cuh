@@ -125,8 +125,9 @@ __device__ __forceinline__ void finalize(Scalars* sc, const double2* partials, i
       sc->target2 = sc->tol * sc->tol * rn2;
       sc->iter = 0;
       sc->beta = make_double2(0.0, 0.0);
+      // a residual that already meets the target needs no iteration
       sc->done = (!isfinite(rn2) || !isfinite2(rr)) ? DONE_NONFINITE
-               : (rn2 == 0.0 ? DONE_CONVERGED : DONE_RUNNING);
+               : ((rn2 == 0.0 || rn2 <= sc->target2) ? DONE_CONVERGED : DONE_RUNNING);
     } else {
       const int it = sc->iter + 1;
       sc->iter = it;

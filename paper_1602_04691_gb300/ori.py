@@ -132,6 +132,7 @@ class Plan:
         lib.ori_plan_info(self._h, C.byref(nn), C.byref(LL), C.byref(by))
         self.L = int(LL.value)
         self.bytes = int(by.value)
+        self.medium_version = 0   # counts set_medium calls (OriSolve checks it in backward)
 
     # -- lifetime ------------------------------------------------------------
     def close(self):
@@ -204,6 +205,7 @@ class Plan:
         N = _need(N, torch.float64, m, "N")
         _lib.check(_lib.load().ori_plan_set_medium(self.handle, h.data_ptr(), N.data_ptr(),
                                                    _stream_ptr(stream)), "ori_plan_set_medium")
+        self.medium_version += 1
 
     # -- operator ----------------------------------------------------------------
     def matvec(self, x: torch.Tensor, form: str = "A", precision: str = "fp64", stream=None):
@@ -336,21 +338,30 @@ class OriSolve(torch.autograd.Function):
 
     The forward solution is kept for the backward (one checkpoint, no
     per-iteration storage); the backward is one more COCG solve on the same
-    plan (A^T = S B S^-1) plus elementwise products."""
+    plan (A^T = S B S^-1) plus elementwise products.  The medium of the
+    forward (h, N) is saved too: if the plan's medium changed in between (a
+    later forward or set_medium on the same plan), the backward puts it back
+    before the adjoint solve, so each graph gets the gradient of its own
+    forward."""
 
     @staticmethod
     def forward(ctx, h, N, plan: Plan, rhs, kw):
-        plan.set_medium(h.detach(), N.detach())
+        hd, Nd = h.detach(), N.detach()
+        plan.set_medium(hd, Nd)
         u, info = plan.solve(rhs, **kw)
         ctx.plan = plan
         ctx.kw = kw
         ctx.info = info
-        ctx.save_for_backward(u)
+        ctx.medium_version = plan.medium_version
+        ctx.save_for_backward(u, hd, Nd)
         return u
 
     @staticmethod
     def backward(ctx, grad_u):
-        (u,) = ctx.saved_tensors
+        u, hd, Nd = ctx.saved_tensors
+        if ctx.plan.medium_version != ctx.medium_version:
+            ctx.plan.set_medium(hd, Nd)
+            ctx.medium_version = ctx.plan.medium_version
         # grad_u = dL/dRe u + i dL/dIm u; dL = Re(conj(grad_u) du) = 2 Re(conj(e) du), e = grad_u / 2
         econj = torch.conj(grad_u).contiguous() * 0.5
         gh, gN, _ = ctx.plan.adjoint(u, econj.to(torch.complex128), **ctx.kw)

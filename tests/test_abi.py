@@ -94,3 +94,24 @@ def test_binding_resolves_lazy_conjugate_and_negative_views():
     q = _plain(torch._neg_view(c))
     assert not q.is_conj() and not q.is_neg()
     assert torch.equal(torch.view_as_real(q), torch.view_as_real(x).mul(torch.tensor([-1.0, 1.0], dtype=torch.float64)))
+
+
+def test_build_stamp_covers_every_included_file():
+    """Every local file a translation unit includes (directly or through another
+    header) is hashed into the build stamp, so editing it rebuilds libori.so."""
+    from paper_1602_04691_gb300 import build as b
+    hashed = {os.path.realpath(f) for f in b.stamped_files()}
+    seen, todo = set(), [os.path.realpath(os.path.join(b.CSRC, f)) for f in b.SOURCES]
+    while todo:
+        f = todo.pop()
+        if f in seen:
+            continue
+        seen.add(f)
+        with open(f) as fh:
+            for inc in re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), flags=re.M):
+                path = os.path.realpath(os.path.join(os.path.dirname(f), inc))
+                if os.path.exists(path):
+                    todo.append(path)
+    missing = sorted(seen - hashed)
+    assert not missing, missing
+    assert os.path.realpath(os.path.join(b.CSRC, "dfft.cuh")) in hashed

@@ -106,10 +106,13 @@ def test_committed_bench_line_keeps_the_output_contract():
     assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
     assert abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-12
     assert abs(roof["achieved"] - roof["alg_bytes_per_launch"] / (roof["ms_per_launch"] * 1e-3) / 1e9) < 1e-6 * roof["achieved"]
+    # the peak is the measured copy bandwidth of the box the line ran on; the
+    # measurement is repeated on each fresh box, so it may differ by a few per cent
+    assert roof["peak_source"].startswith("measured")
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks):
         with open(peaks) as f:
-            assert roof["peak"] == float(json.load(f)["hbm_gbs"])
+            assert abs(roof["peak"] / float(json.load(f)["hbm_gbs"]) - 1.0) < 0.1
     cpu = d["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["sample"]
     e2e = d["e2e"]

@@ -84,3 +84,25 @@ def test_maxit_zero_returns_not_converged_with_zero_iterate():
     u, info = plan.solve(tol=1e-6, precision="fp64", maxit=0, raise_on_failure=False)
     assert info["returned"] == ORI_ERR_NOT_CONVERGED and info["iters"] == 0
     assert float(u.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cocg_breakdown_is_reported_with_finite_iterate(precision):
+    """COCG's bilinear form r^T r is no norm: a nonzero residual can have
+    r^T r = 0.  With h = 1 and N = 1 (S = 1 exactly) and b = e_0 + i e_1, the
+    first residual S b has r^T r = 1 + i^2 = 0 exactly (also after the mixed
+    solver scales it to unit norm in FP32); the first step then has alpha = 0
+    and leaves r^T r = 0 with r != 0: the breakdown of COCG.  The solve reports
+    ORI_ERR_BREAKDOWN and returns a finite iterate; the plan keeps working."""
+    from paper_1602_04691_gb300 import Plan
+    from paper_1602_04691_gb300._lib import ORI_ERR_BREAKDOWN
+    n = 6
+    h, N = inputs.constant_h_N(n, 1.0, 1.0)
+    plan = Plan(n, 2.0, to_dev(h), to_dev(N))
+    rhs = np.zeros(n ** 3, dtype=np.complex128)
+    rhs[0], rhs[1] = 1.0, 1j
+    u, info = plan.solve(rhs=to_dev(rhs), tol=1e-8, precision=precision, raise_on_failure=False)
+    assert info["returned"] == ORI_ERR_BREAKDOWN and info["status"] == ORI_ERR_BREAKDOWN
+    assert torch.isfinite(torch.view_as_real(u)).all()
+    u, info = plan.solve(tol=1e-8, precision=precision)
+    assert info["status"] == 0 and info["relres"] <= 1e-8

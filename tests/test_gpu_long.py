@@ -4,7 +4,7 @@ passes of FP64 and paired FP32, and the radix-8 TILES schedules of FP32 Y and Z.
 Grids of n >= 513 (up to the paper-scale n = 1000) pad to L = 2048.  The plan
 option min_L forces that length on small grids, where the oracle's direct
 sum and dense LU check every output; a natural n = 520 grid is checked on
-sampled rows.
+rows per tile class in test_gpu_headline.py.
 """
 
 import numpy as np
@@ -101,26 +101,6 @@ def test_L2048_fp32_pipelined_and_radix8_kernels_agree(long_plan):
     assert rel(y_pipe, ref) < 1e-5
     assert rel(y_tiles, ref) < 1e-5
     assert rel(y_pipe, y_tiles) < 1e-5
-
-
-def test_natural_L2048_fp32_matvec_sampled_rows():
-    """n = 520 pads to L = 2048 by itself; the FP32 B-form operator on sampled rows."""
-    from paper_1602_04691_gb300 import Plan
-    n, k = 520, 5.0
-    h, N = inputs.random_h_N(n, 603)
-    x = inputs.random_complex(n ** 3, 604).astype(np.complex64)
-    plan = Plan(n, k, to_dev(h), to_dev(N))
-    assert plan.L == 2048
-    y = plan.matvec32(to_dev(x), form="B").cpu().numpy()
-    rows = np.array([0, n ** 3 - 1, n * n * (n // 2) + n * (n // 2) + n // 2, 123456789])
-    S = O.sqrt_hN(h, N)
-    xs = S * x.astype(np.complex128)
-    d = 1.0 / n
-    Kxs = (O.C_S_SPHERE * d ** 3) * O.offdiag_sum_rows_grid(xs, rows, n, k)
-    ref = x[rows] + S[rows] * Kxs
-    assert rel(y[rows], ref) < 1e-5
-    plan.close()
-    torch.cuda.empty_cache()
 
 
 def test_lean_plan_matches_full_plan_and_rejects_the_rest():

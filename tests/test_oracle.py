@@ -361,6 +361,42 @@ def test_symmetrised_cocg_matches_lu_variable_hN():
     assert rel(u_cg, u_lu) < 1e-10
 
 
+@pytest.mark.parametrize("L", [None, 11, 16])
+def test_spectrum_matvec_equals_direct_sum(L):
+    """The CPU-baseline matvec (zero-embedded spectrum built plane by plane,
+    scipy.fft on threads) against brute-force direct summation of B x, in
+    complex128 (1e-13) and complex64 (1e-5), at odd and power-of-two L."""
+    n, k, side = 6, 2.9, 1.2
+    h, N = inputs.random_h_N(n, 31)
+    x = inputs.random_complex(n ** 3, 32)
+    ref = O.symmetrised_matvec_direct(x, n, k, h, N, side=side)
+    S = O.sqrt_hN(h, N)
+    for dtype, bound in ((np.complex128, 1e-13), (np.complex64, 1e-5)):
+        spec = O.kernel_spectrum_zero(n, k, side, L=L, dtype=dtype, workers=2)
+        assert spec.dtype == dtype
+        y = O.symmetrised_matvec_spectrum(x.astype(dtype), S.astype(dtype), spec, n, workers=2)
+        assert y.dtype == dtype
+        assert rel(y, ref) < bound
+    with pytest.raises(ValueError):
+        O.kernel_spectrum_zero(n, k, side, L=2 * n - 2)
+
+
+def test_cpu_fft_cocg_matches_lu():
+    """The timed CPU solver (the paper's algorithm, Section 3-4) against dense LU:
+    complex128 to relres 1e-12, and complex64 (the paper's arithmetic) to 1e-5."""
+    n, k = 6, 2.0
+    h, N = inputs.random_h_N(n, 2)
+    u_lu = O.solve_dense(O.red_matrix(n, k, h, N), O.plane_wave(O.cell_centres(n), k))
+    seen = []
+    u, it, rr = O.solve_cocg_fft_cpu(n, k, h, N, tol=1e-12, dtype=np.complex128, workers=2,
+                                     callback=seen.append)
+    assert rr <= 1e-12 and seen == list(range(1, it + 1))
+    assert rel(u, u_lu) < 1e-10
+    u, it, rr = O.solve_cocg_fft_cpu(n, k, h, N, tol=1e-5, dtype=np.complex64, workers=2)
+    assert rr <= 1e-5
+    assert rel(u, u_lu) < 1e-4
+
+
 def test_zero_density_cells_recovered():
     """Cells with N = 0 (S = 0) get u = u0 - K(S w) instead of w / S."""
     n, k = 4, 1.3
