@@ -8,7 +8,7 @@ inside FP64 iterative refinement, to relative residual 1e-6.  The plan (the
 kernel spectrum) is built once, outside the timed region, and reported apart.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
-paper's algorithm restated in numpy) on a bounded sample instead.
+paper's algorithm restated in numpy/scipy, on the host cores) instead.
 """
 
 from __future__ import annotations
@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-cpu-legs", action="store_true",
+                    help="CPU baseline: only the full solve of the workload, not the smaller legs")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--no-cufft", action="store_true",
@@ -208,42 +210,102 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle baseline (bounded sample)
+# CPU baseline: the oracle's restatement of the paper's algorithm (COCG with
+# the Section 3 FFT convolution, complex64 as in Section 4) on the host cores
 # ---------------------------------------------------------------------------
-def oracle_sample(n_target: int, k: float, seed: int, tol: float, budget_s: float = 12.0):
-    """The oracle as it stands: the paper's algorithm in numpy (FFT matvec with
-    the mirror padding of size 2n-2, COCG) on the host.  Sample: its COCG
-    iteration count at n = 32 (same recipe, same k, tol), and the time of its
-    FFT matvec at n = 64, repeated for about `budget_s` seconds; the solve time
-    at n_target is (iterations + 1) * matvec time * (N log N of the padded
-    cubes at n_target) / (same at 64)."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+class CpuSolve:
+    """One CPU solve of the benchmark's workload, split into its plan (the
+    kernel spectrum) and COCG iterations so that callers can time either."""
+
+    def __init__(self, n, k, seed, dtype_name="complex64", workers=None):
+        import numpy as np
+        import oracle as O
+        from paper_1602_04691_gb300 import inputs
+        self.O, self.np = O, np
+        self.n, self.k = n, k
+        self.dtype = np.dtype(dtype_name).type
+        self.workers = workers or os.cpu_count()
+        self.h, self.N = inputs.random_h_N(n, seed)
+        t0 = time.perf_counter()
+        self.spec = O.kernel_spectrum_zero(n, k, dtype=self.dtype, workers=self.workers)
+        self.plan_s = time.perf_counter() - t0
+
+    def solve(self, tol, maxit=2000, callback=None):
+        t0 = time.perf_counter()
+        u, it, rr = self.O.solve_cocg_fft_cpu(self.n, self.k, self.h, self.N, tol=tol, maxit=maxit,
+                                              dtype=self.dtype, workers=self.workers, spec=self.spec,
+                                              callback=callback)
+        return u, it, rr, time.perf_counter() - t0
+
+
+def cpu_solve_leg(n, k, seed, tol, dtype_name="complex64", workers=None):
+    cs = CpuSolve(n, k, seed, dtype_name, workers)
+    u, it, rr, solve_s = cs.solve(tol)
+    del cs.spec
+    return {"n": n, "dtype": dtype_name, "plan_s": cs.plan_s, "solve_s": solve_s, "iters": it,
+            "relres_recur": rr}, u
+
+
+def cpu_legs(k, seed, tol, workers):
+    """The other CPU legs, each measured: the oracle's direct-sum matvec (numpy,
+    O(N^2)), dense LU at n = 12, and full CPU FFT-COCG solves at smaller n in
+    complex64 and complex128."""
     import numpy as np
     import oracle as O
     from paper_1602_04691_gb300 import inputs
+    legs = {"direct_sum_matvec_s": {}, "fft_cocg": []}
+    for n in (12, 16, 24):
+        h, N = inputs.random_h_N(n, seed)
+        x = inputs.random_complex(n ** 3, seed + 1)
+        t0 = time.perf_counter()
+        O.red_matvec_direct(x, n, k, h, N)
+        legs["direct_sum_matvec_s"][str(n)] = time.perf_counter() - t0
+    t24 = legs["direct_sum_matvec_s"]["24"]
+    legs["direct_sum_matvec_n512_extrapolated_s"] = t24 * (512 / 24) ** 6
+    n = 12
+    h, N = inputs.random_h_N(n, seed)
     t0 = time.perf_counter()
-    h32, N32 = inputs.random_h_N(32, seed)
-    _, iters, _ = O.solve_red_cocg_fft(32, k, h32, N32, tol=tol)
-    t_iters = time.perf_counter() - t0
-    ns = 64
-    h, N = inputs.random_h_N(ns, seed)
-    x = inputs.random_complex(ns ** 3, seed + 1)
-    c = O.kernel_cube(ns, k, 1.0 / ns)
-    reps, t1 = 0, time.perf_counter()
-    while True:
-        O.symmetrised_matvec_fft(x, ns, k, h, N, _c=c)
-        reps += 1
-        if time.perf_counter() - t1 > budget_s and reps >= 2:
-            break
-    t_mv = (time.perf_counter() - t1) / reps
-    Ls, Lt = 2 * ns - 2, 2 * n_target - 2
-    scale = (Lt ** 3 * math.log(Lt ** 3)) / (Ls ** 3 * math.log(Ls ** 3))
-    est = (iters + 1) * t_mv * scale
-    return {
-        "value": est, "unit": "s", "cores": 1, "kind": "oracle",
-        "sample": (f"oracle COCG iterations at n=32 ({iters}, tol {tol:g}, {t_iters:.1f} s) x oracle FFT "
-                   f"matvec time at n=64 ({t_mv * 1e3:.1f} ms, mean of {reps}) scaled to n={n_target} by padded "
-                   f"N log N ({scale:.0f}x); numpy FFT single-threaded; extrapolated"),
-    }
+    A = O.red_matrix(n, k, h, N)
+    u_lu = O.solve_dense(A, O.plane_wave(O.cell_centres(n), k))
+    legs["dense_lu_n12_s"] = time.perf_counter() - t0
+    del A, u_lu
+    for n in (64, 128, 256):
+        for dt in ("complex64", "complex128"):
+            leg, _ = cpu_solve_leg(n, k, seed, tol, dt, workers)
+            legs["fft_cocg"].append(leg)
+    return legs
+
+
+def cpu_baseline(n, k, seed, tol, u_gpu=None, legs=True):
+    """Full CPU solve of the benchmark workload (measured, not scaled), and
+    the smaller legs.  u_gpu: the GPU solution, compared with the CPU one."""
+    import numpy as np
+    workers = os.cpu_count()
+    leg, u = cpu_solve_leg(n, k, seed, tol, "complex64", workers)
+    out = {"value": leg["solve_s"], "unit": "s", "cores": workers, "kind": "oracle",
+           "sample": (f"one full solve of this workload on the host: the oracle's COCG with the zero-padded "
+                      f"FFT convolution (Section 3) in complex64 (Section 4's arithmetic), scipy.fft on "
+                      f"{workers} threads (elementwise numpy on one), {leg['iters']} iterations to recursive "
+                      f"relres {leg['relres_recur']:.2e}; plan (kernel spectrum) {leg['plan_s']:.1f} s not "
+                      f"included; CPU {cpu_model()}"),
+           "plan_s": leg["plan_s"], "iters": leg["iters"]}
+    if u_gpu is not None:
+        out["cpu_vs_gpu_rel_l2"] = float(np.linalg.norm(u - u_gpu) / np.linalg.norm(u_gpu))
+    del u
+    if legs:
+        out["legs"] = cpu_legs(k, seed, tol, workers)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -275,21 +337,50 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
 
 
 def reference_arm(args, world, rank):
+    """The oracle (the paper's algorithm on the host cores, complex64 as in
+    Section 4) on this workload.  The kernel spectrum is built once, untimed.
+    A step is one COCG iteration of the CPU solve; warm-up and timed steps
+    continue one solve to convergence, then start the next.  value = the wall
+    time of the first complete solve in this run (measured); if no solve
+    completes within the run, value = the mean iteration time x the iterations
+    so far, marked as a lower bound."""
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample(args.n, args.k, args.seed, args.tol, budget_s=1.0)
-    vals = []
-    last = None
-    for _ in range(max(1, args.steps)):
-        last = oracle_sample(args.n, args.k, args.seed, args.tol, budget_s=4.0)
-        vals.append(last["value"])
-    v = statistics.median(vals)
-    cpu = dict(last)
-    cpu["value"] = v
+    cs = CpuSolve(args.n, args.k, args.seed, "complex64")
+    total = args.warmup + args.steps
+    marks = []                      # wall-clock time at the end of each iteration
+    solves = []                     # (start, end, iterations) of each completed solve
+
+    def note(it):
+        marks.append(time.perf_counter())
+
+    t_start = time.perf_counter()
+    while len(marks) < total:
+        t0 = time.perf_counter()
+        _, it, rr, _ = cs.solve(args.tol, maxit=total - len(marks), callback=note)
+        if rr <= args.tol:
+            solves.append((t0, time.perf_counter(), it, rr))
+        if it == 0:
+            break
+    timed = marks[args.warmup:total]
+    starts = [marks[args.warmup - 1] if args.warmup > 0 else t_start] + timed[:-1]
+    per_iter = [b - a for a, b in zip(starts, timed)]
+    ms_step = 1e3 * statistics.mean(per_iter)
+    if solves:
+        s0 = solves[0]
+        v = s0[1] - s0[0]
+        how = (f"wall time of a complete CPU solve in this run ({s0[2]} iterations, recursive relres "
+               f"{s0[3]:.2e})")
+    else:
+        v = ms_step / 1e3 * len(marks)
+        how = f"no solve completed in {len(marks)} iterations: mean iteration x {len(marks)} (lower bound)"
+    cpu = {"value": v, "unit": "s", "cores": cs.workers, "kind": "oracle",
+           "sample": (f"oracle COCG + zero-padded FFT convolution (Section 3), complex64, scipy.fft on "
+                      f"{cs.workers} threads; a step = one COCG iteration at the full size; value = {how}; "
+                      f"plan {cs.plan_s:.1f} s not included; CPU {cpu_model()}")}
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
            "config": workload_config(args), "cpu_baseline": cpu,
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -451,13 +542,21 @@ def ours_arm(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         u_host = torch.empty(n ** 3, dtype=torch.complex128).pin_memory()
+        parts_ms = {"h2d": 0.0, "set_medium": 0.0, "solve": 0.0, "d2h": 0.0}
 
         def e2e_step():
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev[0].record()
             h_dev.copy_(h_host, non_blocking=True)
             N_dev.copy_(N_host, non_blocking=True)
+            ev[1].record()
             plan.set_medium(h_dev, N_dev)
+            ev[2].record()
             plan.solve(out=u, **kw)
+            ev[3].record()
             u_host.copy_(u, non_blocking=True)
+            ev[4].record()
+            return ev
 
         # untimed warm-up: the first transfers from freshly pinned pages run slower
         for _ in range(min(args.warmup, 2)):
@@ -466,18 +565,29 @@ def ours_arm(args, world, rank, local):
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record()
         steps_e2e = max(1, min(args.steps, 3))
+        evs = []
         for _ in range(steps_e2e):
-            e2e_step()
+            evs.append(e2e_step())
         g1.record()
         torch.cuda.synchronize()
+        for ev in evs:
+            for key, a, b in (("h2d", 0, 1), ("set_medium", 1, 2), ("solve", 2, 3), ("d2h", 3, 4)):
+                parts_ms[key] += ev[a].elapsed_time(ev[b]) / steps_e2e
         e2e_s = g0.elapsed_time(g1) / 1e3 / steps_e2e
+        h2d_bytes = h_host.numel() * 16 + N_host.numel() * 8
+        d2h_bytes = u_host.numel() * 16
         e2e = {"value": e2e_s / world, "unit": "s",
-               "h2d_bytes_per_step": h_host.numel() * 16 + N_host.numel() * 8,
-               "d2h_bytes_per_step": u_host.numel() * 16}
+               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
+               "parts_ms": parts_ms,
+               "h2d_GBps": h2d_bytes / (parts_ms["h2d"] * 1e-3) / 1e9 if parts_ms["h2d"] > 0 else None,
+               "d2h_GBps": d2h_bytes / (parts_ms["d2h"] * 1e-3) / 1e9 if parts_ms["d2h"] > 0 else None}
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        cpu = oracle_sample(n, k, args.seed, args.tol)
+        plan.solve(out=u, **kw)
+        u_np = u.cpu().numpy()
+        cpu = cpu_baseline(n, k, args.seed, args.tol, u_gpu=u_np, legs=not args.no_cpu_legs)
+        del u_np
 
     stats_main = stats
     plan.close()
