@@ -90,7 +90,7 @@ __device__ __forceinline__ void dif_stage(cpx<T>* X, int M, const cpx<T>* tw, in
 #pragma unroll
     for (int t = 1; t < R; ++t) v[t] = twL_mul<SIGN>(v[t], tw, (j * t * step) & (L - 1));
 #pragma unroll
-    for (int t = 0; t < R; ++t) X[sidx<C>(base + t * s, c)] = v[t];
+    for (int t = 0; t < R; ++t) X[sidx<C>(base + t * s, c)] = settle(v[t]);
   }
 }
 
@@ -111,7 +111,7 @@ __device__ __forceinline__ void dit_stage(cpx<T>* X, int M, const cpx<T>* tw, in
     for (int t = 1; t < R; ++t) v[t] = twL_mul<SIGN>(v[t], tw, (j * t * step) & (L - 1));
     dft<R, SIGN, false>(v);
 #pragma unroll
-    for (int t = 0; t < R; ++t) X[sidx<C>(base + t * s, c)] = v[t];
+    for (int t = 0; t < R; ++t) X[sidx<C>(base + t * s, c)] = settle(v[t]);
   }
 }
 

@@ -9,10 +9,14 @@
 //   fast_two_sum Dekker 1971, same when |a| >= |b| (3 flops)
 //   two_prod    p + e = a * b exactly, e by one fused multiply-add
 // Addition is the "sloppy" pairwise form (one two_sum on the high parts, the
-// low parts added in FP32, one renormalisation): its error is bounded by a
-// small multiple of 2^-48 (|a| + |b|), which keeps FFT butterflies normwise
-// accurate.  Products accumulate all four partial products before one
-// renormalisation.
+// low parts added in FP32): its error is bounded by a small multiple of
+// 2^-48 (|a| + |b|), which keeps FFT butterflies normwise accurate.
+// Products accumulate all four partial products.  Neither renormalises its
+// result: the pair hi + lo stays an exact-enough representation (|lo| grows
+// by about one unit of 2^-24 |hi| per level of additions), so the FFT stages
+// add and multiply unnormalised pairs and renormalise each value once, when
+// they store it (settle), instead of after every operation: an addition
+// costs 8 FP32 operations instead of 11, a product 16 instead of 19.
 #pragma once
 
 #include "common.cuh"
@@ -36,10 +40,7 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 __device__ __forceinline__ dfl operator+(dfl a, dfl b) {
   float s, e;
   two_sum(a.hi, b.hi, s, e);
-  e += a.lo + b.lo;
-  dfl r;
-  fast_two_sum(s, e, r.hi, r.lo);
-  return r;
+  return {s, e + (a.lo + b.lo)};
 }
 __device__ __forceinline__ dfl operator-(dfl a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
@@ -48,8 +49,15 @@ __device__ __forceinline__ dfl operator*(dfl a, dfl b) {
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
+  return {p, e};
+}
+
+// Renormalise: |lo| <= ulp(hi) / 2 again.  The fast form is exact when
+// |hi| >= |lo|; where cancellation left |hi| < |lo| the value is tiny next to
+// the operands that produced it, so the normwise error bound still holds.
+__device__ __forceinline__ dfl settle(dfl a) {
   dfl r;
-  fast_two_sum(p, e, r.hi, r.lo);
+  fast_two_sum(a.hi, a.lo, r.hi, r.lo);
   return r;
 }
 
@@ -66,15 +74,18 @@ __device__ __forceinline__ dfl df_dot2(dfl a, dfl b, dfl c, dfl d, float sign) {
   e = __fmaf_rn(a.lo, b.hi, e);
   e = __fmaf_rn(sign * c.hi, d.lo, e);
   e = __fmaf_rn(sign * c.lo, d.hi, e);
-  dfl r;
-  fast_two_sum(s, e, r.hi, r.lo);
-  return r;
+  return {s, e};
 }
 
 // Complex product in double-float.
 __device__ __forceinline__ cpx<dfl> cmul(cpx<dfl> a, cpx<dfl> b) {
   return {df_dot2(a.x, b.x, a.y, b.y, -1.0f), df_dot2(a.x, b.y, a.y, b.x, 1.0f)};
 }
+
+// A value as it is stored between FFT stages: renormalised for paired FP32,
+// unchanged for the other arithmetics.
+template <class T> __device__ __forceinline__ cpx<T> settle(cpx<T> v) { return v; }
+template <> __device__ __forceinline__ cpx<dfl> settle<dfl>(cpx<dfl> v) { return {settle(v.x), settle(v.y)}; }
 
 // Split a double into hi + lo (hi = nearest float, lo = nearest float of the rest).
 __device__ __forceinline__ dfl df_from_double(double v) {

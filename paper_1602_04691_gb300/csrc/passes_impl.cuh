@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xfwd
 #pragma unroll
   for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
 #pragma unroll
-  for (int k1 = 0; k1 < L1; ++k1) sm[c * PC + k1 * PK + j2] = r[k1];
+  for (int k1 = 0; k1 < L1; ++k1) sm[c * PC + k1 * PK + j2] = settle(r[k1]);
   __syncthreads();
   cpx<T>* out = reinterpret_cast<cpx<T>*>(a.fft_out);
 #pragma unroll
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xfwd
     if (l2 < a.nlines) {
       cpx<T>* o = out + l2 * a.line_len_out;
 #pragma unroll
-      for (int k2 = 0; k2 < L2; ++k2) o[k1 + L1 * k2] = b[k2];
+      for (int k2 = 0; k2 < L2; ++k2) o[k1 + L1 * k2] = settle(b[k2]);
     }
   }
 }
@@ -284,12 +284,12 @@ __device__ __forceinline__ void x_epilogue(const XArgs& a, long long i, cpx<T> v
     switch (a.mode) {
       case EPI_PLUS: {
         const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
-        reinterpret_cast<cpx<T>*>(a.out)[i] = xi + v;
+        reinterpret_cast<cpx<T>*>(a.out)[i] = settle(xi + v);
       } break;
       case EPI_PLUS_S: {
         const cpx<T> xi = reinterpret_cast<const cpx<T>*>(a.xin)[i];
         const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-        reinterpret_cast<cpx<T>*>(a.out)[i] = xi + cmul(s, v);
+        reinterpret_cast<cpx<T>*>(a.out)[i] = settle(xi + cmul(s, v));
       } break;
       case EPI_PLUS_D: {
         const cpx<double> xi = reinterpret_cast<const cpx<double>*>(a.xin)[i];
@@ -304,7 +304,7 @@ __device__ __forceinline__ void x_epilogue(const XArgs& a, long long i, cpx<T> v
       case EPI_COCG: {
         const cpx<T> p = reinterpret_cast<const cpx<T>*>(a.xin)[i];
         const cpx<T> s = ldgc(reinterpret_cast<const cpx<T>*>(a.scale) + i);
-        const cpx<T> q = p + cmul(s, v);
+        const cpx<T> q = settle(p + cmul(s, v));
         reinterpret_cast<cpx<T>*>(a.out)[i] = q;
         accT = accT + cmul(p, q);                 // p^T q, no conjugate
       } break;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv
 #pragma unroll
     for (int ja = 1; ja < L2; ++ja) b[ja] = twL_mul<+1>(b[ja], tw, (ja * k1) & (L - 1));
 #pragma unroll
-    for (int ja = 0; ja < L2; ++ja) sm[c2 * PCI + ja * PKI + k1] = b[ja];
+    for (int ja = 0; ja < L2; ++ja) sm[c2 * PCI + ja * PKI + k1] = settle(b[ja]);
   }
   __syncthreads();
   // stage B: DFT over k1 -> x[ja + L2 jb]
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
 #pragma unroll
     for (int k1 = 1; k1 < L1; ++k1) r[k1] = twL_mul<-1>(r[k1], tw, (j2 * k1) & (L - 1));
 #pragma unroll
-    for (int k1 = 0; k1 < L1; ++k1) sm[c * PC + k1 * PK + j2] = r[k1];
+    for (int k1 = 0; k1 < L1; ++k1) sm[c * PC + k1 * PK + j2] = settle(r[k1]);
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
 #pragma unroll
           for (int k2 = 0; k2 < L2; ++k2) {
             const int k = k1 + L1 * k2;
-            if (k < a.n_out) out[(long long)k * a.out_pt + c2] = b[it][k2];
+            if (k < a.n_out) out[(long long)k * a.out_pt + c2] = settle(b[it][k2]);
           }
         }
       }
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
 #pragma unroll
     for (int ja = 1; ja < L2; ++ja) b[it][ja] = twL_mul<+1>(b[it][ja], tw, (ja * k1) & (L - 1));
 #pragma unroll
-    for (int ja = 0; ja < L2; ++ja) sm[c2 * PCI + ja * PKI + k1] = b[it][ja];
+    for (int ja = 0; ja < L2; ++ja) sm[c2 * PCI + ja * PKI + k1] = settle(b[it][ja]);
   }
   __syncthreads();
   // inverse stage B
@@ -706,7 +706,7 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT) k_strided(SArgs a0) {
 #pragma unroll
     for (int jb = 0; jb < L1; ++jb) {
       const int j = ja + L2 * jb;
-      if (j < a.n_out) out[(long long)j * a.out_pt + c] = r[jb];
+      if (j < a.n_out) out[(long long)j * a.out_pt + c] = settle(r[jb]);
     }
   }
 }
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_st
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
-      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
+      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = settle(v[t]);
     }
     __syncthreads();
     dif_rest<L, C>(X, TW, tid, NT);
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_st
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int z = j + t * S8;
-        if (c < colmax && z < a.n_out) out[(long long)z * a.out_pt + c] = v[t];
+        if (c < colmax && z < a.n_out) out[(long long)z * a.out_pt + c] = settle(v[t]);
       }
     }
   }
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xf
 #pragma unroll
     for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
-    for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
+    for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = settle(v[t]);
   }
   __syncthreads();
   dif_rest<L, C>(X, TW, tid, NT);
@@ -1327,7 +1327,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
-      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = v[t];
+      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = settle(v[t]);
     }
     __syncthreads();
     if (next < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, next, per_rhs, S);
@@ -1339,7 +1339,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
       const int mz = mirror_index(digit_rev<L>(p), L);
       const int mx = mirror_index(cb * C + c, L);
       const int si = sidx<C>(p, c);
-      X[si] = cmul(X[si], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx));
+      X[si] = settle(cmul(X[si], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx)));
     }
     __syncthreads();
     dit_head<L, C>(X, TW, tid, NT);
@@ -1356,7 +1356,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int z = j + t * S8;
-        if (z < a.n_out) out[(long long)z * a.out_pt + c] = v[t];
+        if (z < a.n_out) out[(long long)z * a.out_pt + c] = settle(v[t]);
       }
     }
     tile = next;
