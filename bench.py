@@ -128,21 +128,36 @@ def traffic_from_profiles(kernel: str, n: int):
     return ent["dram_bytes_per_launch"]
 
 
+def split_L1(L: int) -> int:
+    """First-stage radix of the default split L = L1 * L2 (Split<L> in the sources)."""
+    lg = L.bit_length() - 1
+    return 1 << ((lg + 1) // 2)
+
+
 def fp32_kernel_name(kind: str, L: int, sched: dict) -> str:
     """The FP32 kernel that runs a pass of the B-form matvec at padded length L
-    (L >= 64) under a launch schedule (1 = ORI_SCHED_TILES)."""
+    (L >= 64) under a launch schedule (1 = ORI_SCHED_TILES; *_variant: tile
+    width and radix split of the persistent Y and Z kernels at L = 256..1024)."""
     tiles = {key: sched.get(key, 0) == 1 for key in ("yfwd", "zconv", "yinv")}
     if kind == "update":
         return "k_cocg_update<float>"
+    L1 = split_L1(L)
+
+    def pipe(key):
+        v = sched.get(key + "_variant", 0) if 256 <= L <= 1024 else 0
+        C, l1 = {0: (16, L1), 1: (8, L1), 2: (16, 2 * L1)}[v] if L <= 1024 else (8, L1)
+        return C, l1
+
     if L <= 1024:
+        (cy, ly), (cz, lz), (ci, li) = pipe("yfwd"), pipe("zconv"), pipe("yinv")
         return {"xfwd": f"k_xfwd_pipe<{L}, 4>", "xinv": f"k_xinv_pipe<{L}, 4>",
-                "yfwd": f"k_strided<float, {L}>(FWD)" if tiles["yfwd"] else f"k_yfwd_pipe<float, {L}, 16>",
-                "zconv": f"k_strided<float, {L}>(ZCONV)" if tiles["zconv"] else f"k_zconv_pipe<float, {L}, 16>",
-                "yinv": f"k_strided<float, {L}>(INV)" if tiles["yinv"] else f"k_yinv_pipe<{L}, 16>"}[kind]
+                "yfwd": f"k_strided<float, {L}>(FWD)" if tiles["yfwd"] else f"k_yfwd_pipe<float, {L}, {cy}, {ly}>",
+                "zconv": f"k_strided<float, {L}>(ZCONV)" if tiles["zconv"] else f"k_zconv_pipe<float, {L}, {cz}, {lz}>",
+                "yinv": f"k_strided<float, {L}>(INV)" if tiles["yinv"] else f"k_yinv_pipe<{L}, {ci}, {li}>"}[kind]
     return {"xfwd": f"k_xfwd_pipe<{L}, 4>", "xinv": f"k_xinv_pipe<{L}, 4>",
-            "yfwd": f"k_strided_smem<float, {L}, 4>(FWD)" if tiles["yfwd"] else f"k_yfwd_pipe<float, {L}, 8>",
-            "zconv": f"k_zconv_smem<float, {L}, 8>" if tiles["zconv"] else f"k_zconv_pipe<float, {L}, 8>",
-            "yinv": f"k_strided_smem<float, {L}, 4>(INV)" if tiles["yinv"] else f"k_yinv_pipe<{L}, 8>"}[kind]
+            "yfwd": f"k_strided_smem<float, {L}, 4>(FWD)" if tiles["yfwd"] else f"k_yfwd_pipe<float, {L}, 8, {L1}>",
+            "zconv": f"k_zconv_smem<float, {L}, 8>" if tiles["zconv"] else f"k_zconv_pipe<float, {L}, 8, {L1}>",
+            "yinv": f"k_strided_smem<float, {L}, 4>(INV)" if tiles["yinv"] else f"k_yinv_pipe<{L}, 8, {L1}>"}[kind]
 
 
 # ---------------------------------------------------------------------------
@@ -562,6 +577,18 @@ def ours_arm(args, world, rank, local):
         for _ in range(min(args.warmup, 2)):
             e2e_step()
         torch.cuda.synchronize()
+        # the host link alone: the same pinned buffers copied with nothing else running
+        link = {}
+        for key, fn, nbytes in (("h2d", lambda: h_dev.copy_(h_host, non_blocking=True), h_host.numel() * 16),
+                                ("d2h", lambda: u_host.copy_(u, non_blocking=True), u_host.numel() * 16)):
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()
+            c0.record()
+            for _ in range(3):
+                fn()
+            c1.record()
+            torch.cuda.synchronize()
+            link[key + "_GBps"] = 3 * nbytes / (c0.elapsed_time(c1) * 1e-3) / 1e9
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record()
         steps_e2e = max(1, min(args.steps, 3))
@@ -580,7 +607,8 @@ def ours_arm(args, world, rank, local):
                "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                "parts_ms": parts_ms,
                "h2d_GBps": h2d_bytes / (parts_ms["h2d"] * 1e-3) / 1e9 if parts_ms["h2d"] > 0 else None,
-               "d2h_GBps": d2h_bytes / (parts_ms["d2h"] * 1e-3) / 1e9 if parts_ms["d2h"] > 0 else None}
+               "d2h_GBps": d2h_bytes / (parts_ms["d2h"] * 1e-3) / 1e9 if parts_ms["d2h"] > 0 else None,
+               "host_link_alone": link}
 
     cpu = None
     if not args.no_cpu and rank == 0:

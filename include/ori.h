@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define ORI_ABI_VERSION 3
+#define ORI_ABI_VERSION 4
 
 typedef struct ori_plan_s* ori_plan_t;
 
@@ -323,8 +323,10 @@ ori_status ori_adjoint_solve(ori_plan_t plan, const double* u_dev,
  * kernels: a persistent one that streams the next tile into shared memory
  * with cp.async while it transforms the current one, and one CTA per tile of
  * columns.  Which is faster depends on n, the batch size and the GPU; so does
- * the grid of the vector kernels.  The paper has no counterpart (its code is
- * a CPU FFT library).  Paired-FP32 and FP64 passes have one schedule each.
+ * the grid of the vector kernels, and the tile width and radix split of the
+ * persistent kernels (the launch variants).  The paper relied on its FFT
+ * library's planner (Section 3).  Paired-FP32 and FP64 passes have one
+ * schedule each.
  */
 enum { ORI_SCHED_PERSISTENT = 0, ORI_SCHED_TILES = 1 };
 
@@ -337,7 +339,14 @@ typedef struct {
   int vec_ctas_per_sm;  /* vector kernels (updates, norms): CTAs per SM, 1..16;
                            0 -> 8 (default)                                        */
   int yinv;             /* FP32 Y inverse pass                                     */
-  int reserved[3];
+  int yfwd_variant;     /* persistent FP32 Y-forward, Z and Y-inverse kernels at padded
+                           lengths L = 256 .. 1024 (ori_plan_info): 0 (default) tiles
+                           of 16 columns with the transform split L = L1 * L2,
+                           L1 = 2^ceil(log2(L) / 2); 1: tiles of 8 columns;
+                           2: 16 columns, split (2 L1) * (L2 / 2).  Other lengths
+                           have variant 0 only                                     */
+  int zconv_variant;
+  int yinv_variant;
 } ori_schedule;
 
 /* The plan's current schedule. */
@@ -350,8 +359,10 @@ ori_status ori_plan_set_schedule(ori_plan_t plan, const ori_schedule* s);
 /*
  * ori_plan_autotune - time the candidate schedules on this plan for a batch of
  * nrhs systems (1..4096) and keep the fastest.  Starting from the plan's
- * schedule, each field in turn (Y-forward, Z and Y-inverse kernels, then the
- * persistent CTA cap 1 or 2) takes the alternative that lowers the time of
+ * schedule, each field in turn (Y-forward, Z and Y-inverse kernels, their
+ * launch variants 1 and 2 where the length has them and the kernel is the
+ * persistent one, then the persistent CTA cap 1 or 2) takes the alternative
+ * that lowers the time of
  * `reps` (1..100) FP32 operator applications y = B x on the plan's scratch
  * vectors (each timing after one warm-up); then the vector grid (4, 8 or 16
  * CTAs per SM) is timed on the FP32 COCG update.  Grows the plan's batch scratch to nrhs like

@@ -13,6 +13,8 @@ import os
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libori.so")
 
+ABI_VERSION = 4   # ORI_ABI_VERSION of include/ori.h that these declarations follow
+
 ORI_OK = 0
 ORI_ERR_INVALID_ARG = 1
 ORI_ERR_CUDA = 2
@@ -74,11 +76,17 @@ class SolveInfo(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("yfwd", C.c_int), ("zconv", C.c_int), ("ctas_per_sm", C.c_int),
-                ("vec_ctas_per_sm", C.c_int), ("yinv", C.c_int), ("reserved", C.c_int * 3)]
+                ("vec_ctas_per_sm", C.c_int), ("yinv", C.c_int), ("yfwd_variant", C.c_int),
+                ("zconv_variant", C.c_int), ("yinv_variant", C.c_int)]
+
+    VARIANTS = ("yfwd_variant", "zconv_variant", "yinv_variant")
 
     def as_dict(self):
-        return {"yfwd": int(self.yfwd), "zconv": int(self.zconv), "yinv": int(self.yinv),
-                "ctas_per_sm": int(self.ctas_per_sm), "vec_ctas_per_sm": int(self.vec_ctas_per_sm)}
+        d = {"yfwd": int(self.yfwd), "zconv": int(self.zconv), "yinv": int(self.yinv),
+             "ctas_per_sm": int(self.ctas_per_sm), "vec_ctas_per_sm": int(self.vec_ctas_per_sm)}
+        for k in self.VARIANTS:
+            d[k] = int(getattr(self, k))
+        return d
 
     @classmethod
     def from_dict(cls, d):
@@ -88,6 +96,8 @@ class Schedule(C.Structure):
         s.ctas_per_sm = int(d["ctas_per_sm"])
         s.vec_ctas_per_sm = int(d["vec_ctas_per_sm"])
         s.yinv = int(d.get("yinv", 0))
+        for k in cls.VARIANTS:
+            setattr(s, k, int(d.get(k, 0)))
         return s
 
 
@@ -171,6 +181,9 @@ def load():
     lib.ori_last_error.restype = C.c_char_p
     lib.ori_abi_version.argtypes = []
     lib.ori_abi_version.restype = i
+    if lib.ori_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{LIB_PATH} has ABI version {lib.ori_abi_version()}, the binding expects "
+                           f"{ABI_VERSION}: rebuild it with __graft_entry__.build()")
     _lib = lib
     return lib
 

@@ -5,10 +5,14 @@ plan; this module keeps the winners in a JSON file keyed by GPU name, grid
 size n, batch size and arithmetic, so that later plans for the same key take
 the cached schedule without timing anything.  The file maps
 
-    "<gpu name>|n=<n>|nrhs=<nrhs>|arith=fp32"  ->  {"schedule": {...}, "ms": t}
+    "<gpu name>|n=<n>|nrhs=<nrhs>|arith=fp32|sched=2"  ->  {"schedule": {...}, "ms": t}
 
-where "schedule" holds the ori_schedule fields and "ms" the FP32 operator
-time of the whole batch measured when the entry was written.
+where "schedule" holds the ori_schedule fields (kernel choice, launch variant
+(tile width and radix split) and CTA cap of the FP32 Y-forward, Z and
+Y-inverse passes, and the vector-kernel grid) and "ms" the FP32 operator time
+of the whole batch measured when the entry was written.  "sched" numbers the
+set of fields the tuner searches: entries written for an older set are tuned
+again.
 
 Cache location: the ``path`` argument, else the ORI_AUTOTUNE_CACHE
 environment variable, else ``~/.cache/ori_autotune.json``.
@@ -21,6 +25,7 @@ import os
 import tempfile
 
 ARITH = "fp32"   # the tuned schedules are those of the FP32 passes
+SCHED_FIELDS_VERSION = 2   # 2: launch variants (tile width, radix split) added
 
 
 def cache_path(path: str | None = None) -> str:
@@ -33,7 +38,7 @@ def cache_path(path: str | None = None) -> str:
 
 
 def cache_key(gpu_name: str, n: int, nrhs: int, arith: str = ARITH) -> str:
-    return f"{gpu_name}|n={int(n)}|nrhs={int(nrhs)}|arith={arith}"
+    return f"{gpu_name}|n={int(n)}|nrhs={int(nrhs)}|arith={arith}|sched={SCHED_FIELDS_VERSION}"
 
 
 def load(path: str) -> dict:
@@ -62,7 +67,8 @@ def store(path: str, key: str, schedule: dict, ms: float) -> None:
         raise
 
 
-_FIELDS = ("yfwd", "zconv", "yinv", "ctas_per_sm", "vec_ctas_per_sm")
+_FIELDS = ("yfwd", "zconv", "yinv", "ctas_per_sm", "vec_ctas_per_sm", "yfwd_variant", "zconv_variant",
+           "yinv_variant")
 
 
 def valid_schedule(s) -> bool:

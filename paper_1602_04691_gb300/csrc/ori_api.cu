@@ -137,6 +137,7 @@ struct ori_plan_s {
   int vec_grid = 0;
   // launch schedule (ori_schedule): FP32 Y-forward / Z kernels, CTA cap, vector grid
   int sched_y = SCHED_PERSISTENT, sched_z = SCHED_PERSISTENT, sched_yi = SCHED_PERSISTENT, cta_cap = 0, vec_ctas = 8;
+  int var_y = 0, var_z = 0, var_yi = 0;   // launch variants of the persistent FP32 kernels
   // accounting (ori_plan_stats) and optional per-kernel event timing
   ori_plan_stats stats{};
   bool capturing = false;
@@ -403,7 +404,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.in_pt = L; y.out_pt = L; y.ncols = L; y.n_in = n; y.n_out = L; y.nouter = n;
   y.twL = tw; y.done = mask.flags; y.done_stride = mask.stride; y.sm_count = p->sm_count;
   y.nrhs = nrhs; y.bs_in = bsT1; y.bs_out = bsT2;
-  y.sched = p->sched_y; y.cta_cap = p->cta_cap;
+  y.sched = p->sched_y; y.cta_cap = p->cta_cap; y.variant = p->var_y;
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + K, e0, e1); e0 = e1;
@@ -419,7 +420,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.bs_ghat = H3 * (long long)sizeof(cpx<T>);
   z.bs_ghatZ = (long long)p->H * p->H * p->L * (long long)sizeof(cpx<float>);
   z.rhs_per_ghat = rhs_per_k;
-  z.sched = p->sched_z; z.cta_cap = p->cta_cap;
+  z.sched = p->sched_z; z.cta_cap = p->cta_cap; z.variant = p->var_z;
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + K, e0, e1); e0 = e1;
@@ -430,7 +431,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   yi.in_pt = L; yi.out_pt = L; yi.ncols = L; yi.n_in = L; yi.n_out = n; yi.nouter = n;
   yi.twL = tw; yi.done = mask.flags; yi.done_stride = mask.stride;
   yi.nrhs = nrhs; yi.bs_in = bsT2; yi.bs_out = bsT1;
-  yi.sm_count = p->sm_count; yi.sched = p->sched_yi; yi.cta_cap = p->cta_cap;
+  yi.sm_count = p->sm_count; yi.sched = p->sched_yi; yi.cta_cap = p->cta_cap; yi.variant = p->var_yi;
   ORI_CUDA(run_strided<T>(L, SMODE_INV, false, yi, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + K, e0, e1); e0 = e1;
@@ -1420,6 +1421,9 @@ static void apply_schedule(ori_plan_s* p, const ori_schedule& s) {
   p->sched_y = s.yfwd;
   p->sched_z = s.zconv;
   p->sched_yi = s.yinv;
+  p->var_y = s.yfwd_variant;
+  p->var_z = s.zconv_variant;
+  p->var_yi = s.yinv_variant;
   p->cta_cap = s.ctas_per_sm;
   p->vec_ctas = s.vec_ctas_per_sm > 0 ? s.vec_ctas_per_sm : 8;
   p->vec_grid = std::max(1, p->sm_count) * p->vec_ctas;
@@ -1431,6 +1435,9 @@ static ori_schedule current_schedule(const ori_plan_s* p) {
   s.yfwd = p->sched_y;
   s.zconv = p->sched_z;
   s.yinv = p->sched_yi;
+  s.yfwd_variant = p->var_y;
+  s.zconv_variant = p->var_z;
+  s.yinv_variant = p->var_yi;
   s.ctas_per_sm = p->cta_cap;
   s.vec_ctas_per_sm = p->vec_ctas;
   return s;
@@ -1496,12 +1503,24 @@ static ori_status autotune(ori_plan_s* p, int nrhs, int reps, ori_schedule* best
   // one field at a time, keeping the best value of each before the next
   ORI_TRY(time_fp32_operator(p, nrhs, reps, &best_t));
   if (p->L >= 64 && p->L <= 1024) {   // longer transforms have one schedule
-    for (int field = 0; field < 4; ++field) {
-      const int values[2] = {field < 3 ? SCHED_TILES : 1, field < 3 ? SCHED_TILES : 2};
-      for (int vi = 0; vi < (field < 3 ? 1 : 2); ++vi) {
+    const int nv = pipe_variants(p->L);
+    // fields: 0-2 kernel choice of Y fwd, Z, Y inv; 3-5 their launch variants
+    // (persistent kernels only); 6 the persistent CTA cap
+    for (int field = 0; field < 7; ++field) {
+      const bool var_field = field >= 3 && field < 6;
+      if (var_field) {
+        const int sched = field == 3 ? best.yfwd : field == 4 ? best.zconv : best.yinv;
+        if (sched != SCHED_PERSISTENT || nv < 2) continue;
+      }
+      const int nval = field < 3 ? 1 : (var_field ? nv - 1 : 2);
+      for (int vi = 0; vi < nval; ++vi) {
         ori_schedule s = best;
-        int* f = field == 0 ? &s.yfwd : field == 1 ? &s.zconv : field == 2 ? &s.yinv : &s.ctas_per_sm;
-        *f = values[vi];
+        int* f = field == 0 ? &s.yfwd : field == 1 ? &s.zconv : field == 2 ? &s.yinv
+               : field == 3 ? &s.yfwd_variant : field == 4 ? &s.zconv_variant : field == 5 ? &s.yinv_variant
+               : &s.ctas_per_sm;
+        const int value = field < 3 ? SCHED_TILES : (var_field ? (vi + 1 == *f ? 0 : vi + 1) : vi + 1);
+        if (value == *f) continue;
+        *f = value;
         apply_schedule(p, s);
         float t = 0.f;
         ORI_TRY(time_fp32_operator(p, nrhs, reps, &t));
@@ -1554,6 +1573,11 @@ ori_status ori_plan_set_schedule(ori_plan_t p, const ori_schedule* s) {
   if (s->ctas_per_sm < 0 || s->ctas_per_sm > 64) return fail(ORI_ERR_INVALID_ARG, "ctas_per_sm must be in [0, 64]");
   if (s->vec_ctas_per_sm < 0 || s->vec_ctas_per_sm > kMaxVecCtasPerSm)
     return fail(ORI_ERR_INVALID_ARG, "vec_ctas_per_sm must be in [0, 16]");
+  const int nv = pipe_variants(p->L);
+  auto var_ok = [nv](int v) { return v >= 0 && v < nv; };
+  if (!var_ok(s->yfwd_variant) || !var_ok(s->zconv_variant) || !var_ok(s->yinv_variant))
+    return fail(ORI_ERR_INVALID_ARG, "launch variants must be in [0, " + std::to_string(nv) +
+                                         ") at this padded length");
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   apply_schedule(p, *s);
   return ORI_OK;

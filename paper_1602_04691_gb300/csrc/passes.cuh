@@ -121,6 +121,7 @@ struct SArgs {
   // SCHED_TILES = one CTA per tile of columns
   int sched;
   int cta_cap;
+  int variant;                     // pipelined FP32 kernels: launch variant (has_pipe_variants)
 };
 
 enum { SCHED_PERSISTENT = 0, SCHED_TILES = 1 };
@@ -165,10 +166,18 @@ __device__ __forceinline__ SArgs s_for_rhs(SArgs a, int rhs) {
   return a;
 }
 
-template <int L, int C, class T>
+// Launch variants of the pipelined FP32 Y-forward, Z and Y-inverse passes at
+// the padded lengths where the autotuner chooses among them:
+//   0: the default tile (16 columns) and split L = L1 * L2 of Split<L>;
+//   1: 8-column tiles, same split;
+//   2: 16-column tiles, first stage of radix 2 * L1 (second of L2 / 2).
+constexpr bool has_pipe_variants(int L) { return L >= 256 && L <= 1024; }
+constexpr int pipe_variants(int L) { return has_pipe_variants(L) ? 3 : 1; }
+
+template <int L, int C, class T, int L1X = Split<L>::L1>
 struct Tile {
-  static constexpr int L1 = Split<L>::L1;
-  static constexpr int L2 = Split<L>::L2;
+  static constexpr int L1 = L1X;
+  static constexpr int L2 = L / L1X;
   static constexpr int NT = C * L2;            // threads per CTA
   static constexpr int PK = L2 + 1;            // forward exchange [c][k1][j2]
   static constexpr int PC = (L1 * PK) | 1;

@@ -29,9 +29,9 @@ __device__ __forceinline__ cpx<T> tw_mul_val(cpx<T> z, cpx<T> w) {
 // tab2[k1 * L2 + j] = tab[(j * k1) mod L] for k1 < L1, j < L2 (L entries), so
 // that a thread with fixed j (or fixed k1) finds its twiddles at constant
 // offsets from one base pointer.
-template <int L, class T>
+template <int L, int L2X = Split<L>::L2, class T>
 __device__ __forceinline__ void fill_tw2(cpx<T>* tab2, const cpx<T>* tab, int tid, int nt) {
-  constexpr int L2 = Split<L>::L2;
+  constexpr int L2 = L2X;
   for (int i = tid; i < L; i += nt) {
     const int k1 = i / L2, j = i - k1 * L2;
     tab2[i] = tab[(j * k1) & (L - 1)];
@@ -1074,9 +1074,9 @@ __device__ __forceinline__ int next_live_tile(const SArgs& a, int t, int step, i
   return t;
 }
 
-template <int L, int C, class T>
+template <int L, int C, class T, int L1X = Split<L>::L1>
 struct ZPipe {
-  using TL = Tile<L, C, T>;
+  using TL = Tile<L, C, T, L1X>;
   static constexpr int NT = TL::NT;
   static constexpr bool GZ = sizeof(T) == 4;              // spectrum staged through smem
   static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
@@ -1085,9 +1085,9 @@ struct ZPipe {
   static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + TW_ELEMS) * sizeof(cpx<T>);
 };
 
-template <class T, int L, int C>
+template <class T, int L, int C, int L1X>
 __device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
-  constexpr int NT = ZPipe<L, C, T>::NT;
+  constexpr int NT = ZPipe<L, C, T, L1X>::NT;
   constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;    // 16-byte chunks per row
   const int col_blocks = L / C;
   const int rhs = tile / per_rhs;
@@ -1129,10 +1129,10 @@ __device__ __forceinline__ void zpipe_prefetch_rows(const SArgs& a, int tile, in
 // and kx in the tile, copied to S as [mz][C].  The Z-tile order stores the
 // FP32 spectrum in groups of kZGroup columns, [my][kx / kZGroup][mz][kZGroup];
 // a tile of C columns (C divides kZGroup) reads C of each group row.
-template <class T, int L, int C>
+template <class T, int L, int C, int L1X>
 __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int rhs, int ky, int cb, cpx<T>* S) {
   static_assert(kZGroup % C == 0, "tile width must divide the spectrum group");
-  constexpr int NT = ZPipe<L, C, T>::NT;
+  constexpr int NT = ZPipe<L, C, T, L1X>::NT;
   const int my = mirror_index(ky, L);
   const int g = a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0;
   const int kx0 = cb * C;
@@ -1149,11 +1149,12 @@ __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int rhs, int
   cp_async_commit();
 }
 
-template <class T, int L, int C>
-__global__ void __launch_bounds__(ZPipe<L, C, T>::NT, (ZPipe<L, C, T>::NT <= 256 && sizeof(T) == 4 && L <= 1024) ? 2 : 1)
+template <class T, int L, int C, int L1X = Split<L>::L1>
+__global__ void __launch_bounds__(ZPipe<L, C, T, L1X>::NT,
+                                  (ZPipe<L, C, T, L1X>::NT <= 256 && sizeof(T) == 4 && L <= 1024 && L1X < 64) ? 2 : 1)
 k_zconv_pipe(SArgs a) {
-  using TL = Tile<L, C, T>;
-  using ZP = ZPipe<L, C, T>;
+  using TL = Tile<L, C, T, L1X>;
+  using ZP = ZPipe<L, C, T, L1X>;
   constexpr bool GZ = ZP::GZ;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PK = TL::PK, PC = TL::PC, PKI = TL::PKI, PCI = TL::PCI;
@@ -1162,7 +1163,7 @@ k_zconv_pipe(SArgs a) {
   cpx<T>* S = E + ZP::E_ELEMS;
   cpx<T>* TWS = S + ZP::S_ELEMS;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
-  if (GZ) fill_tw2<L>(TWS, twg, threadIdx.x, NT);   // [k1][j] layout
+  if (GZ) fill_tw2<L, L2>(TWS, twg, threadIdx.x, NT);   // [k1][j] layout
   const cpx<T>* tw = GZ ? TWS : twg;
   const int col_blocks = L / C;
   const int per_rhs = L * col_blocks;
@@ -1172,7 +1173,7 @@ k_zconv_pipe(SArgs a) {
   const int c = tid % C, jl = tid / C;
 
   int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
-  if (tile < ntiles) zpipe_prefetch<T, L, C>(a, tile, per_rhs, S);
+  if (tile < ntiles) zpipe_prefetch<T, L, C, L1X>(a, tile, per_rhs, S);
   while (tile < ntiles) {
     const int rhs = tile / per_rhs;
     const int tl = tile - rhs * per_rhs;
@@ -1192,8 +1193,8 @@ k_zconv_pipe(SArgs a) {
       }
     }
     __syncthreads();   // staging buffer consumed
-    if (GZ) zpipe_prefetch_ghat<T, L, C>(a, rhs, ky, cb, S);
-    else if (next < ntiles) zpipe_prefetch<T, L, C>(a, next, per_rhs, S);
+    if (GZ) zpipe_prefetch_ghat<T, L, C, L1X>(a, rhs, ky, cb, S);
+    else if (next < ntiles) zpipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
     dft<L1, -1, true>(r);
     if (GZ) {
       const cpx<T>* t2 = tw + jl;
@@ -1247,7 +1248,7 @@ k_zconv_pipe(SArgs a) {
       }
     }
     __syncthreads();   // forward exchange and the spectrum slice fully read
-    if (GZ && next < ntiles) zpipe_prefetch<T, L, C>(a, next, per_rhs, S);
+    if (GZ && next < ntiles) zpipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
       const int s = tid + it * NT;
@@ -1390,18 +1391,18 @@ cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
 // stream into shared memory with cp.async while the current one is
 // transformed.
 // ---------------------------------------------------------------------------
-template <int L, int C, class T>
+template <int L, int C, class T, int L1X = Split<L>::L1>
 struct YPipe {
-  using TL = Tile<L, C, T>;
+  using TL = Tile<L, C, T, L1X>;
   static constexpr int NT = TL::NT;
   static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
   static constexpr size_t S_ELEMS = size_t(L / 2) * C;
   static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>);
 };
 
-template <class T, int L, int C>
+template <class T, int L, int C, int L1X>
 __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
-  constexpr int NT = YPipe<L, C, T>::NT;
+  constexpr int NT = YPipe<L, C, T, L1X>::NT;
   constexpr int PER_ROW = C * int(sizeof(cpx<T>)) / 16;
   constexpr int EPC = 16 / int(sizeof(cpx<T>));
   const int rhs = tile / per_rhs;
@@ -1416,11 +1417,13 @@ __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, int per
   cp_async_commit();
 }
 
-template <class T, int L, int C>
-__global__ void __launch_bounds__(YPipe<L, C, T>::NT, (L > 1024 || YPipe<L, C, T>::NT >= 512) ? 1 : (YPipe<L, C, T>::NT >= 256 ? 2 : 512 / YPipe<L, C, T>::NT))
+template <class T, int L, int C, int L1X = Split<L>::L1>
+__global__ void __launch_bounds__(YPipe<L, C, T, L1X>::NT,
+                                  (L > 1024 || L1X >= 64 || YPipe<L, C, T, L1X>::NT >= 512)
+                                      ? 1 : (YPipe<L, C, T, L1X>::NT >= 256 ? 2 : 512 / YPipe<L, C, T, L1X>::NT))
 k_yfwd_pipe(SArgs a) {
-  using TL = Tile<L, C, T>;
-  using YP = YPipe<L, C, T>;
+  using TL = Tile<L, C, T, L1X>;
+  using YP = YPipe<L, C, T, L1X>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PK = TL::PK, PC = TL::PC;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1428,14 +1431,14 @@ k_yfwd_pipe(SArgs a) {
   cpx<T>* S = E + YP::E_ELEMS;
   cpx<T>* TW = S + YP::S_ELEMS;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
-  fill_tw2<L>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
+  fill_tw2<L, L2>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
   const int per_rhs = a.nouter * a.col_blocks;
   const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
   const int step = gridDim.x;
   const int tid = threadIdx.x;
   const int c = tid % C, jl = tid / C;
   int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
-  if (tile < ntiles) ypipe_prefetch<T, L, C>(a, tile, per_rhs, S);
+  if (tile < ntiles) ypipe_prefetch<T, L, C, L1X>(a, tile, per_rhs, S);
   while (tile < ntiles) {
     const int rhs = tile / per_rhs;
     const int tl = tile - rhs * per_rhs;
@@ -1453,7 +1456,7 @@ k_yfwd_pipe(SArgs a) {
       }
     }
     __syncthreads();
-    if (next < ntiles) ypipe_prefetch<T, L, C>(a, next, per_rhs, S);
+    if (next < ntiles) ypipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
     dft<L1, -1, true>(r);
     const cpx<T>* t2 = TW + jl;
 #pragma unroll
@@ -1488,17 +1491,17 @@ k_yfwd_pipe(SArgs a) {
 // two DFT stages reuses that buffer in place, and the next tile is requested
 // as soon as the second stage has read the exchange.
 // ---------------------------------------------------------------------------
-template <int L, int C>
+template <int L, int C, int L1X = Split<L>::L1>
 struct YInvPipe {
-  using TL = Tile<L, C, float>;
+  using TL = Tile<L, C, float, L1X>;
   static constexpr int NT = TL::NT;
   static constexpr int BUF = (C * L > TL::SMEM_ELEMS) ? C * L : TL::SMEM_ELEMS;
   static constexpr size_t SMEM_BYTES = size_t(BUF + L) * sizeof(cpx<float>);
 };
 
-template <int L, int C>
+template <int L, int C, int L1X>
 __device__ __forceinline__ void yinv_prefetch(const SArgs& a, int tile, int per_rhs, cpx<float>* B) {
-  constexpr int NT = YInvPipe<L, C>::NT;
+  constexpr int NT = YInvPipe<L, C, L1X>::NT;
   constexpr int PER_ROW = C * int(sizeof(cpx<float>)) / 16;
   const int rhs = tile / per_rhs;
   const int tl = tile - rhs * per_rhs;
@@ -1512,19 +1515,21 @@ __device__ __forceinline__ void yinv_prefetch(const SArgs& a, int tile, int per_
   cp_async_commit();
 }
 
-template <int L, int C>
-__global__ void __launch_bounds__(YInvPipe<L, C>::NT, (L > 1024 || YInvPipe<L, C>::NT >= 512) ? 1 : (YInvPipe<L, C>::NT >= 256 ? 2 : 512 / YInvPipe<L, C>::NT))
+template <int L, int C, int L1X = Split<L>::L1>
+__global__ void __launch_bounds__(YInvPipe<L, C, L1X>::NT,
+                                  (L > 1024 || L1X >= 64 || YInvPipe<L, C, L1X>::NT >= 512)
+                                      ? 1 : (YInvPipe<L, C, L1X>::NT >= 256 ? 2 : 512 / YInvPipe<L, C, L1X>::NT))
 k_yinv_pipe(SArgs a) {
   using T = float;
-  using TL = Tile<L, C, T>;
-  using YP = YInvPipe<L, C>;
+  using TL = Tile<L, C, T, L1X>;
+  using YP = YInvPipe<L, C, L1X>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PKI = TL::PKI, PCI = TL::PCI;
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* B = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* TW = B + YP::BUF;
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
-  fill_tw2<L>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
+  fill_tw2<L, L2>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
   const int per_rhs = a.nouter * a.col_blocks;
   const int ntiles = per_rhs * (a.nrhs > 1 ? a.nrhs : 1);
   const int step = gridDim.x;
@@ -1532,7 +1537,7 @@ k_yinv_pipe(SArgs a) {
   int c, ja;
   map_t<LAYOUT_STRIDED, C, L2>(tid, c, ja);
   int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
-  if (tile < ntiles) yinv_prefetch<L, C>(a, tile, per_rhs, B);
+  if (tile < ntiles) yinv_prefetch<L, C, L1X>(a, tile, per_rhs, B);
   while (tile < ntiles) {
     const int rhs = tile / per_rhs;
     const int tl = tile - rhs * per_rhs;
@@ -1566,7 +1571,7 @@ k_yinv_pipe(SArgs a) {
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) r[k1] = B[c * PCI + ja * PKI + k1];
     __syncthreads();   // exchange consumed: the buffer takes the next tile
-    if (next < ntiles) yinv_prefetch<L, C>(a, next, per_rhs, B);
+    if (next < ntiles) yinv_prefetch<L, C, L1X>(a, next, per_rhs, B);
     dft<L1, +1, false>(r);
     cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + outer * a.out_outer + (long long)cb * C;
 #pragma unroll
@@ -1579,13 +1584,10 @@ k_yinv_pipe(SArgs a) {
   cp_async_wait_all();
 }
 
-template <int L>
-cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  // 128-byte rows (8 columns: 1.42 ms, 16: 1.24 ms at n = 512); at L = 2048 the
-  // 16-column exchange buffer exceeds shared memory: 8 columns, one CTA per SM
-  constexpr int C = L > 1024 ? 8 : 16;
-  using YP = YInvPipe<L, C>;
-  auto kfn = k_yinv_pipe<L, C>;
+template <int L, int C, int L1X>
+cudaError_t launch_yinv_pipe_V(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  using YP = YInvPipe<L, C, L1X>;
+  auto kfn = k_yinv_pipe<L, C, L1X>;
   static int per_sm = 0;
   if (setup) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(YP::SMEM_BYTES));
@@ -1604,13 +1606,10 @@ cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
   return cudaGetLastError();
 }
 
-template <class T, int L>
-cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  // 128-byte rows (8 columns: 1.37 ms, 16: 1.30 ms at n = 512); 8 at L = 2048
-  // as for the inverse
-  constexpr int C = L > 1024 ? 8 : 16;
-  using YP = YPipe<L, C, T>;
-  auto kfn = k_yfwd_pipe<T, L, C>;
+template <class T, int L, int C, int L1X>
+cudaError_t launch_yfwd_pipe_V(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  using YP = YPipe<L, C, T, L1X>;
+  auto kfn = k_yfwd_pipe<T, L, C, L1X>;
   static int per_sm = 0;
   if (setup) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(YP::SMEM_BYTES));
@@ -1628,14 +1627,10 @@ cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count
   return cudaGetLastError();
 }
 
-template <class T, int L>
-cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
-  // 128-byte rows (measured: 64-byte rows are slower at L <= 1024); at L = 2048
-  // a 16-column tile's exchange buffer alone exceeds shared memory, so 8 columns
-  // (256 threads, one CTA per SM with up to 255 registers a thread)
-  constexpr int C = (L > 1024 && sizeof(T) == 4) ? 8 : 128 / int(sizeof(cpx<T>));
-  using ZP = ZPipe<L, C, T>;
-  auto kfn = k_zconv_pipe<T, L, C>;
+template <class T, int L, int C, int L1X>
+cudaError_t launch_zconv_pipe_V(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  using ZP = ZPipe<L, C, T, L1X>;
+  auto kfn = k_zconv_pipe<T, L, C, L1X>;
   static int per_sm = 0;   // resident CTAs per SM, measured once at set-up
   if (setup) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ZP::SMEM_BYTES));
@@ -1650,6 +1645,59 @@ cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
   const unsigned gx = unsigned(std::max(1LL, std::min(ntiles, (long long)std::max(1, sm_count) * resident)));
   kfn<<<gx, ZP::NT, ZP::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
+}
+
+// Dispatch on the launch variant (has_pipe_variants): the set-up call
+// prepares every variant, a launch runs the one a.variant names.
+template <class T, int L, int C0, template <class, int, int, int> class Launch>
+cudaError_t dispatch_pipe_variant(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int L1 = Split<L>::L1;
+  if constexpr (sizeof(T) == 4 && has_pipe_variants(L)) {
+    if (setup) {
+      cudaError_t e = Launch<T, L, 16, L1>::run(a, s, true, sm_count);
+      if (e == cudaSuccess) e = Launch<T, L, 8, L1>::run(a, s, true, sm_count);
+      if (e == cudaSuccess) e = Launch<T, L, 16, 2 * L1>::run(a, s, true, sm_count);
+      return e;
+    }
+    if (a.variant == 1) return Launch<T, L, 8, L1>::run(a, s, false, sm_count);
+    if (a.variant == 2) return Launch<T, L, 16, 2 * L1>::run(a, s, false, sm_count);
+    return Launch<T, L, 16, L1>::run(a, s, false, sm_count);
+  } else {
+    return Launch<T, L, C0, L1>::run(a, s, setup, sm_count);
+  }
+}
+
+template <class T, int L, int C, int L1X>
+struct ZconvPipeLaunch {
+  static cudaError_t run(SArgs a, cudaStream_t s, bool setup, int sm) { return launch_zconv_pipe_V<T, L, C, L1X>(a, s, setup, sm); }
+};
+template <class T, int L, int C, int L1X>
+struct YfwdPipeLaunch {
+  static cudaError_t run(SArgs a, cudaStream_t s, bool setup, int sm) { return launch_yfwd_pipe_V<T, L, C, L1X>(a, s, setup, sm); }
+};
+template <class T, int L, int C, int L1X>
+struct YinvPipeLaunch {
+  static cudaError_t run(SArgs a, cudaStream_t s, bool setup, int sm) { return launch_yinv_pipe_V<L, C, L1X>(a, s, setup, sm); }
+};
+
+// Default tile widths: 128-byte rows (Z: 64-byte rows measured slower at
+// L <= 1024; Y: 8 columns 1.37 / 1.42 ms against 16 columns 1.30 / 1.24 ms at
+// n = 512); at L = 2048 a 16-column tile's exchange buffer exceeds shared
+// memory, so 8 columns (256 threads, one CTA per SM, up to 255 registers).
+template <class T, int L>
+cudaError_t launch_zconv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = (L > 1024 && sizeof(T) == 4) ? 8 : 128 / int(sizeof(cpx<T>));
+  return dispatch_pipe_variant<T, L, C, ZconvPipeLaunch>(a, s, setup, sm_count);
+}
+template <class T, int L>
+cudaError_t launch_yfwd_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = L > 1024 ? 8 : 16;
+  return dispatch_pipe_variant<T, L, C, YfwdPipeLaunch>(a, s, setup, sm_count);
+}
+template <int L>
+cudaError_t launch_yinv_pipe_L(SArgs a, cudaStream_t s, bool setup, int sm_count) {
+  constexpr int C = L > 1024 ? 8 : 16;
+  return dispatch_pipe_variant<float, L, C, YinvPipeLaunch>(a, s, setup, sm_count);
 }
 
 // Z-pass kernel choice for L >= 64: the shared-memory radix-8 kernel for

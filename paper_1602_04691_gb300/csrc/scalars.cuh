@@ -125,9 +125,11 @@ __device__ __forceinline__ void finalize(Scalars* sc, const double2* partials, i
       sc->target2 = sc->tol * sc->tol * rn2;
       sc->iter = 0;
       sc->beta = make_double2(0.0, 0.0);
-      // a residual that already meets the target needs no iteration
+      // a residual that already meets the target needs no iteration; a nonzero
+      // residual with r^T r = 0 cannot start COCG (rho is the divisor of beta)
       sc->done = (!isfinite(rn2) || !isfinite2(rr)) ? DONE_NONFINITE
-               : ((rn2 == 0.0 || rn2 <= sc->target2) ? DONE_CONVERGED : DONE_RUNNING);
+               : ((rn2 == 0.0 || rn2 <= sc->target2) ? DONE_CONVERGED
+               : ((rr.x == 0.0 && rr.y == 0.0) ? DONE_BREAKDOWN : DONE_RUNNING));
     } else {
       const int it = sc->iter + 1;
       sc->iter = it;
@@ -143,6 +145,9 @@ __device__ __forceinline__ void finalize(Scalars* sc, const double2* partials, i
         sc->done = DONE_MAXIT;
       }
       sc->beta = cdiv(rr, sc->rho);
+      // beta = rho' / rho: a vanished rho (or a rho' at rounding level over it)
+      // is a breakdown, not a NaN to carry into p
+      if (sc->done == DONE_RUNNING && !isfinite2(sc->beta)) sc->done = DONE_BREAKDOWN;
       sc->rho = rr;
     }
     sc->count = 0;

@@ -16,11 +16,12 @@ class FakePlan:
 
     def autotune_now(self, nrhs, reps):
         self.tuned += 1
-        return {"yfwd": 1, "zconv": 0, "yinv": 1, "ctas_per_sm": 1, "vec_ctas_per_sm": 4}, 1.25 * nrhs
+        return {"yfwd": 1, "zconv": 0, "yinv": 1, "ctas_per_sm": 1, "vec_ctas_per_sm": 4,
+                "yfwd_variant": 0, "zconv_variant": 2, "yinv_variant": 1}, 1.25 * nrhs
 
 
-def test_key_names_gpu_n_batch_and_arithmetic():
-    assert AT.cache_key("GPU X", 512, 64) == "GPU X|n=512|nrhs=64|arith=fp32"
+def test_key_names_gpu_n_batch_arithmetic_and_field_set():
+    assert AT.cache_key("GPU X", 512, 64) == "GPU X|n=512|nrhs=64|arith=fp32|sched=2"
 
 
 def test_miss_tunes_and_stores_then_hit_applies(tmp_path):
@@ -29,7 +30,8 @@ def test_miss_tunes_and_stores_then_hit_applies(tmp_path):
     r1 = AT.tune(p, 64, "GPU X", path=path)
     assert not r1["cached"] and p.tuned == 1 and r1["ms"] == 80.0
     data = json.load(open(path))
-    assert data["GPU X|n=128|nrhs=64|arith=fp32"]["schedule"]["yfwd"] == 1
+    entry = data["GPU X|n=128|nrhs=64|arith=fp32|sched=2"]["schedule"]
+    assert entry["yfwd"] == 1 and entry["zconv_variant"] == 2 and entry["yinv_variant"] == 1
     q = FakePlan(128)
     r2 = AT.tune(q, 64, "GPU X", path=path)
     assert r2["cached"] and q.tuned == 0 and q.applied == [r1["schedule"]]
@@ -56,6 +58,16 @@ def test_corrupt_or_invalid_cache_is_ignored(tmp_path):
     path.write_text(json.dumps({AT.cache_key("G", 16, 2): {"schedule": {"yfwd": "x"}}}))
     q = FakePlan(16)
     assert not AT.tune(q, 2, "G", path=str(path))["cached"] and q.tuned == 1
+
+
+def test_entry_without_launch_variants_is_tuned_again(tmp_path):
+    """An entry of the older field set (no launch variants) is neither applied nor trusted."""
+    path = tmp_path / "old.json"
+    old = {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8}
+    path.write_text(json.dumps({"G|n=16|nrhs=2|arith=fp32": {"schedule": old, "ms": 1.0},
+                                AT.cache_key("G", 16, 2): {"schedule": old, "ms": 1.0}}))
+    q = FakePlan(16)
+    assert not AT.tune(q, 2, "G", path=str(path))["cached"] and q.tuned == 1 and q.applied == []
 
 
 def test_env_variable_names_default_path(tmp_path, monkeypatch):

@@ -34,11 +34,16 @@ def test_byte_model_at_n512():
 def test_kernel_names_follow_length_and_schedule():
     pers = {"yfwd": 0, "zconv": 0, "yinv": 0}
     tiles = {"yfwd": 1, "zconv": 1, "yinv": 1}
-    assert bench.fp32_kernel_name("zconv", 1024, pers) == "k_zconv_pipe<float, 1024, 16>"
+    assert bench.fp32_kernel_name("zconv", 1024, pers) == "k_zconv_pipe<float, 1024, 16, 32>"
+    assert bench.fp32_kernel_name("zconv", 1024, dict(pers, zconv_variant=1)) == "k_zconv_pipe<float, 1024, 8, 32>"
+    assert bench.fp32_kernel_name("zconv", 1024, dict(pers, zconv_variant=2)) == "k_zconv_pipe<float, 1024, 16, 64>"
+    assert bench.fp32_kernel_name("yfwd", 512, dict(pers, yfwd_variant=2)) == "k_yfwd_pipe<float, 512, 16, 64>"
+    assert bench.fp32_kernel_name("yinv", 256, dict(pers, yinv_variant=1)) == "k_yinv_pipe<256, 8, 16>"
+    assert bench.fp32_kernel_name("zconv", 128, dict(pers, zconv_variant=2)) == "k_zconv_pipe<float, 128, 16, 16>"
     assert bench.fp32_kernel_name("zconv", 1024, tiles) == "k_strided<float, 1024>(ZCONV)"
-    assert bench.fp32_kernel_name("zconv", 2048, pers) == "k_zconv_pipe<float, 2048, 8>"
+    assert bench.fp32_kernel_name("zconv", 2048, pers) == "k_zconv_pipe<float, 2048, 8, 64>"
     assert bench.fp32_kernel_name("zconv", 2048, tiles) == "k_zconv_smem<float, 2048, 8>"
-    assert bench.fp32_kernel_name("yinv", 2048, pers) == "k_yinv_pipe<2048, 8>"
+    assert bench.fp32_kernel_name("yinv", 2048, pers) == "k_yinv_pipe<2048, 8, 64>"
     assert bench.fp32_kernel_name("yfwd", 2048, tiles) == "k_strided_smem<float, 2048, 4>(FWD)"
     # the X passes have one kernel per length whatever the schedule
     assert bench.fp32_kernel_name("xfwd", 2048, pers) == bench.fp32_kernel_name("xfwd", 2048, tiles)

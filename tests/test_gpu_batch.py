@@ -180,13 +180,14 @@ def test_every_schedule_matches_oracle_and_autotune_caches(tmp_path):
     ref = O.red_matvec_direct(x, n, ks[0], h, N)
     plan = make_plan(n, ks, h, N)
     default = plan.schedule()
-    assert default == {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8}
+    assert default == {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8,
+                       "yfwd_variant": 0, "zconv_variant": 0, "yinv_variant": 0}
     dirs = [(0.0, 0.0, 1.0), (0.6, 0.8, 0.0)]
     for y in (0, 1):
         for z in (0, 1):
             for yi in (0, 1):
                 for cap, vec in ((0, 8), (1, 4), (2, 16)):
-                    plan.set_schedule({"yfwd": y, "zconv": z, "yinv": yi, "ctas_per_sm": cap, "vec_ctas_per_sm": vec})
+                    plan.set_schedule(dict(default, yfwd=y, zconv=z, yinv=yi, ctas_per_sm=cap, vec_ctas_per_sm=vec))
                     y32 = plan.matvec(to_dev(x), form="A", precision="fp32").cpu().numpy()
                     assert rel(y32, ref) < 1e-5, (y, z, yi, cap)
                     _, infos = plan.solve_batch(dirs, tol=1e-6, precision="mixed")
@@ -202,6 +203,39 @@ def test_every_schedule_matches_oracle_and_autotune_caches(tmp_path):
     assert all(i["relres"] <= 1e-6 for i in infos)
 
 
+@pytest.mark.parametrize("n", [100, 200, 260])
+def test_every_launch_variant_matches_oracle(n):
+    """The tile-width and radix-split variants of the persistent FP32 Y-forward,
+    Z and Y-inverse kernels at L = 256, 512 and 1024 (n = 100, 200, 260): each
+    alone, and all at once, give the FP32 operator within 1e-5 of the oracle's
+    direct sums on rows of every tile class; a mixed solve meets tol with
+    them."""
+    k = 3.0
+    h, N = inputs.random_h_N(n, 90 + n)
+    x = inputs.random_complex(n ** 3, 91 + n).astype(np.complex64)
+    plan = make_plan(n, k, h, N)
+    assert plan.L in (256, 512, 1024)
+    default = plan.schedule()
+    rng = np.random.default_rng(n)
+    rows = np.unique(np.concatenate([[0, n - 1, n * n - 1, n ** 3 - 1, n ** 3 - n, (n // 2) * (n * n + n + 1)],
+                                     rng.choice(n ** 3, 24, replace=False)]))
+    S = O.sqrt_hN(h, N)
+    G = O.kernel_octant(n, k)
+    ref = x[rows] + S[rows] * (O.C_S_SPHERE / n ** 3) * O.offdiag_sum_rows_octant(
+        S * x.astype(np.complex128), rows, n, k, octant=G)
+    xd = to_dev(x)
+    schedules = [dict(default, **{f: v}) for f in ("yfwd_variant", "zconv_variant", "yinv_variant") for v in (1, 2)]
+    schedules += [dict(default, yfwd_variant=v, zconv_variant=v, yinv_variant=v) for v in (1, 2)]
+    for sch in schedules:
+        plan.set_schedule(sch)
+        y = plan.matvec32(xd, form="B").cpu().numpy()
+        assert rel(y[rows], ref) < 1e-5, sch
+    _, info = plan.solve(tol=1e-6, precision="mixed")
+    assert info["status"] == 0 and info["relres"] <= 1e-6
+    plan.set_schedule(default)
+    plan.close()
+
+
 def test_set_schedule_rejects_bad_fields():
     from paper_1602_04691_gb300 import OriError
     n = 8
@@ -210,8 +244,9 @@ def test_set_schedule_rejects_bad_fields():
     for bad in ({"yfwd": 2, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8},
                 {"yfwd": 0, "zconv": 0, "yinv": 3, "ctas_per_sm": 0, "vec_ctas_per_sm": 8},
                 {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": -1, "vec_ctas_per_sm": 8},
-                {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 17}):
-        with pytest.raises(OriError):
+                {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 17},
+                {"yfwd": 0, "zconv": 0, "yinv": 0, "ctas_per_sm": 0, "vec_ctas_per_sm": 8, "zconv_variant": 1}):
+        with pytest.raises(OriError):                # n = 8 pads to L = 16: variant 0 only
             plan.set_schedule(bad)
     assert plan.schedule()["vec_ctas_per_sm"] == 8
 

@@ -91,9 +91,10 @@ def test_cocg_breakdown_is_reported_with_finite_iterate(precision):
     """COCG's bilinear form r^T r is no norm: a nonzero residual can have
     r^T r = 0.  With h = 1 and N = 1 (S = 1 exactly) and b = e_0 + i e_1, the
     first residual S b has r^T r = 1 + i^2 = 0 exactly (also after the mixed
-    solver scales it to unit norm in FP32); the first step then has alpha = 0
-    and leaves r^T r = 0 with r != 0: the breakdown of COCG.  The solve reports
-    ORI_ERR_BREAKDOWN and returns a finite iterate; the plan keeps working."""
+    solver scales it to unit norm in FP32), and rho = r^T r is the divisor of
+    beta: the breakdown of COCG, found before the first step.  The solve
+    reports ORI_ERR_BREAKDOWN and returns a finite iterate; the plan keeps
+    working."""
     from paper_1602_04691_gb300 import Plan
     from paper_1602_04691_gb300._lib import ORI_ERR_BREAKDOWN
     n = 6

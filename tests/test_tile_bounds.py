@@ -1,7 +1,9 @@
 """Shared-memory bounds of the pipelined FP32 FFT kernels, checked on the CPU.
 
-For every padded length L the launchers instantiate (64 ... 2048) and the
-tile width each launcher picks, every shared-memory index the kernels form
+For every padded length L the launchers instantiate (64 ... 2048), the tile
+width each launcher picks and, at L = 256 ... 1024, each launch variant of the
+Y and Z kernels (8-column tiles; a split with a doubled first radix), every
+shared-memory index the kernels form
 (staged inputs, the exchange between the two DFT stages, the spectrum slice,
 the twiddle table) is enumerated over all threads and loop indices and must
 stay inside its buffer, and each CTA's shared memory must fit in 227 KB.
@@ -30,8 +32,8 @@ def split(L):
     return L1, L // L1
 
 
-def tile(L, C):
-    L1, L2 = split(L)
+def tile(L, C, L1=None):
+    L1, L2 = split(L) if L1 is None else (L1, L // L1)
     PK, PKI = L2 + 1, L1 + 1
     PC, PCI = (L1 * PK) | 1, (L2 * PKI) | 1
     return dict(L1=L1, L2=L2, NT=C * L2, PK=PK, PC=PC, PKI=PKI, PCI=PCI, SE=max(C * PC, C * PCI))
@@ -39,6 +41,16 @@ def tile(L, C):
 
 def yz_cols(L):                  # Y and Z launchers (FP32)
     return 8 if L > 1024 else 16
+
+
+def yz_variants(L):              # (C, L1) of each launch variant (has_pipe_variants)
+    L1 = split(L)[0]
+    if 256 <= L <= 1024:
+        return [(16, L1), (8, L1), (16, 2 * L1)]
+    return [(yz_cols(L), L1)]
+
+
+YZ = [(L, C, L1) for L in LS for C, L1 in yz_variants(L)]
 
 
 def x_cols(L):                   # xpipe_cols<L>()
@@ -50,10 +62,10 @@ def grid(*ranges):
     return np.meshgrid(*[np.arange(r) for r in ranges], indexing="ij")
 
 
-@pytest.mark.parametrize("L", LS)
-def test_zconv_pipe_indices(L):
-    C = yz_cols(L)
-    t = tile(L, C)
+@pytest.mark.parametrize("L,C,L1v", YZ)
+def test_zconv_pipe_indices(L, C, L1v):
+    t = tile(L, C, L1v)
+    assert t["L1"] >= t["L2"] and 16 % C == 0                       # NI >= 1; C divides the spectrum group
     L1, L2, NT, PK, PC, PKI, PCI = (t[k] for k in ("L1", "L2", "NT", "PK", "PC", "PKI", "PCI"))
     E, S, TW = t["SE"], (L // 2 + 1) * C, L
     assert (E + S + TW) * CB <= SMEM_MAX
@@ -81,10 +93,9 @@ def test_zconv_pipe_indices(L):
     assert (c * PCI + jl * PKI + k1).max() < E                       # inverse exchange load
 
 
-@pytest.mark.parametrize("L", LS)
-def test_yfwd_pipe_indices(L):
-    C = yz_cols(L)
-    t = tile(L, C)
+@pytest.mark.parametrize("L,C,L1v", YZ)
+def test_yfwd_pipe_indices(L, C, L1v):
+    t = tile(L, C, L1v)
     L1, L2, NT, PK, PC = (t[k] for k in ("L1", "L2", "NT", "PK", "PC"))
     E, S = t["SE"], (L // 2) * C
     assert (E + S + L) * CB <= SMEM_MAX
@@ -98,10 +109,9 @@ def test_yfwd_pipe_indices(L):
     assert ((s % C) * PC + (s // C) * PK + j).max() < E
 
 
-@pytest.mark.parametrize("L", LS)
-def test_yinv_pipe_indices(L):
-    C = yz_cols(L)
-    t = tile(L, C)
+@pytest.mark.parametrize("L,C,L1v", YZ)
+def test_yinv_pipe_indices(L, C, L1v):
+    t = tile(L, C, L1v)
     L1, L2, NT, PKI, PCI = (t[k] for k in ("L1", "L2", "NT", "PKI", "PCI"))
     BUF = max(C * L, t["SE"])
     assert (BUF + L) * CB <= SMEM_MAX
@@ -158,7 +168,11 @@ def _read(name):
 @pytest.mark.parametrize("name,lines", [
     ("common.cuh", ["static constexpr int L1 = 1 << ((lg + 1) / 2);",
                     "static constexpr int L2 = L / L1;"]),
-    ("passes.cuh", ["static constexpr int NT = C * L2;",
+    ("passes.cuh", ["constexpr bool has_pipe_variants(int L) { return L >= 256 && L <= 1024; }",
+                    "template <int L, int C, class T, int L1X = Split<L>::L1>",
+                    "static constexpr int L1 = L1X;",
+                    "static constexpr int L2 = L / L1X;",
+                    "static constexpr int NT = C * L2;",
                     "static constexpr int PK = L2 + 1;",
                     "static constexpr int PC = (L1 * PK) | 1;",
                     "static constexpr int PKI = L1 + 1;",
@@ -174,6 +188,12 @@ def _read(name):
                          "constexpr int C = L > 1024 ? 8 : 16;",
                          "constexpr int C = (L > 1024 && sizeof(T) == 4) ? 8 : 128 / int(sizeof(cpx<T>));",
                          "constexpr int C = xpipe_cols<L>();",
+                         "cudaError_t e = Launch<T, L, 16, L1>::run(a, s, true, sm_count);",
+                         "if (e == cudaSuccess) e = Launch<T, L, 8, L1>::run(a, s, true, sm_count);",
+                         "if (e == cudaSuccess) e = Launch<T, L, 16, 2 * L1>::run(a, s, true, sm_count);",
+                         "if (a.variant == 1) return Launch<T, L, 8, L1>::run(a, s, false, sm_count);",
+                         "if (a.variant == 2) return Launch<T, L, 16, 2 * L1>::run(a, s, false, sm_count);",
+                         "return Launch<T, L, 16, L1>::run(a, s, false, sm_count);",
                          "if (j < a.n_in) r[j1] = S[j * C + c];",
                          "E[c * PC + k1 * PK + jl] = r[k1];",
                          "b[it][j] = E[c2 * PC + k1 * PK + j];",
