@@ -21,6 +21,33 @@ template <class T>
 __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <class T>
 __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+// FP32 complex sums as one packed two-lane instruction (add/sub.rn.f32x2,
+// sm_100 and later): the same rounding per lane as two scalar operations,
+// half the issue slots.  The FFT passes are bound by instruction issue, and
+// their butterflies are mostly complex additions.
+__device__ __forceinline__ unsigned long long pack2(cpx<float> a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ cpx<float> unpack2(unsigned long long v) {
+  cpx<float> r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+template <>
+__device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+template <>
+__device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+  return unpack2(r);
+}
+
 template <class T>
 __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
   return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
