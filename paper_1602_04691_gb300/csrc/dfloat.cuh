@@ -82,10 +82,63 @@ __device__ __forceinline__ cpx<dfl> cmul(cpx<dfl> a, cpx<dfl> b) {
   return {df_dot2(a.x, b.x, a.y, b.y, -1.0f), df_dot2(a.x, b.y, a.y, b.x, 1.0f)};
 }
 
-// A value as it is stored between FFT stages: renormalised for paired FP32,
-// unchanged for the other arithmetics.
+// Complex sums and the renormalisation in packed two-lane FP32 instructions
+// (f32x2, sm_100 and later): the real and imaginary parts go through the
+// same error-free transformation side by side, each lane rounded as the
+// scalar operation would be, in half the issue slots.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// a + b (SUB = false) or a - b (SUB = true): two_sum of the high parts
+// (Knuth; with c = -b for the difference: e = (a - (s - bb)) - (b + bb)), the
+// low parts added, no renormalisation.
+template <bool SUB>
+__device__ __forceinline__ cpx<dfl> df_cadd(cpx<dfl> a, cpx<dfl> b) {
+  const unsigned long long ah = pk2(a.x.hi, a.y.hi), bh = pk2(b.x.hi, b.y.hi);
+  const unsigned long long s = SUB ? fsub2(ah, bh) : fadd2(ah, bh);
+  const unsigned long long bb = fsub2(s, ah);
+  const unsigned long long e = SUB ? fsub2(fsub2(ah, fsub2(s, bb)), fadd2(bh, bb))
+                                   : fadd2(fsub2(ah, fsub2(s, bb)), fsub2(bh, bb));
+  const unsigned long long al = pk2(a.x.lo, a.y.lo), bl = pk2(b.x.lo, b.y.lo);
+  const unsigned long long lo = fadd2(e, SUB ? fsub2(al, bl) : fadd2(al, bl));
+  cpx<dfl> r;
+  upk2(s, r.x.hi, r.y.hi);
+  upk2(lo, r.x.lo, r.y.lo);
+  return r;
+}
+template <>
+__device__ __forceinline__ cpx<dfl> operator+(cpx<dfl> a, cpx<dfl> b) { return df_cadd<false>(a, b); }
+template <>
+__device__ __forceinline__ cpx<dfl> operator-(cpx<dfl> a, cpx<dfl> b) { return df_cadd<true>(a, b); }
+
+// A value as it is stored between FFT stages: renormalised for paired FP32
+// (fast_two_sum on both lanes), unchanged for the other arithmetics.
 template <class T> __device__ __forceinline__ cpx<T> settle(cpx<T> v) { return v; }
-template <> __device__ __forceinline__ cpx<dfl> settle<dfl>(cpx<dfl> v) { return {settle(v.x), settle(v.y)}; }
+template <> __device__ __forceinline__ cpx<dfl> settle<dfl>(cpx<dfl> v) {
+  const unsigned long long h = pk2(v.x.hi, v.y.hi), l = pk2(v.x.lo, v.y.lo);
+  const unsigned long long s = fadd2(h, l);
+  const unsigned long long e = fsub2(l, fsub2(s, h));
+  cpx<dfl> r;
+  upk2(s, r.x.hi, r.y.hi);
+  upk2(e, r.x.lo, r.y.lo);
+  return r;
+}
 
 // Split a double into hi + lo (hi = nearest float, lo = nearest float of the rest).
 __device__ __forceinline__ dfl df_from_double(double v) {
