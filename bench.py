@@ -54,6 +54,9 @@ def parse():
                     help="lean plan (mixed solves only; needed for the largest grids, e.g. --n 1000)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch schedule (no autotuning before the timed region)")
+    ap.add_argument("--schedule", default=None,
+                    help="JSON object of ori_schedule fields to run with instead of autotuning (for example the "
+                         "schedule a bench line reports, to profile the same kernels)")
     ap.add_argument("--experiment", action="store_true",
                     help="run the Section 4 experiment scaled to one GPU (RED n=20, IE n=40, ORI n=480) "
                          "and print its JSON line instead of the benchmark")
@@ -110,10 +113,11 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel: str, n: int):
-    """DRAM bytes per launch from a committed ncu summary, only if the kernel
-    sources are unchanged since it was taken and it was taken on this grid size
-    (other sizes may pad to another L and run other kernels)."""
+def traffic_from_profiles(kind: str, n: int, variant: int = 0):
+    """DRAM bytes per launch of pass `kind` (launch variant `variant`) from the
+    committed ncu summary, only if the kernel sources are unchanged since it
+    was taken and its figure is for this grid size (other sizes may pad to
+    another L and run other kernels)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -122,7 +126,7 @@ def traffic_from_profiles(kernel: str, n: int):
         return None
     if d.get("source_hash") != source_hash():
         return None
-    ent = d.get("kernels", {}).get(kernel)
+    ent = d.get("kernels", {}).get(kind, {}).get(str(variant))
     if not ent or ent.get("n") != n:
         return None
     return ent["dram_bytes_per_launch"]
@@ -439,7 +443,10 @@ def ours_arm(args, world, rank, local):
         h_dev = N_dev = None
         torch.cuda.empty_cache()
     tune_path = os.path.join(tempfile.gettempdir(), f"ori_autotune_bench_{os.getpid()}.json")
-    if args.no_autotune:
+    if args.schedule:
+        plan.set_schedule(dict(plan.schedule(), **json.loads(args.schedule)))
+        tuned = {"schedule": plan.schedule(), "ms": None}
+    elif args.no_autotune:
         tuned = {"schedule": plan.schedule(), "ms": None}
     else:
         tuned = plan.autotune(nrhs=1, path=tune_path)
@@ -489,7 +496,8 @@ def ours_arm(args, world, rank, local):
     roof = {"bound": "hbm", "kernel": fp32_kernel_name(dom, L, plan.schedule()), "achieved": achieved,
             "peak": pk["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-            "traffic": traffic_from_profiles(dom, n), "alg_bytes_per_launch": ab,
+            "traffic": traffic_from_profiles(dom, n, plan.schedule().get(dom + "_variant", 0)),
+            "alg_bytes_per_launch": ab,
             "ms_per_launch": dom_ms, "peak_source": pk["source"] + " (burst copy)"}
     passes = {}
     for kk in fp32_kinds:

@@ -189,7 +189,14 @@ constexpr int bitrev(int i, int R) {
 // Radix-2 decimation in frequency, then the bit-reversal permutation (free:
 // all indices are compile-time constants).  HALF: a[j] = 0 for j >= R/2 on
 // input (the zero padding of Section 3), which removes the first stage's adds.
-template <int R, int SIGN, bool HALF, class T>
+// SCALAR: complex sums part by part (T's own addition) instead of the
+// complex operator, which for some T is a packed two-lane instruction.
+template <class T>
+__device__ __forceinline__ cpx<T> add_parts(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T>
+__device__ __forceinline__ cpx<T> sub_parts(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
+
+template <int R, int SIGN, bool HALF, class T, bool SCALAR = false>
 __device__ __forceinline__ void dft(cpx<T> (&a)[R]) {
   if constexpr (R > 1) {
 #pragma unroll
@@ -204,8 +211,8 @@ __device__ __forceinline__ void dft(cpx<T> (&a)[R]) {
             a[b + j + s] = tw64_mul<SIGN>(u, idx);
           } else {
             const cpx<T> v = a[b + j + s];
-            a[b + j] = u + v;
-            a[b + j + s] = tw64_mul<SIGN>(u - v, idx);
+            a[b + j] = SCALAR ? add_parts(u, v) : u + v;
+            a[b + j + s] = tw64_mul<SIGN>(SCALAR ? sub_parts(u, v) : u - v, idx);
           }
         }
       }

@@ -1276,7 +1276,9 @@ k_zconv_pipe(SArgs a) {
 // Z convolution for the paired-FP32 residual: persistent CTAs, a tile of C
 // columns (C * 16 B = 128 B rows) held in shared memory and transformed in
 // place by looped radix-8 stages (dfft.cuh); the next tile's input rows
-// stream into a staging buffer with cp.async meanwhile.
+// stream into a staging buffer with cp.async meanwhile.  Its butterflies add
+// part by part: this pass is bound by instruction issue, and the packed
+// complex sum's register moves cost it more than they save (measured).
 // ---------------------------------------------------------------------------
 template <int L, int C, class T>
 struct ZSmem {
@@ -1292,6 +1294,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
   using ZS = ZSmem<L, C, T>;
   constexpr int NT = ZS::NT;
   constexpr int S8 = L / 8;          // span of the first (and last) radix-8 stage
+  constexpr bool SC = std::is_same<T, dfl>::value;   // paired FP32: sums part by part
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* S = X + ZS::X_ELEMS;
@@ -1324,7 +1327,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
         v[t] = czero<T>();
         if (t < 4 && j + t * S8 < a.n_in) v[t] = S[(j + t * S8) * C + c];
       }
-      dft<8, -1, true>(v);
+      dft<8, -1, true, T, SC>(v);
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
@@ -1332,7 +1335,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
     }
     __syncthreads();
     if (next < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, next, per_rhs, S);
-    dif_rest<L, C>(X, TW, tid, NT);
+    dif_rest<L, C, T, SC>(X, TW, tid, NT);
     // spectrum: position p holds frequency kz = digit_rev(p)
     const int my = mirror_index(ky, L);
     for (int e = tid; e < C * L; e += NT) {
@@ -1343,7 +1346,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
       X[si] = settle(cmul(X[si], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx)));
     }
     __syncthreads();
-    dit_head<L, C>(X, TW, tid, NT);
+    dit_head<L, C, T, SC>(X, TW, tid, NT);
     // last inverse stage (M = L), keep rows z < n_out
     cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + (long long)ky * a.out_outer + (long long)cb * C;
     for (int g = tid; g < C * S8; g += NT) {
@@ -1353,7 +1356,7 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
       for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
-      dft<8, +1, false>(v);
+      dft<8, +1, false, T, SC>(v);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int z = j + t * S8;

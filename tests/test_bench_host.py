@@ -56,7 +56,8 @@ def _write_traffic(tmp_path, monkeypatch, source_hash, n):
     prof.mkdir()
     (prof / "traffic.json").write_text(json.dumps({
         "source_hash": source_hash,
-        "kernels": {"zconv": {"n": n, "dram_bytes_per_launch": 1.0e10}}}))
+        "kernels": {"zconv": {"0": {"n": n, "dram_bytes_per_launch": 1.0e10},
+                              "2": {"n": n, "dram_bytes_per_launch": 1.1e10}}}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
 
 
@@ -65,6 +66,8 @@ def test_traffic_reported_only_for_current_sources_and_same_grid(tmp_path, monke
     monkeypatch.setattr(bench, "source_hash", lambda: current)
     _write_traffic(tmp_path, monkeypatch, current, 512)
     assert bench.traffic_from_profiles("zconv", 512) == 1.0e10
+    assert bench.traffic_from_profiles("zconv", 512, 2) == 1.1e10  # another launch variant
+    assert bench.traffic_from_profiles("zconv", 512, 1) is None    # not captured
     assert bench.traffic_from_profiles("zconv", 1000) is None     # another L, other kernels
     assert bench.traffic_from_profiles("xfwd", 512) is None       # not captured
 
@@ -89,9 +92,9 @@ def test_committed_traffic_agrees_with_the_byte_model():
     if d["source_hash"] != bench.source_hash():
         pytest.skip("kernel sources changed since the committed capture (bench reports traffic null)")
     for kind in ("xfwd", "yfwd", "zconv", "yinv", "xinv", "update"):
-        ent = d["kernels"][kind]
-        ratio = ent["dram_bytes_per_launch"] / bench.alg_bytes(kind, ent["n"], 2 * ent["n"], 8)
-        assert 0.9 < ratio < 1.3, (kind, ratio)
+        for variant, ent in d["kernels"][kind].items():
+            ratio = ent["dram_bytes_per_launch"] / bench.alg_bytes(kind, ent["n"], 2 * ent["n"], 8)
+            assert 0.9 < ratio < 1.3, (kind, variant, ratio)
 
 
 def test_committed_bench_line_keeps_the_output_contract():
