@@ -148,19 +148,19 @@ __global__ void k_rhs(const cpx<double>* __restrict__ rhs, const cpx<double>* __
     __syncthreads();
   }
   double acc = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3;
-       i += (long long)gridDim.x * blockDim.x) {
-    cpx<double> u;
-    if (rhs != nullptr) {
-      u = rhs[i];
-    } else {
-      const int ix = int(i % n), iy = int((i / n) % n), iz = int(i / ((long long)n * n));
-      u = cmul(cmul(e[ix], e[n + iy]), e[2 * n + iz]);
+  // blocks take whole lines (iz, iy): one index division per line, and the
+  // line's phase e_y e_z once per thread; threads run along x
+  for (int line = blockIdx.x; line < n * n; line += gridDim.x) {
+    const int iz = line / n, iy = line - iz * n;
+    const cpx<double> pyz = rhs == nullptr ? cmul(e[n + iy], e[2 * n + iz]) : cpx<double>{0.0, 0.0};
+    for (int ix = threadIdx.x; ix < n; ix += blockDim.x) {
+      const long long i = (long long)line * n + ix;
+      const cpx<double> u = rhs != nullptr ? rhs[i] : cmul(e[ix], pyz);
+      if (u0 != nullptr) u0[i] = u;
+      const cpx<double> bv = cmul(S[i], u);
+      b[i] = bv;
+      acc += bv.x * bv.x + bv.y * bv.y;
     }
-    if (u0 != nullptr) u0[i] = u;
-    const cpx<double> bv = cmul(S[i], u);
-    b[i] = bv;
-    acc += bv.x * bv.x + bv.y * bv.y;
   }
   block_partial(make_double2(acc, 0.0), red, partials);
   if (last_block_arrives(sc, s_last)) finalize(sc, partials, gridDim.x, FIN_SUM, red);
@@ -435,7 +435,9 @@ __global__ void k_field_partial(const cpx<double>* __restrict__ Q, const double*
     const double px = pts[3 * pi], py = pts[3 * pi + 1], pz = pts[3 * pi + 2];
     double ar = 0.0, ai = 0.0;
     for (long long m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
-      const int ix = int(m % n), iy = int((m / n) % n), iz = int(m / ((long long)n * n));
+      const unsigned mu = unsigned(m), nu = unsigned(n);   // n^3 <= 2^30: 32-bit division
+      const unsigned line = mu / nu;
+      const int ix = int(mu - line * nu), iy = int(line % nu), iz = int(line / nu);
       const double dx = px - (ox + (ix + 0.5) * d);
       const double dy = py - (oy + (iy + 0.5) * d);
       const double dz = pz - (oz + (iz + 0.5) * d);
