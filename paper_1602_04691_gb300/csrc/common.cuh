@@ -167,11 +167,17 @@ __device__ __forceinline__ cpx<double> ldgc(const cpx<double>* p) {
   return {v.x, v.y};
 }
 
+// Load and store of one complex value as the FFT stages keep it in shared
+// memory and as the twiddle tables hold it: T's own layout here; paired FP32
+// specialises the pair (dfloat.cuh).
+template <class T> __device__ __forceinline__ cpx<T> ld_stage(const cpx<T>* p) { return *p; }
+template <class T> __device__ __forceinline__ void st_stage(cpx<T>* p, cpx<T> v) { *p = v; }
+
 // z * exp(SIGN * 2 pi i m / L) from a table tab[m] = (cos, sin)(2 pi m / L).
 template <int SIGN, class T>
 __device__ __forceinline__ cpx<T> twL_mul(cpx<T> z, const cpx<T>* __restrict__ tab, int m) {
   // generic load: the table may sit in global memory or in shared memory
-  const cpx<T> w = tab[m];
+  const cpx<T> w = ld_stage(tab + m);
   return cmul(z, cpx<T>{w.x, SIGN > 0 ? w.y : -w.y});
 }
 
@@ -189,14 +195,7 @@ constexpr int bitrev(int i, int R) {
 // Radix-2 decimation in frequency, then the bit-reversal permutation (free:
 // all indices are compile-time constants).  HALF: a[j] = 0 for j >= R/2 on
 // input (the zero padding of Section 3), which removes the first stage's adds.
-// SCALAR: complex sums part by part (T's own addition) instead of the
-// complex operator, which for some T is a packed two-lane instruction.
-template <class T>
-__device__ __forceinline__ cpx<T> add_parts(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
-template <class T>
-__device__ __forceinline__ cpx<T> sub_parts(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
-
-template <int R, int SIGN, bool HALF, class T, bool SCALAR = false>
+template <int R, int SIGN, bool HALF, class T>
 __device__ __forceinline__ void dft(cpx<T> (&a)[R]) {
   if constexpr (R > 1) {
 #pragma unroll
@@ -211,8 +210,8 @@ __device__ __forceinline__ void dft(cpx<T> (&a)[R]) {
             a[b + j + s] = tw64_mul<SIGN>(u, idx);
           } else {
             const cpx<T> v = a[b + j + s];
-            a[b + j] = SCALAR ? add_parts(u, v) : u + v;
-            a[b + j + s] = tw64_mul<SIGN>(SCALAR ? sub_parts(u, v) : u - v, idx);
+            a[b + j] = u + v;
+            a[b + j + s] = tw64_mul<SIGN>(u - v, idx);
           }
         }
       }

@@ -75,7 +75,7 @@ __device__ __forceinline__ int sidx(int j, int c) { return j * C + (c ^ (j & (C 
 
 // One in-place decimation-in-frequency stage of radix R on all C columns:
 // blocks of M points, span s = M / R; outputs multiplied by w_M^(j t').
-template <int R, int SIGN, int L, int C, class T, bool SCALAR = false>
+template <int R, int SIGN, int L, int C, class T>
 __device__ __forceinline__ void dif_stage(cpx<T>* X, int M, const cpx<T>* tw, int tid, int nt) {
   const int s = M / R;
   const int step = L / M;
@@ -85,18 +85,18 @@ __device__ __forceinline__ void dif_stage(cpx<T>* X, int M, const cpx<T>* tw, in
     const int base = blk * M + j;
     cpx<T> v[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) v[t] = X[sidx<C>(base + t * s, c)];
-    dft<R, SIGN, false, T, SCALAR>(v);
+    for (int t = 0; t < R; ++t) v[t] = ld_stage(X + sidx<C>(base + t * s, c));
+    dft<R, SIGN, false>(v);
 #pragma unroll
     for (int t = 1; t < R; ++t) v[t] = twL_mul<SIGN>(v[t], tw, (j * t * step) & (L - 1));
 #pragma unroll
-    for (int t = 0; t < R; ++t) X[sidx<C>(base + t * s, c)] = settle(v[t]);
+    for (int t = 0; t < R; ++t) st_stage(X + sidx<C>(base + t * s, c), settle(v[t]));
   }
 }
 
 // One in-place decimation-in-time stage: inputs multiplied by w_M^(j t), then
 // the radix-R butterfly.
-template <int R, int SIGN, int L, int C, class T, bool SCALAR = false>
+template <int R, int SIGN, int L, int C, class T>
 __device__ __forceinline__ void dit_stage(cpx<T>* X, int M, const cpx<T>* tw, int tid, int nt) {
   const int s = M / R;
   const int step = L / M;
@@ -106,48 +106,48 @@ __device__ __forceinline__ void dit_stage(cpx<T>* X, int M, const cpx<T>* tw, in
     const int base = blk * M + j;
     cpx<T> v[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) v[t] = X[sidx<C>(base + t * s, c)];
+    for (int t = 0; t < R; ++t) v[t] = ld_stage(X + sidx<C>(base + t * s, c));
 #pragma unroll
     for (int t = 1; t < R; ++t) v[t] = twL_mul<SIGN>(v[t], tw, (j * t * step) & (L - 1));
-    dft<R, SIGN, false, T, SCALAR>(v);
+    dft<R, SIGN, false>(v);
 #pragma unroll
-    for (int t = 0; t < R; ++t) X[sidx<C>(base + t * s, c)] = settle(v[t]);
+    for (int t = 0; t < R; ++t) st_stage(X + sidx<C>(base + t * s, c), settle(v[t]));
   }
 }
 
 // Forward DIF stages after the first one (which the callers fuse with their
 // loads): block sizes L/8, L/64, ...
-template <int L, int C, class T, bool SCALAR = false>
+template <int L, int C, class T>
 __device__ __forceinline__ void dif_rest(cpx<T>* X, const cpx<T>* tw, int tid, int nt) {
   using DR = DRad<L>;
   int M = L / 8;
 #pragma unroll 1
   for (int st = 1; st < DR::NST8; ++st) {
-    dif_stage<8, -1, L, C, T, SCALAR>(X, M, tw, tid, nt);
+    dif_stage<8, -1, L, C>(X, M, tw, tid, nt);
     __syncthreads();
     M /= 8;
   }
   if constexpr (DR::RL > 1) {
-    dif_stage<DR::RL, -1, L, C, T, SCALAR>(X, M, tw, tid, nt);
+    dif_stage<DR::RL, -1, L, C>(X, M, tw, tid, nt);
     __syncthreads();
   }
 }
 
 // Inverse DIT stages except the last (block size L), which the callers fuse
 // with their stores: block sizes RL (if any), then 8 RL, 64 RL, ... up to L/8.
-template <int L, int C, class T, bool SCALAR = false>
+template <int L, int C, class T>
 __device__ __forceinline__ void dit_head(cpx<T>* X, const cpx<T>* tw, int tid, int nt) {
   using DR = DRad<L>;
   int M = 1;
   if constexpr (DR::RL > 1) {
     M = DR::RL;
-    dit_stage<DR::RL, +1, L, C, T, SCALAR>(X, M, tw, tid, nt);
+    dit_stage<DR::RL, +1, L, C>(X, M, tw, tid, nt);
     __syncthreads();
   }
 #pragma unroll 1
   for (int st = 1; st < DR::NST8; ++st) {
     M *= 8;
-    dit_stage<8, +1, L, C, T, SCALAR>(X, M, tw, tid, nt);
+    dit_stage<8, +1, L, C>(X, M, tw, tid, nt);
     __syncthreads();
   }
 }

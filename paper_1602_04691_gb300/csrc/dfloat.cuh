@@ -122,6 +122,19 @@ __device__ __forceinline__ cpx<dfl> df_cadd(cpx<dfl> a, cpx<dfl> b) {
   upk2(lo, r.x.lo, r.y.lo);
   return r;
 }
+// Between FFT stages (shared-memory tiles) and in the twiddle tables a
+// paired-FP32 complex value is stored as (re.hi, im.hi, re.lo, im.lo): one
+// 16-byte access then yields the two lane pairs the packed instructions take.
+template <>
+__device__ __forceinline__ cpx<dfl> ld_stage<dfl>(const cpx<dfl>* p) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  return {{f.x, f.z}, {f.y, f.w}};
+}
+template <>
+__device__ __forceinline__ void st_stage<dfl>(cpx<dfl>* p, cpx<dfl> v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.x.hi, v.y.hi, v.x.lo, v.y.lo);
+}
+
 template <>
 __device__ __forceinline__ cpx<dfl> operator+(cpx<dfl> a, cpx<dfl> b) { return df_cadd<false>(a, b); }
 template <>

@@ -710,7 +710,14 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
       cpx<dfl>* twdf = new cpx<dfl>[p->L];
       host_twiddles<double>(p->L, twd);
       host_twiddles<float>(p->L, twf);
-      for (int m = 0; m < p->L; ++m) twdf[m] = {df_from_double_host(twd[m].x), df_from_double_host(twd[m].y)};
+      for (int m = 0; m < p->L; ++m) {   // the stage layout of paired FP32: (re.hi, im.hi, re.lo, im.lo)
+        const dfl re = df_from_double_host(twd[m].x), im = df_from_double_host(twd[m].y);
+        float* f = reinterpret_cast<float*>(twdf + m);
+        f[0] = re.hi;
+        f[1] = im.hi;
+        f[2] = re.lo;
+        f[3] = im.lo;
+      }
       cudaError_t e1 = cudaMemcpy(p->tw64, twd, sizeof(cpx<double>) * p->L, cudaMemcpyHostToDevice);
       cudaError_t e2 = cudaMemcpy(p->tw32, twf, sizeof(cpx<float>) * p->L, cudaMemcpyHostToDevice);
       cudaError_t e3 = cudaMemcpy(p->twdf, twdf, sizeof(cpx<dfl>) * p->L, cudaMemcpyHostToDevice);

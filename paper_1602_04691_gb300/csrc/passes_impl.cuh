@@ -756,20 +756,20 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_st
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
-      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = settle(v[t]);
+      for (int t = 0; t < 8; ++t) st_stage(X + sidx<C>(j + t * S8, c), settle(v[t]));
     }
     __syncthreads();
     dif_rest<L, C>(X, TW, tid, NT);
     for (int e = tid; e < C * L; e += NT) {
       const int c = e % C, p = e / C;
       const int k = digit_rev<L>(p);
-      if (c < colmax && k < a.n_out) out[(long long)k * a.out_pt + c] = X[sidx<C>(p, c)];
+      if (c < colmax && k < a.n_out) out[(long long)k * a.out_pt + c] = ld_stage(X + sidx<C>(p, c));
     }
   } else {
     for (int e = tid; e < C * L; e += NT) {
       const int c = e % C, p = e / C;
       const int k = digit_rev<L>(p);
-      X[sidx<C>(p, c)] = c < colmax ? in[(long long)k * a.in_pt + c] : czero<T>();
+      st_stage(X + sidx<C>(p, c), c < colmax ? in[(long long)k * a.in_pt + c] : czero<T>());
     }
     __syncthreads();
     dit_head<L, C>(X, TW, tid, NT);
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_st
       const int c = g % C, j = g / C;
       cpx<T> v[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
+      for (int t = 0; t < 8; ++t) v[t] = ld_stage(X + sidx<C>(j + t * S8, c));
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
       dft<8, +1, false>(v);
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xf
 #pragma unroll
     for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
-    for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = settle(v[t]);
+    for (int t = 0; t < 8; ++t) st_stage(X + sidx<C>(j + t * S8, c), settle(v[t]));
   }
   __syncthreads();
   dif_rest<L, C>(X, TW, tid, NT);
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xf
   for (int e = tid; e < C * L; e += NT) {
     const int k = e % L, c = e / L;
     const long long line = (long long)blockIdx.x * C + c;
-    if (line < a.nlines) out[line * a.line_len_out + k] = X[sidx<C>(inv_digit_rev<L>(k), c)];
+    if (line < a.nlines) out[line * a.line_len_out + k] = ld_stage(X + sidx<C>(inv_digit_rev<L>(k), c));
   }
 }
 
@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xi
   for (int e = tid; e < C * L; e += NT) {
     const int k = e % L, c = e / L;
     const long long line = (long long)blockIdx.x * C + c;
-    X[sidx<C>(inv_digit_rev<L>(k), c)] = line < a.nlines ? in[line * a.line_len_in + k] : czero<T>();
+    st_stage(X + sidx<C>(inv_digit_rev<L>(k), c), line < a.nlines ? in[line * a.line_len_in + k] : czero<T>());
   }
   __syncthreads();
   dit_head<L, C>(X, TW, tid, NT);
@@ -860,7 +860,7 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xi
     const long long line = (long long)blockIdx.x * C + c;
     cpx<T> v[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
+    for (int t = 0; t < 8; ++t) v[t] = ld_stage(X + sidx<C>(j + t * S8, c));
 #pragma unroll
     for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
     dft<8, +1, false>(v);
@@ -1276,9 +1276,7 @@ k_zconv_pipe(SArgs a) {
 // Z convolution for the paired-FP32 residual: persistent CTAs, a tile of C
 // columns (C * 16 B = 128 B rows) held in shared memory and transformed in
 // place by looped radix-8 stages (dfft.cuh); the next tile's input rows
-// stream into a staging buffer with cp.async meanwhile.  Its butterflies add
-// part by part: this pass is bound by instruction issue, and the packed
-// complex sum's register moves cost it more than they save (measured).
+// stream into a staging buffer with cp.async meanwhile.
 // ---------------------------------------------------------------------------
 template <int L, int C, class T>
 struct ZSmem {
@@ -1294,7 +1292,6 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
   using ZS = ZSmem<L, C, T>;
   constexpr int NT = ZS::NT;
   constexpr int S8 = L / 8;          // span of the first (and last) radix-8 stage
-  constexpr bool SC = std::is_same<T, dfl>::value;   // paired FP32: sums part by part
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* X = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* S = X + ZS::X_ELEMS;
@@ -1327,15 +1324,15 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
         v[t] = czero<T>();
         if (t < 4 && j + t * S8 < a.n_in) v[t] = S[(j + t * S8) * C + c];
       }
-      dft<8, -1, true, T, SC>(v);
+      dft<8, -1, true>(v);
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<-1>(v[t], TW, (j * t) & (L - 1));
 #pragma unroll
-      for (int t = 0; t < 8; ++t) X[sidx<C>(j + t * S8, c)] = settle(v[t]);
+      for (int t = 0; t < 8; ++t) st_stage(X + sidx<C>(j + t * S8, c), settle(v[t]));
     }
     __syncthreads();
     if (next < ntiles) zpipe_prefetch_rows<T, L, C, NT>(a, next, per_rhs, S);
-    dif_rest<L, C, T, SC>(X, TW, tid, NT);
+    dif_rest<L, C>(X, TW, tid, NT);
     // spectrum: position p holds frequency kz = digit_rev(p)
     const int my = mirror_index(ky, L);
     for (int e = tid; e < C * L; e += NT) {
@@ -1343,20 +1340,20 @@ __global__ void __launch_bounds__(ZSmem<L, C, T>::NT, ZSmem<L, C, T>::MINB) k_zc
       const int mz = mirror_index(digit_rev<L>(p), L);
       const int mx = mirror_index(cb * C + c, L);
       const int si = sidx<C>(p, c);
-      X[si] = settle(cmul(X[si], ldgc(gh + ((long long)mz * a.H + my) * a.H + mx)));
+      st_stage(X + si, settle(cmul(ld_stage(X + si), ldgc(gh + ((long long)mz * a.H + my) * a.H + mx))));
     }
     __syncthreads();
-    dit_head<L, C, T, SC>(X, TW, tid, NT);
+    dit_head<L, C>(X, TW, tid, NT);
     // last inverse stage (M = L), keep rows z < n_out
     cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + (long long)ky * a.out_outer + (long long)cb * C;
     for (int g = tid; g < C * S8; g += NT) {
       const int c = g % C, j = g / C;
       cpx<T> v[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = X[sidx<C>(j + t * S8, c)];
+      for (int t = 0; t < 8; ++t) v[t] = ld_stage(X + sidx<C>(j + t * S8, c));
 #pragma unroll
       for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
-      dft<8, +1, false, T, SC>(v);
+      dft<8, +1, false>(v);
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int z = j + t * S8;
