@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define ORI_ABI_VERSION 4
+#define ORI_ABI_VERSION 5
 
 typedef struct ori_plan_s* ori_plan_t;
 
@@ -125,7 +125,9 @@ typedef struct {
                           the residual with an FP32 operator application when the
                           error bound allows (see ori_solve_info.resid_updates);
                           0 recomputes b - B w every step                           */
-  int    reserved[5];
+  int    history;      /* 1: record COCG's residual estimate after every iteration
+                          (read with ori_plan_residual_history); 0 (default): off  */
+  int    reserved[4];
   const double* x0;    /* NULL (default): start from u = 0.  Else an initial guess of u
                           on the device, n^3 complex128 per system (ori_cocg_solve_batch:
                           system r at offset r n^3).  The solve starts from w = S x0
@@ -181,6 +183,33 @@ void ori_default_plan_opts(ori_plan_opts* o);
 ori_status ori_plan(int64_t n, double k, const ori_domain* dom,
                     const double* h_dev, const double* N_dev,
                     const ori_plan_opts* opts, void* stream, ori_plan_t* out);
+
+/*
+ * Saving and reusing a plan's kernel spectra (the plan build's expensive part:
+ * the FP64 FFT of the kernel cube per wave number).  The spectra depend on n,
+ * the padded length L, c_S, the cell size side / n and the wave numbers, not
+ * on h, N or the origin.
+ *
+ * ori_plan_spectrum_bytes - *bytes = size of the saved form: a 576-byte header
+ *   (format tag, n, L, wave numbers, c_S, side) and n_k (L/2+1)^3 complex128
+ *   spectrum entries.
+ * ori_plan_save_spectrum - write the saved form into host_buf (bytes >= the
+ *   size above; pageable or pinned host memory).  A lean plan writes its
+ *   paired-FP32 spectrum widened to complex128 (about 48 significant bits).
+ *   Synchronises `stream`.
+ * ori_plan_from_spectrum - as ori_plan, but the spectra come from a saved form
+ *   instead of being computed: n, L (with opts->min_L), c_S (opts->c_S) and
+ *   side (dom->side) must equal the saved ones, and the wave numbers are the
+ *   saved ones (k, opts->n_k and opts->ks are ignored).  A mismatch, or a
+ *   buffer that is too short or not a saved spectrum, returns
+ *   ORI_ERR_INVALID_ARG.  Synchronises `stream`.
+ */
+ori_status ori_plan_spectrum_bytes(ori_plan_t plan, size_t* bytes);
+ori_status ori_plan_save_spectrum(ori_plan_t plan, void* host_buf, size_t bytes, void* stream);
+ori_status ori_plan_from_spectrum(int64_t n, const ori_domain* dom, const double* h_dev,
+                                  const double* N_dev, const ori_plan_opts* opts,
+                                  const void* host_buf, size_t bytes, void* stream,
+                                  ori_plan_t* out);
 
 /* Replace h and N (same layout as ori_plan) without recomputing the spectrum.
  * Synchronises `stream`. */
@@ -432,6 +461,17 @@ ori_status ori_plan_set_timing(ori_plan_t plan, int on);
 ori_status ori_plan_get_stats(ori_plan_t plan, ori_plan_stats* out);
 /* Zero the counters. */
 ori_status ori_plan_reset_stats(ori_plan_t plan);
+
+/*
+ * ori_plan_residual_history - the residual estimates of the last solve that ran
+ * with opts->history = 1: for system `system` of that solve (0 for
+ * ori_cocg_solve), COCG's recursive residual ||r|| / ||RHS|| after every
+ * iteration, the refinement steps of a mixed solve one after another (the
+ * first 512 iterations of each step).  Copies min(count, max) values to
+ * out_host (may be NULL when max = 0); *count receives the number recorded.
+ */
+ori_status ori_plan_residual_history(ori_plan_t plan, int system, double* out_host, int max,
+                                     int* count);
 
 /* Static description of a status code. */
 const char* ori_status_string(int status);

@@ -13,7 +13,7 @@ import os
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libori.so")
 
-ABI_VERSION = 4   # ORI_ABI_VERSION of include/ori.h that these declarations follow
+ABI_VERSION = 5   # ORI_ABI_VERSION of include/ori.h that these declarations follow
 
 ORI_OK = 0
 ORI_ERR_INVALID_ARG = 1
@@ -38,7 +38,8 @@ EXPORTS = [
     "ori_adjoint_solve", "ori_status_string", "ori_last_error", "ori_abi_version",
     "ori_plan_set_timing", "ori_plan_get_stats", "ori_plan_reset_stats", "ori_matvec_noalloc",
     "ori_cocg_solve_batch", "ori_plan_get_schedule", "ori_plan_set_schedule", "ori_plan_autotune",
-    "ori_field",
+    "ori_field", "ori_plan_spectrum_bytes", "ori_plan_save_spectrum", "ori_plan_from_spectrum",
+    "ori_plan_residual_history",
 ]
 
 ORI_SCHED_PERSISTENT = 0
@@ -62,7 +63,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("precision", C.c_int),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int), ("check_every", C.c_int),
                 ("alpha", C.c_double * 3), ("use_graph", C.c_int), ("residual", C.c_int),
-                ("resid_update", C.c_int), ("reserved", C.c_int * 5), ("x0", C.c_void_p)]
+                ("resid_update", C.c_int), ("history", C.c_int), ("reserved", C.c_int * 4), ("x0", C.c_void_p)]
 
 
 class SolveInfo(C.Structure):
@@ -173,6 +174,15 @@ def load():
     lib.ori_plan_get_stats.restype = i
     lib.ori_plan_reset_stats.argtypes = [vp]
     lib.ori_plan_reset_stats.restype = i
+    lib.ori_plan_spectrum_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+    lib.ori_plan_spectrum_bytes.restype = i
+    lib.ori_plan_save_spectrum.argtypes = [vp, vp, C.c_size_t, vp]
+    lib.ori_plan_save_spectrum.restype = i
+    lib.ori_plan_from_spectrum.argtypes = [i64, C.POINTER(Domain), vp, vp, C.POINTER(PlanOpts), vp, C.c_size_t, vp,
+                                           C.POINTER(vp)]
+    lib.ori_plan_from_spectrum.restype = i
+    lib.ori_plan_residual_history.argtypes = [vp, i, vp, i, C.POINTER(i)]
+    lib.ori_plan_residual_history.restype = i
     lib.ori_matvec_noalloc.argtypes = [i64, d, C.POINTER(Domain), d, vp, vp, vp, vp, vp]
     lib.ori_matvec_noalloc.restype = i
     lib.ori_status_string.argtypes = [i]

@@ -75,6 +75,8 @@ struct ori_plan_s {
   double d = 0, c_S = 0, side = 0, origin[3] = {0, 0, 0};
   std::vector<double> ks;          // wave numbers; one spectrum each
   bool lean = false;               // mixed-solve-only plan (ori_plan_opts.lean)
+  std::vector<std::vector<double>> history;   // per system: residual estimates of the last solve
+                                              // run with ori_solve_opts.history
   size_t bytes = 0, mem_cap = 0;
   int sm_count = 0;
   unsigned long long zero_S = 0;
@@ -584,6 +586,65 @@ static ori_status build_spectrum(ori_plan_s* p) {
   return st;
 }
 
+// Saved form of a plan's spectra (ori_plan_save_spectrum): this header, then
+// n_k (L/2+1)^3 complex128 entries from byte kSpecPayload on.
+struct SpecHeader {
+  char tag[8];          // "ORISPEC", NUL-terminated
+  int32_t version;      // 1
+  int32_t n, L, n_k;
+  double c_S, side;
+  uint64_t entries;     // n_k (L/2+1)^3
+  double ks[64];
+};
+static constexpr size_t kSpecPayload = 576;
+static_assert(sizeof(SpecHeader) <= kSpecPayload, "spectrum header");
+static const char kSpecTag[8] = {'O', 'R', 'I', 'S', 'P', 'E', 'C', 0};
+
+static size_t spectrum_bytes(const ori_plan_s* p) {
+  return kSpecPayload + p->ks.size() * size_t(p->H) * p->H * p->H * sizeof(cpx<double>);
+}
+
+// Fill the plan's spectra from a saved form whose header has been checked.
+static ori_status load_spectrum(ori_plan_s* p, const unsigned char* buf) {
+  NvtxRange nvtx("ori plan spectrum (saved)");
+  const long long H3 = (long long)p->H * p->H * p->H;
+  const long long HZ = (long long)p->H * p->H * p->L;
+  const cpx<double>* src = reinterpret_cast<const cpx<double>*>(buf + kSpecPayload);
+  // a lean plan has no FP64 spectrum: the entries go through a bounded staging buffer
+  const long long chunk = p->ghat64 ? H3 : std::min<long long>(H3, 1LL << 26);
+  cpx<double>* stage = nullptr;
+  if (!p->ghat64) {
+    cudaError_t e = cudaMalloc(&stage, size_t(chunk) * sizeof(cpx<double>));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ORI_ERR_OOM, std::string("cudaMalloc (spectrum load): ") + cudaGetErrorString(e));
+    }
+  }
+  ori_status st = ORI_OK;
+  for (size_t ik = 0; ik < p->ks.size() && st == ORI_OK; ++ik) {
+    for (long long off = 0; off < H3 && st == ORI_OK; off += chunk) {
+      const long long cnt = std::min(chunk, H3 - off);
+      cpx<double>* dst = p->ghat64 ? p->ghat64 + ik * H3 + off : stage;
+      cudaError_t e = cudaMemcpyAsync(dst, src + ik * H3 + off, size_t(cnt) * sizeof(cpx<double>),
+                                      cudaMemcpyHostToDevice, p->ps);
+      if (e == cudaSuccess) {
+        k_spectrum_convert<<<p->vec_grid, 256, 0, p->ps>>>(dst, cnt, p->ghat32 + ik * H3 + off, p->ghatdf + ik * H3 + off);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(p->ps);   // the staging buffer is reused
+      if (e != cudaSuccess) st = fail(ORI_ERR_CUDA, std::string("spectrum load: ") + cudaGetErrorString(e));
+    }
+    if (st == ORI_OK && p->ghatZ32) {
+      k_build_ghatZ<<<p->vec_grid, 256, 0, p->ps>>>(p->ghat32 + ik * H3, p->ghatZ32 + ik * HZ, p->L, p->H);
+      cudaError_t e = cudaGetLastError();
+      if (e == cudaSuccess) e = cudaStreamSynchronize(p->ps);
+      if (e != cudaSuccess) st = fail(ORI_ERR_CUDA, std::string("spectrum load: ") + cudaGetErrorString(e));
+    }
+  }
+  if (stage) cudaFree(stage);
+  return st;
+}
+
 static bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
 extern "C" {
@@ -627,8 +688,12 @@ const char* ori_status_string(int s) {
   }
 }
 
-ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_dev,
-                    const double* N_dev, const ori_plan_opts* opts, void* stream, ori_plan_t* out) {
+}  // extern "C"
+
+// ori_plan and ori_plan_from_spectrum: spec == NULL builds the spectra.
+static ori_status plan_create(int64_t n, double k, const ori_domain* dom, const double* h_dev, const double* N_dev,
+                              const ori_plan_opts* opts, void* stream, const void* spec, size_t spec_bytes,
+                              ori_plan_t* out) {
   g_last_error.clear();
   if (!out) return fail(ORI_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -647,7 +712,25 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
   if (o.min_L != 0 && (o.min_L < 4 || o.min_L > 2048 || (o.min_L & (o.min_L - 1)) != 0))
     return fail(ORI_ERR_INVALID_ARG, "min_L must be 0 or a power of two in [4, 2048]");
   std::vector<double> ks;
-  if (o.n_k > 0) {
+  if (spec) {
+    SpecHeader hd;
+    if (spec_bytes < kSpecPayload) return fail(ORI_ERR_INVALID_ARG, "saved spectrum: buffer shorter than its header");
+    std::memcpy(&hd, spec, sizeof(hd));
+    if (std::memcmp(hd.tag, kSpecTag, sizeof(kSpecTag)) != 0 || hd.version != 1)
+      return fail(ORI_ERR_INVALID_ARG, "saved spectrum: not a saved spectrum of this format");
+    int Lw = 4;
+    while (Lw < 2 * n) Lw *= 2;
+    Lw = std::max(Lw, o.min_L);
+    const long long H = Lw / 2 + 1;
+    if (hd.n != n || hd.L != Lw)
+      return fail(ORI_ERR_INVALID_ARG, "saved spectrum: n or padded length L differs from this plan's");
+    if (hd.c_S != o.c_S || hd.side != dom->side)
+      return fail(ORI_ERR_INVALID_ARG, "saved spectrum: c_S or the cube side differs from this plan's");
+    if (hd.n_k < 1 || hd.n_k > 64 || hd.entries != uint64_t(hd.n_k) * uint64_t(H * H * H) ||
+        spec_bytes < kSpecPayload + hd.entries * sizeof(cpx<double>))
+      return fail(ORI_ERR_INVALID_ARG, "saved spectrum: truncated or inconsistent");
+    ks.assign(hd.ks, hd.ks + hd.n_k);
+  } else if (o.n_k > 0) {
     if (!o.ks) return fail(ORI_ERR_INVALID_ARG, "opts->ks is NULL while opts->n_k > 0");
     if (o.n_k > 64) return fail(ORI_ERR_INVALID_ARG, "at most 64 wave numbers per plan");
     ks.assign(o.ks, o.ks + o.n_k);
@@ -727,7 +810,7 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
       if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) { st = fail(ORI_ERR_CUDA, "twiddle upload failed"); break; }
     }
     if ((st = set_medium(p, h_dev, N_dev))) break;
-    if ((st = build_spectrum(p))) break;
+    if ((st = spec ? load_spectrum(p, static_cast<const unsigned char*>(spec)) : build_spectrum(p))) break;
     if ((st = ensure_capacity(p, 1))) break;   // after the spectrum build: lower peak memory
     if ((st = leave(p, user))) break;
   } while (0);
@@ -736,6 +819,80 @@ ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_
     return st;
   }
   *out = p;
+  return ORI_OK;
+}
+
+extern "C" {
+
+ori_status ori_plan(int64_t n, double k, const ori_domain* dom, const double* h_dev,
+                    const double* N_dev, const ori_plan_opts* opts, void* stream, ori_plan_t* out) {
+  return plan_create(n, k, dom, h_dev, N_dev, opts, stream, nullptr, 0, out);
+}
+
+ori_status ori_plan_from_spectrum(int64_t n, const ori_domain* dom, const double* h_dev, const double* N_dev,
+                                  const ori_plan_opts* opts, const void* host_buf, size_t bytes, void* stream,
+                                  ori_plan_t* out) {
+  if (!host_buf) {
+    g_last_error.clear();
+    return fail(ORI_ERR_INVALID_ARG, "host_buf is NULL");
+  }
+  return plan_create(n, 1.0, dom, h_dev, N_dev, opts, stream, host_buf, bytes, out);
+}
+
+ori_status ori_plan_spectrum_bytes(ori_plan_t p, size_t* bytes) {
+  g_last_error.clear();
+  if (!p || !bytes) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  *bytes = spectrum_bytes(p);
+  return ORI_OK;
+}
+
+ori_status ori_plan_save_spectrum(ori_plan_t p, void* host_buf, size_t bytes, void* stream) {
+  g_last_error.clear();
+  if (!p || !host_buf) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < spectrum_bytes(p)) return fail(ORI_ERR_INVALID_ARG, "host_buf is shorter than ori_plan_spectrum_bytes");
+  ORI_TRY(enter(p, reinterpret_cast<cudaStream_t>(stream)));
+  SpecHeader hd{};
+  std::memcpy(hd.tag, kSpecTag, sizeof(kSpecTag));
+  hd.version = 1;
+  hd.n = p->n;
+  hd.L = p->L;
+  hd.n_k = int32_t(p->ks.size());
+  hd.c_S = p->c_S;
+  hd.side = p->side;
+  const size_t H3 = size_t(p->H) * p->H * p->H;
+  hd.entries = uint64_t(p->ks.size() * H3);
+  for (size_t i = 0; i < p->ks.size(); ++i) hd.ks[i] = p->ks[i];
+  unsigned char* out = static_cast<unsigned char*>(host_buf);
+  std::memset(out, 0, kSpecPayload);
+  std::memcpy(out, &hd, sizeof(hd));
+  cpx<double>* dst = reinterpret_cast<cpx<double>*>(out + kSpecPayload);
+  const size_t nbytes = p->ks.size() * H3 * sizeof(cpx<double>);
+  if (p->ghat64) {
+    ORI_CUDA(cudaMemcpyAsync(dst, p->ghat64, nbytes, cudaMemcpyDeviceToHost, p->ps));
+    ORI_CUDA(cudaStreamSynchronize(p->ps));
+  } else {
+    // lean plan: the paired-FP32 spectrum (same 16 bytes per entry), widened in place
+    ORI_CUDA(cudaMemcpyAsync(dst, p->ghatdf, nbytes, cudaMemcpyDeviceToHost, p->ps));
+    ORI_CUDA(cudaStreamSynchronize(p->ps));
+    for (size_t i = 0; i < p->ks.size() * H3; ++i) {
+      float f[4];
+      std::memcpy(f, dst + i, sizeof(f));   // re.hi, re.lo, im.hi, im.lo
+      const cpx<double> v{double(f[0]) + double(f[1]), double(f[2]) + double(f[3])};
+      std::memcpy(dst + i, &v, sizeof(v));
+    }
+  }
+  ORI_TRY(leave(p, reinterpret_cast<cudaStream_t>(stream)));
+  return ORI_OK;
+}
+
+ori_status ori_plan_residual_history(ori_plan_t p, int system, double* out_host, int max, int* count) {
+  g_last_error.clear();
+  if (!p || !count || max < 0 || (max > 0 && !out_host)) return fail(ORI_ERR_INVALID_ARG, "bad argument");
+  if (system < 0 || system >= int(p->history.size()))
+    return fail(ORI_ERR_INVALID_ARG, "no residual history for this system (solve with opts.history = 1)");
+  const std::vector<double>& h = p->history[size_t(system)];
+  *count = int(h.size());
+  for (int i = 0; i < std::min(max, int(h.size())); ++i) out_host[i] = h[size_t(i)];
   return ORI_OK;
 }
 
@@ -1057,6 +1214,22 @@ static ori_status push_doubles(ori_plan_s* p, double* dst, const double* src, in
   return ORI_OK;
 }
 
+// Append COCG's recursive residual after each iteration of the last inner run
+// to the history of every system taking part: ||r|| / ||RHS||, where the
+// inner system was scaled by 1 / scale[r] (FP64 COCG: scale 1).
+static ori_status record_history(ori_plan_s* p, int nrhs, const InnerResult* ir, const double* scale,
+                                 const double* bnorm, const std::vector<int>& part) {
+  std::vector<double> buf(kHistMax);
+  for (int i = 0; i < nrhs; ++i) {
+    if (!part[i] || bnorm[i] <= 0) continue;
+    const int cnt = std::min(ir[i].iters, kHistMax);
+    if (cnt <= 0) continue;
+    ORI_CUDA(cudaMemcpy(buf.data(), p->sc[i].hist, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int t = 0; t < cnt; ++t) p->history[i].push_back(scale[i] * std::sqrt(buf[t]) / bnorm[i]);
+  }
+  return ORI_OK;
+}
+
 // Solve B w_r = b64_r for the batch (b64 and bnorm[r] ready); w -> p->w.
 static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* bnorm, const ori_solve_opts& o,
                           ori_solve_info* info, bool warm = false) {
@@ -1107,6 +1280,10 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
       for (int i = 0; i < nrhs; ++i) tin[i] = active[i] ? std::min(1.0, o.tol * bnorm[i] / rn[i]) : 1.0;
       ORI_TRY(cocg_inner<double>(p, nrhs, rhs_per_k, p->w, p->r64, p->p64, p->q64, p->S64, tin.data(), budget,
                                  o.check_every, graph, ir.data(), false));
+      if (o.history) {
+        const std::vector<double> one(nrhs, 1.0);
+        ORI_TRY(record_history(p, nrhs, ir.data(), one.data(), bnorm, active));
+      }
       for (int i = 0; i < nrhs; ++i) p->h_skip[i] = active[i] ? 0 : 1;
       ORI_TRY(push_skip(p, nrhs));
       std::vector<double> rn_new(rn);
@@ -1164,6 +1341,7 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
     ORI_VEC(p, ORI_PASS_VECTOR, (k_normalise_to_f32<<<dim3(vg, nrhs), 256, 0, p->ps>>>(p->r64, p->r32, n3, p->d_scl)));
     ORI_TRY(cocg_inner<float>(p, nrhs, rhs_per_k, p->x32, p->r32, p->p32, p->q32, p->S32, tin.data(), budget,
                               o.check_every, graph, ir.data()));
+    if (o.history) ORI_TRY(record_history(p, nrhs, ir.data(), rn.data(), bnorm, active));
     bool nonfinite_all = true;
     std::vector<double> scl(nrhs, 0.0);
     for (int i = 0; i < nrhs; ++i) {
@@ -1260,6 +1438,7 @@ static ori_status check_solve_opts(const ori_solve_opts* in, ori_solve_opts* o) 
   if (!finite3(o->alpha)) return fail(ORI_ERR_INVALID_ARG, "alpha must be finite");
   if (o->residual != ORI_DF && o->residual != ORI_FP64)
     return fail(ORI_ERR_INVALID_ARG, "residual must be ORI_DF or ORI_FP64");
+  if (o->history != 0 && o->history != 1) return fail(ORI_ERR_INVALID_ARG, "history must be 0 or 1");
   return ORI_OK;
 }
 
@@ -1272,6 +1451,7 @@ static ori_status solve_batch(ori_plan_s* p, int nk, int ndir, const double* rhs
   if (p->lean && (o.precision == ORI_FP64 || o.residual == ORI_FP64))
     return fail(ORI_ERR_UNSUPPORTED, "a lean plan solves in mixed precision with the paired-FP32 residual only");
   ORI_TRY(ensure_capacity(p, nrhs));
+  if (o.history) p->history.assign(size_t(nrhs), std::vector<double>());
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
   std::vector<double> kv(nrhs), dv(3 * nrhs);
@@ -1391,6 +1571,7 @@ ori_status ori_adjoint_solve(ori_plan_t p, const double* u_dev, const double* ec
   ori_solve_info info{};
   cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
   ORI_TRY(ensure_capacity(p, 1));
+  if (o.history) p->history.assign(1, std::vector<double>());
   ORI_TRY(enter(p, user));
   ORI_CUDA(cudaEventRecord(p->ev0, p->ps));
   ORI_VEC(p, ORI_PASS_VECTOR,

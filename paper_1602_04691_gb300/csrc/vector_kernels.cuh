@@ -67,6 +67,17 @@ __global__ void k_extract_ghat(const cpx<double>* __restrict__ cube, cpx<double>
   }
 }
 
+// A saved FP64 spectrum (count entries) into the FP32 and paired-FP32 copies.
+__global__ void k_spectrum_convert(const cpx<double>* __restrict__ g64, long long count, cpx<float>* g32,
+                                   cpx<dfl>* gdf) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cpx<double> v = g64[i];
+    g32[i] = ccast<float>(v);
+    gdf[i] = c_from_c64<dfl>(v);
+  }
+}
+
 // FP32 spectrum in the order the Z pass reads it: for each my and each block
 // of 16 kx columns, the entries mz = 0..L/2 as rows of 16 (one contiguous
 // slice per Z tile).  gz[((my * (L/16) + cb) * H + mz) * 16 + c] =

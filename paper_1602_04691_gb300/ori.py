@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 
 import torch
 
@@ -60,7 +61,7 @@ def _out(t: torch.Tensor, dtype, numel: int, name: str) -> torch.Tensor:
 
 def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_outer=8,
                check_every=8, alpha=(0.0, 0.0, 1.0), use_graph=True, residual="df",
-               resid_update=True, x0=None) -> _lib.SolveOpts:
+               resid_update=True, x0=None, history=False) -> _lib.SolveOpts:
     lib = _lib.load()
     o = _lib.SolveOpts()
     lib.ori_default_solve_opts(C.byref(o))
@@ -75,6 +76,7 @@ def solve_opts(tol=1e-6, precision="mixed", maxit=1000, inner_tol=1e-5, max_oute
     o.use_graph = 1 if use_graph else 0
     o.residual = _PREC[residual]
     o.resid_update = 1 if resid_update else 0
+    o.history = 1 if history else 0
     if x0 is not None:
         if not (isinstance(x0, torch.Tensor) and x0.is_cuda and x0.dtype == torch.complex128
                 and x0.is_contiguous() and not x0.is_conj() and not x0.is_neg()):
@@ -90,13 +92,22 @@ class Plan:
     densities, both C-ordered [z][y][x].  c_S defaults to 4 pi (spheres).
     k may be a sequence of wave numbers: the plan then holds one spectrum per
     entry, ``solve_batch`` solves for all of them, and the single-system
-    calls use the first."""
+    calls use the first.  ``spectrum``: the bytes of ``save_spectrum`` of a
+    plan with the same n, padded length, c_S and side (or a path to a file of
+    them); the plan then takes its spectra from there instead of computing
+    them, and its wave numbers are the saved ones (k is ignored)."""
 
     def __init__(self, n: int, k, h: torch.Tensor, N: torch.Tensor, side: float = 1.0,
                  origin=(0.0, 0.0, 0.0), c_S: float | None = None, mem_cap: int = 0, min_L: int = 0,
-                 lean: bool = False, stream=None):
+                 lean: bool = False, stream=None, spectrum=None):
         lib = _lib.load()
         self.n = int(n)
+        if spectrum is not None:
+            if isinstance(spectrum, (str, os.PathLike)):
+                with open(spectrum, "rb") as f:
+                    spectrum = f.read()
+            spectrum = bytes(spectrum)
+            k = list(_saved_wave_numbers(spectrum))
         self.ks = [float(v) for v in k] if hasattr(k, "__len__") else [float(k)]
         if not self.ks:
             raise ValueError("k must hold at least one wave number")
@@ -124,9 +135,13 @@ class Plan:
             po.ks = C.cast(ks_arr, C.POINTER(C.c_double))
         handle = C.c_void_p()
         with torch.cuda.device(self.device):
-            st = lib.ori_plan(self.n, self.k, C.byref(dom), h.data_ptr(), N.data_ptr(), C.byref(po),
-                              _stream_ptr(stream), C.byref(handle))
-        _lib.check(st, "ori_plan")
+            if spectrum is not None:
+                st = lib.ori_plan_from_spectrum(self.n, C.byref(dom), h.data_ptr(), N.data_ptr(), C.byref(po),
+                                                spectrum, len(spectrum), _stream_ptr(stream), C.byref(handle))
+            else:
+                st = lib.ori_plan(self.n, self.k, C.byref(dom), h.data_ptr(), N.data_ptr(), C.byref(po),
+                                  _stream_ptr(stream), C.byref(handle))
+        _lib.check(st, "ori_plan_from_spectrum" if spectrum is not None else "ori_plan")
         self._h = handle
         nn, LL, by = C.c_int64(), C.c_int64(), C.c_size_t()
         lib.ori_plan_info(self._h, C.byref(nn), C.byref(LL), C.byref(by))
@@ -198,6 +213,35 @@ class Plan:
         name = torch.cuda.get_device_name(self.device)
         return _at.tune(self, nrhs, name, path=path, reps=reps, force=force)
 
+    # -- saved spectra and residual histories --------------------------------------
+    def save_spectrum(self, path: str | None = None, stream=None) -> bytes:
+        """The plan's kernel spectra in their saved form (ori_plan_save_spectrum);
+        written to `path` as well when given.  Plan(..., spectrum=...) reuses them."""
+        lib = _lib.load()
+        nb = C.c_size_t()
+        _lib.check(lib.ori_plan_spectrum_bytes(self.handle, C.byref(nb)), "ori_plan_spectrum_bytes")
+        buf = C.create_string_buffer(nb.value)
+        with torch.cuda.device(self.device):
+            _lib.check(lib.ori_plan_save_spectrum(self.handle, buf, nb.value, _stream_ptr(stream)),
+                       "ori_plan_save_spectrum")
+        data = buf.raw
+        if path is not None:
+            with open(path, "wb") as f:
+                f.write(data)
+        return data
+
+    def residual_history(self, system: int = 0) -> list:
+        """COCG's residual estimates ||r|| / ||RHS|| after each iteration of the last
+        solve run with history=True (refinement steps one after another)."""
+        lib = _lib.load()
+        cnt = C.c_int()
+        _lib.check(lib.ori_plan_residual_history(self.handle, int(system), None, 0, C.byref(cnt)),
+                   "ori_plan_residual_history")
+        out = (C.c_double * max(1, cnt.value))()
+        _lib.check(lib.ori_plan_residual_history(self.handle, int(system), out, cnt.value, C.byref(cnt)),
+                   "ori_plan_residual_history")
+        return [float(out[i]) for i in range(cnt.value)]
+
     # -- medium ----------------------------------------------------------------
     def set_medium(self, h: torch.Tensor, N: torch.Tensor, stream=None):
         m = self.n ** 3
@@ -242,6 +286,8 @@ class Plan:
             _lib.check(st, "ori_cocg_solve")
         d = info.as_dict()
         d["returned"] = st
+        if kw.get("history"):
+            d["history"] = self.residual_history(0)
         return u, d
 
     def solve_batch(self, alphas=None, rhs: torch.Tensor | None = None, out: torch.Tensor | None = None,
@@ -319,6 +365,17 @@ class Plan:
         d = info.as_dict()
         d["returned"] = st
         return gh, gN, d
+
+
+def _saved_wave_numbers(data: bytes):
+    """Wave numbers stored in a saved spectrum's header (the library checks the rest)."""
+    import struct
+    if len(data) < 576 or data[:8] != b"ORISPEC\0":
+        raise ValueError("not a saved spectrum")
+    n_k = struct.unpack_from("<i", data, 20)[0]
+    if not 1 <= n_k <= 64:
+        raise ValueError("saved spectrum: bad wave-number count")
+    return struct.unpack_from(f"<{n_k}d", data, 48)
 
 
 def solve(h: torch.Tensor, N: torch.Tensor, k, side: float = 1.0, origin=(0.0, 0.0, 0.0), rhs=None,
