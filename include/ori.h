@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define ORI_ABI_VERSION 5
+#define ORI_ABI_VERSION 6
 
 typedef struct ori_plan_s* ori_plan_t;
 
@@ -449,6 +449,8 @@ typedef struct {
   uint64_t fp32_matvecs;           /* FP32 operator applications            */
   uint64_t fp64_matvecs;           /* FP64 operator applications            */
   uint64_t df_matvecs;             /* paired-FP32 operator applications     */
+  uint64_t fp32_bulk_matvecs;      /* FP32 applications whose Z pass staged its
+                                      tiles by bulk copies (TMA)            */
 } ori_plan_stats;
 
 /* Turn per-kernel CUDA-event timing on (1) or off (0).  With timing on, every
@@ -457,7 +459,9 @@ typedef struct {
  * solver's synchronisation points, and at ori_plan_get_stats.  Timing adds
  * an event record between kernels; leave it off outside measurements. */
 ori_status ori_plan_set_timing(ori_plan_t plan, int on);
-/* Copy the counters (synchronises the plan's stream). */
+/* Copy the counters (synchronises the plan's stream).  Returns ORI_ERR_CUDA
+ * (counters still copied) when a kernel gave up waiting for a bulk copy since
+ * the last check; solver calls check the same at their synchronisation points. */
 ori_status ori_plan_get_stats(ori_plan_t plan, ori_plan_stats* out);
 /* Zero the counters. */
 ori_status ori_plan_reset_stats(ori_plan_t plan);

@@ -13,7 +13,7 @@ import os
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libori.so")
 
-ABI_VERSION = 5   # ORI_ABI_VERSION of include/ori.h that these declarations follow
+ABI_VERSION = 6   # ORI_ABI_VERSION of include/ori.h that these declarations follow
 
 ORI_OK = 0
 ORI_ERR_INVALID_ARG = 1
@@ -105,7 +105,8 @@ class Schedule(C.Structure):
 class PlanStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_uint64), ("pass_ms", C.c_double * 24),
                 ("pass_count", C.c_uint64 * 24), ("fp32_matvecs", C.c_uint64),
-                ("fp64_matvecs", C.c_uint64), ("df_matvecs", C.c_uint64)]
+                ("fp64_matvecs", C.c_uint64), ("df_matvecs", C.c_uint64),
+                ("fp32_bulk_matvecs", C.c_uint64)]
 
     def as_dict(self):
         return {
@@ -115,6 +116,7 @@ class PlanStats(C.Structure):
             "fp32_matvecs": int(self.fp32_matvecs),
             "fp64_matvecs": int(self.fp64_matvecs),
             "df_matvecs": int(self.df_matvecs),
+            "fp32_bulk_matvecs": int(self.fp32_bulk_matvecs),
         }
 
 

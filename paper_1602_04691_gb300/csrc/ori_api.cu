@@ -2,11 +2,13 @@
 // (FP64, and mixed FP32 / FP64-class refinement), batched solves over several
 // incidence directions and wave numbers, and the adjoint gradient.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -99,6 +101,13 @@ struct ori_plan_s {
   cpx<float>* tw32 = nullptr;
   cpx<dfl>* twdf = nullptr;
   unsigned long long* d_count = nullptr;
+  int* d_fault = nullptr;          // set by a kernel whose bounded wait on a bulk copy gave up
+  int* h_fault = nullptr;          // pinned mirror
+  // tensor map of the FP32 Z pass's input rows (bulk-copy staging), for T2f
+  // and a batch of zmap_R right-hand sides
+  CUtensorMap zmap{};
+  const void* zmap_ptr = nullptr;
+  int zmap_R = 0, zmap_ok = 0, zbox = 0;
   // batch capacity: pass scratch and solver state for cap right-hand sides
   int cap = 0;
   cpx<float>* T1f = nullptr;
@@ -325,9 +334,11 @@ static void plan_free(ori_plan_s* p) {
   cudaDeviceSynchronize();
   free_capacity(p);
   void* ptrs[] = {p->h, p->N, p->w64, p->S64, p->Sinv, p->w32, p->S32, p->wdf, p->Sdf,
-                  p->ghat64, p->ghat32, p->ghatdf, p->ghatZ32, p->tw64, p->tw32, p->twdf, p->d_count};
+                  p->ghat64, p->ghat32, p->ghatdf, p->ghatZ32, p->tw64, p->tw32, p->twdf, p->d_count,
+                  p->d_fault};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (p->h_fault) cudaFreeHost(p->h_fault);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->evj) cudaEventDestroy(p->evj);
@@ -378,6 +389,65 @@ struct Mask {
   int stride = 0;               // bytes
 };
 
+static ori_status check_fault(ori_plan_s* p);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Whether the FP32 Z pass stages its tiles by bulk copies: the pipelined
+// kernel with 16-column tiles (ZPipe::TMA), given a valid tensor map.
+static bool z_bulk_staged(const ori_plan_s* p) {
+  const int L = p->L;
+  if (!p->zmap_ok || L < 64 || L > 1024 || p->sched_z == SCHED_TILES) return false;
+  return !(has_pipe_variants(L) && p->var_z == 1);
+}
+
+// The tensor map of the FP32 Z pass's input: T2f seen as [rhs][z][ky][kx]
+// with dims (kx: L, ky: L, z: n, rhs: R), 8-byte elements, boxes of
+// 16 x 1 x zbox x 1 (128-byte rows; zbox = min(L / 2, 256), so that the boxes
+// covering z < n end within the tile's L / 2 + 1 staged rows).  Encoded when
+// T2f or the batch size changes; without an encoder, an aligned base or a
+// length the kernel stages by bulk copies, the kernel keeps cp.async.
+static void z_tensor_map(ori_plan_s* p, SArgs& z, int nrhs) {
+  const int R = std::max(1, nrhs);
+  if (p->zmap_ptr != p->T2f || p->zmap_R != R) {
+    p->zmap_ok = 0;
+    p->zmap_ptr = p->T2f;
+    p->zmap_R = R;
+    const int L = p->L;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc != nullptr && L >= 64 && L <= 1024 && (reinterpret_cast<uintptr_t>(p->T2f) & 15u) == 0) {
+      const cuuint64_t es = sizeof(cpx<float>);
+      const cuuint64_t dims[4] = {cuuint64_t(L), cuuint64_t(L), cuuint64_t(p->n), cuuint64_t(R)};
+      const cuuint64_t strides[3] = {cuuint64_t(L) * es, cuuint64_t(L) * L * es, cuuint64_t(t2_elems(p)) * es};
+      const int zbox = std::min(L / 2, 256);
+      const cuuint32_t box[4] = {cuuint32_t(kZGroup), 1, cuuint32_t(zbox), 1};
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      if (enc(&p->zmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, p->T2f, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+        p->zmap_ok = 1;
+        p->zbox = zbox;
+      }
+    }
+  }
+  z.zrows = p->zmap;
+  z.zrows_ok = p->zmap_ok;
+  z.zbox = p->zbox;
+  z.err = p->d_fault;
+}
+
 template <class T>
 static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s, Mask mask,
                            int nrhs = 1, int rhs_per_k = 1) {
@@ -423,6 +493,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   z.bs_ghatZ = (long long)p->H * p->H * p->L * (long long)sizeof(cpx<float>);
   z.rhs_per_ghat = rhs_per_k;
   z.sched = p->sched_z; z.cta_cap = p->cta_cap; z.variant = p->var_z;
+  if (f32) z_tensor_map(p, z, nrhs);
   ORI_CUDA(run_strided<T>(L, SMODE_ZCONV, true, z, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + K, e0, e1); e0 = e1;
@@ -446,6 +517,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_XINV + K, e0, e1);
   if (!p->capturing) {
     if (K == 0) p->stats.fp32_matvecs += nrhs;
+    if (K == 0 && z_bulk_staged(p)) p->stats.fp32_bulk_matvecs += nrhs;
     else if (K == ORI_PASS_FP64) p->stats.fp64_matvecs += nrhs;
     else p->stats.df_matvecs += nrhs;
   }
@@ -778,8 +850,14 @@ static ori_status plan_create(int64_t n, double k, const ori_domain* dom, const 
         (st = alloc_n(p, &p->ghatdf, nk * H3)) ||
         (st = alloc_n(p, &p->ghatZ32, nk * size_t(p->H) * p->H * p->L)) ||
         (st = alloc_n(p, &p->tw64, size_t(p->L))) || (st = alloc_n(p, &p->tw32, size_t(p->L))) ||
-        (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)))
+        (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)) ||
+        (st = alloc_n(p, &p->d_fault, 1)))
       break;
+    if (cudaMemset(p->d_fault, 0, sizeof(int)) != cudaSuccess || cudaMallocHost(&p->h_fault, sizeof(int)) != cudaSuccess) {
+      st = fail(ORI_ERR_CUDA, "fault flag");
+      break;
+    }
+    *p->h_fault = 0;
     unsigned bx32 = 0, bx64 = 0, bxdf = 0;
     if ((st = setup_kernels<float>(p->L, &bx32, p->n, p->sm_count)) ||
         (st = setup_kernels<double>(p->L, &bx64, p->n, p->sm_count)) ||
@@ -924,10 +1002,11 @@ ori_status ori_plan_set_timing(ori_plan_t p, int on) {
 
 ori_status ori_plan_get_stats(ori_plan_t p, ori_plan_stats* out) {
   if (!p || !out) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
+  ORI_CUDA(cudaMemcpyAsync(p->h_fault, p->d_fault, sizeof(int), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   if (p->timing) t_harvest(p);
   *out = p->stats;
-  return ORI_OK;
+  return check_fault(p);
 }
 
 ori_status ori_plan_reset_stats(ori_plan_t p) {
@@ -1050,9 +1129,20 @@ struct InnerResult {
 static ori_status read_heads(ori_plan_s* p, int nrhs) {
   ORI_CUDA(cudaMemcpy2DAsync(p->h_sc, sizeof(Scalars), p->sc, sizeof(Scalars), offsetof(Scalars, hist),
                              size_t(nrhs), cudaMemcpyDeviceToHost, p->ps));
+  ORI_CUDA(cudaMemcpyAsync(p->h_fault, p->d_fault, sizeof(int), cudaMemcpyDeviceToHost, p->ps));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   if (p->timing) t_harvest(p);
-  return ORI_OK;
+  return check_fault(p);
+}
+
+// After a synchronisation that brought d_fault to h_fault: a kernel that gave
+// up waiting for a bulk copy makes the call fail (the flag is cleared).
+static ori_status check_fault(ori_plan_s* p) {
+  if (*p->h_fault == 0) return ORI_OK;
+  *p->h_fault = 0;
+  ORI_CUDA(cudaMemsetAsync(p->d_fault, 0, sizeof(int), p->ps));
+  ORI_CUDA(cudaStreamSynchronize(p->ps));
+  return fail(ORI_ERR_CUDA, "a bulk copy into shared memory did not complete within its time limit");
 }
 
 // COCG on B x_r = r_r for every right-hand side r of the batch (r holds the
@@ -1153,8 +1243,12 @@ static ori_status cocg_inner(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, 
     res[i].relres_recur = p->h_sc[i].rnorm2_0 > 0 ? std::sqrt(p->h_sc[i].rnorm2 / p->h_sc[i].rnorm2_0) : 0.0;
     if (use_graph && res[i].iters > 1) real_matvecs += res[i].iters - 1;   // ran inside replayed graphs
   }
-  if (sizeof(T) == 4) p->stats.fp32_matvecs += real_matvecs;
-  else p->stats.fp64_matvecs += real_matvecs;
+  if (sizeof(T) == 4) {
+    p->stats.fp32_matvecs += real_matvecs;
+    if (z_bulk_staged(p)) p->stats.fp32_bulk_matvecs += real_matvecs;
+  } else {
+    p->stats.fp64_matvecs += real_matvecs;
+  }
   (void)graph_iters_total;
   return ORI_OK;
 }

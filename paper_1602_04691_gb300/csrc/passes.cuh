@@ -26,6 +26,8 @@
 
 #include "common.cuh"
 
+#include <cuda.h>   // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
+
 #include <algorithm>
 
 namespace ori {
@@ -122,6 +124,13 @@ struct SArgs {
   int sched;
   int cta_cap;
   int variant;                     // pipelined FP32 kernels: launch variant (has_pipe_variants)
+  // FP32 Z pass with 16-column tiles: the input rows of a tile arrive by TMA
+  // (cp.async.bulk.tensor) through this map of the input cube, dims (kx, ky,
+  // z, right-hand side), box (16, 1, zbox, 1); zrows_ok = 0 keeps cp.async
+  CUtensorMap zrows;
+  int zrows_ok;
+  int zbox;
+  int* err;                        // set to 1 when a bounded wait on a copy gave up
 };
 
 enum { SCHED_PERSISTENT = 0, SCHED_TILES = 1 };

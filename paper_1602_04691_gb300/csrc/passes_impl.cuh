@@ -19,6 +19,57 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Bulk copies (TMA) into shared memory with mbarrier completion.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return unsigned(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// orders this thread's earlier shared-memory accesses before later async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase `parity` of a barrier: false once kMbarWaitNs
+// have passed (or kMbarTries unsuccessful tries, should the timer stand still).
+constexpr unsigned long long kMbarWaitNs = 2000000000ull;
+constexpr int kMbarTries = 1 << 26;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (int i = 0; i < kMbarTries; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kMbarWaitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 // z * w (SIGN > 0) or z * conj(w) (SIGN < 0) for a twiddle value w already loaded.
 template <int SIGN, class T>
 __device__ __forceinline__ cpx<T> tw_mul_val(cpx<T> z, cpx<T> w) {
@@ -1079,11 +1130,50 @@ struct ZPipe {
   using TL = Tile<L, C, T, L1X>;
   static constexpr int NT = TL::NT;
   static constexpr bool GZ = sizeof(T) == 4;              // spectrum staged through smem
+  // 128-byte rows of the input and of the Z-tile-ordered spectrum: both
+  // arrive by bulk copy (TMA) when the host supplied the tensor map
+  static constexpr bool TMA = GZ && C == kZGroup;
   static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
   static constexpr size_t S_ELEMS = size_t(L / 2 + (GZ ? 1 : 0)) * C;  // input rows / spectrum slice
   static constexpr size_t TW_ELEMS = GZ ? size_t(L) : 0;                // twiddle table copy
-  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + TW_ELEMS) * sizeof(cpx<T>);
+  // with TMA: 128 bytes of slack to align the tile to 128 bytes, and the mbarrier
+  static constexpr size_t TMA_BYTES = TMA ? 128 + 16 : 0;
+  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + TW_ELEMS) * sizeof(cpx<T>) + TMA_BYTES;
 };
+
+// Bulk-copy staging of the FP32 Z pass (ZPipe::TMA).  Thread 0 issues the
+// copies; every thread waits on the barrier.  The n_in input rows of a tile,
+// 128 bytes each, come as ceil(n_in / zbox) boxes of zbox rows through the
+// tensor map a.zrows (rows past n_in are zero-filled; zbox is a power of two
+// dividing L / 2 or equal to it, so the boxes end within the L / 2 + 1 rows of S).
+template <int L, int C>
+__device__ __forceinline__ void zpipe_tma_rows(const SArgs& a, int tile, int per_rhs, cpx<float>* S,
+                                               unsigned long long* bar) {
+  const int col_blocks = L / C;
+  const int rhs = tile / per_rhs;
+  const int tl = tile - rhs * per_rhs;
+  const int ky = ky_of_slot(tl / col_blocks, L);
+  const int cb = tl % col_blocks;
+  const int nbox = (a.n_in + a.zbox - 1) / a.zbox;
+  fence_proxy_async();
+  mbar_expect_tx(bar, unsigned(nbox * a.zbox * C * int(sizeof(cpx<float>))));
+  for (int q = 0; q < nbox; ++q) tma_load_4d(S + q * a.zbox * C, &a.zrows, cb * C, ky, q * a.zbox, rhs, bar);
+}
+// The spectrum slice of a tile: with C == kZGroup the L / 2 + 1 rows of C
+// entries are one contiguous run of the Z-tile-ordered spectrum.
+template <int L, int C>
+__device__ __forceinline__ void zpipe_tma_ghat(const SArgs& a, int rhs, int ky, int cb, cpx<float>* S,
+                                               unsigned long long* bar) {
+  static_assert(C == kZGroup, "one contiguous run per tile");
+  const int my = mirror_index(ky, L);
+  const int g = a.rhs_per_ghat > 0 ? rhs / a.rhs_per_ghat : 0;
+  const cpx<float>* src = reinterpret_cast<const cpx<float>*>(bmove(a.ghatZ, a.bs_ghatZ * g)) +
+                          ((long long)my * (L / kZGroup) + cb) * (L / 2 + 1) * kZGroup;
+  constexpr unsigned bytes = unsigned(L / 2 + 1) * C * unsigned(sizeof(cpx<float>));
+  fence_proxy_async();
+  mbar_expect_tx(bar, bytes);
+  bulk_load(S, src, bytes, bar);
+}
 
 template <class T, int L, int C, int L1X>
 __device__ __forceinline__ void zpipe_prefetch(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
@@ -1152,16 +1242,19 @@ __device__ __forceinline__ void zpipe_prefetch_ghat(const SArgs& a, int rhs, int
 template <class T, int L, int C, int L1X = Split<L>::L1>
 __global__ void __launch_bounds__(ZPipe<L, C, T, L1X>::NT,
                                   (ZPipe<L, C, T, L1X>::NT <= 256 && sizeof(T) == 4 && L <= 1024 && L1X < 64) ? 2 : 1)
-k_zconv_pipe(SArgs a) {
+k_zconv_pipe(const __grid_constant__ SArgs a) {
   using TL = Tile<L, C, T, L1X>;
   using ZP = ZPipe<L, C, T, L1X>;
   constexpr bool GZ = ZP::GZ;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PK = TL::PK, PC = TL::PC, PKI = TL::PKI, PCI = TL::PCI;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* base = smraw;
+  if constexpr (ZP::TMA) base += (128u - (smem_addr(smraw) & 127u)) & 127u;   // E, S: 128-byte aligned
+  cpx<T>* E = reinterpret_cast<cpx<T>*>(base);
   cpx<T>* S = E + ZP::E_ELEMS;
   cpx<T>* TWS = S + ZP::S_ELEMS;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(TWS + ZP::TW_ELEMS);
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
   if (GZ) fill_tw2<L, L2>(TWS, twg, threadIdx.x, NT);   // [k1][j] layout
   const cpx<T>* tw = GZ ? TWS : twg;
@@ -1171,17 +1264,55 @@ k_zconv_pipe(SArgs a) {
   const int step = gridDim.x;
   const int tid = threadIdx.x;
   const int c = tid % C, jl = tid / C;
+  const bool tma = ZP::TMA && a.zrows_ok != 0;   // uniform over the grid
+  unsigned phase = 0;                            // parity of the barrier phase awaited next
+  if (tma) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  // Wait for the staged copy (bulk copies: bounded; a copy that has not
+  // landed after kMbarWaitNs sets *a.err and the CTA leaves after one more
+  // bounded wait for it).  Also the barrier that ends the use of E by the
+  // previous step.  Returns false when the CTA must leave.
+  auto staged = [&]() -> bool {
+    if constexpr (ZP::TMA) {
+      if (tma) {
+        const bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0 && a.err != nullptr) atomicExch(a.err, 1);
+          if (!ok) mbar_wait(bar, phase);
+          return false;
+        }
+        phase ^= 1u;
+        return true;
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    return true;
+  };
+  auto stage_rows = [&](int t) {
+    if constexpr (ZP::TMA) {
+      if (tma) {
+        if (tid == 0) zpipe_tma_rows<L, C>(a, t, per_rhs, reinterpret_cast<cpx<float>*>(S), bar);
+        return;
+      }
+    }
+    zpipe_prefetch<T, L, C, L1X>(a, t, per_rhs, S);
+  };
 
   int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
-  if (tile < ntiles) zpipe_prefetch<T, L, C, L1X>(a, tile, per_rhs, S);
+  if (tile < ntiles) stage_rows(tile);
   while (tile < ntiles) {
     const int rhs = tile / per_rhs;
     const int tl = tile - rhs * per_rhs;
     const int ky = ky_of_slot(tl / col_blocks, L);
     const int cb = tl % col_blocks;
     const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
-    cp_async_wait_all();
-    __syncthreads();   // staged rows visible; previous tile done with E
+    if (!staged()) return;   // staged rows visible; previous tile done with E
     // stage 1: DFT over j1 of rows j1*L2 + j2 (zero padded beyond n_in)
     cpx<T> r[L1];
 #pragma unroll
@@ -1193,8 +1324,17 @@ k_zconv_pipe(SArgs a) {
       }
     }
     __syncthreads();   // staging buffer consumed
-    if (GZ) zpipe_prefetch_ghat<T, L, C, L1X>(a, rhs, ky, cb, S);
-    else if (next < ntiles) zpipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
+    if constexpr (ZP::TMA) {
+      if (tma) {
+        if (tid == 0) zpipe_tma_ghat<L, C>(a, rhs, ky, cb, reinterpret_cast<cpx<float>*>(S), bar);
+      } else {
+        zpipe_prefetch_ghat<T, L, C, L1X>(a, rhs, ky, cb, S);
+      }
+    } else if (GZ) {
+      zpipe_prefetch_ghat<T, L, C, L1X>(a, rhs, ky, cb, S);
+    } else if (next < ntiles) {
+      zpipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
+    }
     dft<L1, -1, true>(r);
     if (GZ) {
       const cpx<T>* t2 = tw + jl;
@@ -1206,8 +1346,11 @@ k_zconv_pipe(SArgs a) {
     }
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) E[c * PC + k1 * PK + jl] = r[k1];
-    if (GZ) cp_async_wait_all();
-    __syncthreads();
+    if (GZ) {
+      if (!staged()) return;   // spectrum slice visible
+    } else {
+      __syncthreads();
+    }
     // stage 2 (DFT over j2), spectrum, inverse stage A (DFT over k2)
     cpx<T> b[NI][L2];
     const int my = mirror_index(ky, L);
@@ -1248,7 +1391,7 @@ k_zconv_pipe(SArgs a) {
       }
     }
     __syncthreads();   // forward exchange and the spectrum slice fully read
-    if (GZ && next < ntiles) zpipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
+    if (GZ && next < ntiles) stage_rows(next);
 #pragma unroll
     for (int it = 0; it < NI; ++it) {
       const int s = tid + it * NT;

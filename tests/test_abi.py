@@ -42,7 +42,7 @@ def test_binding_declares_every_export(libpath):
     from paper_1602_04691_gb300 import _lib
     assert sorted(_lib.EXPORTS) == _declared()
     lib = _lib.load()
-    assert lib.ori_abi_version() == 5
+    assert lib.ori_abi_version() == 6
     assert lib.ori_status_string(0) == b"ok"
     assert lib.ori_status_string(5) == b"COCG breakdown"
 

@@ -203,13 +203,20 @@ def test_every_schedule_matches_oracle_and_autotune_caches(tmp_path):
     assert all(i["relres"] <= 1e-6 for i in infos)
 
 
+def bulk_staged(sch):
+    """1 when the FP32 Z pass runs the persistent kernel with 16-column tiles."""
+    return int(sch["zconv"] == 0 and sch["zconv_variant"] != 1)
+
+
 @pytest.mark.parametrize("n", [100, 200, 260])
 def test_every_launch_variant_matches_oracle(n):
     """The tile-width and radix-split variants of the persistent FP32 Y-forward,
     Z and Y-inverse kernels at L = 256, 512 and 1024 (n = 100, 200, 260): each
     alone, and all at once, give the FP32 operator within 1e-5 of the oracle's
     direct sums on rows of every tile class; a mixed solve meets tol with
-    them."""
+    them.  The 16-column Z tiles are staged by bulk copies (TMA): the plan's
+    counters show it for every such variant and for every FP32 operator
+    application of the solve."""
     k = 3.0
     h, N = inputs.random_h_N(n, 90 + n)
     x = inputs.random_complex(n ** 3, 91 + n).astype(np.complex64)
@@ -226,13 +233,21 @@ def test_every_launch_variant_matches_oracle(n):
     xd = to_dev(x)
     schedules = [dict(default, **{f: v}) for f in ("yfwd_variant", "zconv_variant", "yinv_variant") for v in (1, 2)]
     schedules += [dict(default, yfwd_variant=v, zconv_variant=v, yinv_variant=v) for v in (1, 2)]
-    for sch in schedules:
+    for sch in [default] + schedules:
         plan.set_schedule(sch)
+        plan.reset_stats()
         y = plan.matvec32(xd, form="B").cpu().numpy()
         assert rel(y[rows], ref) < 1e-5, sch
+        # 16-column Z tiles stage their rows and spectrum slices by bulk copies
+        st = plan.stats()
+        assert st["fp32_matvecs"] == 1
+        assert st["fp32_bulk_matvecs"] == bulk_staged(sch), sch
+    plan.set_schedule(default)
+    plan.reset_stats()
     _, info = plan.solve(tol=1e-6, precision="mixed")
     assert info["status"] == 0 and info["relres"] <= 1e-6
-    plan.set_schedule(default)
+    st = plan.stats()
+    assert st["fp32_matvecs"] > 0 and st["fp32_bulk_matvecs"] == st["fp32_matvecs"] * bulk_staged(default)
     plan.close()
 
 

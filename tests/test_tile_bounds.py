@@ -6,7 +6,9 @@ Y and Z kernels (8-column tiles; a split with a doubled first radix), every
 shared-memory index the kernels form
 (staged inputs, the exchange between the two DFT stages, the spectrum slice,
 the twiddle table) is enumerated over all threads and loop indices and must
-stay inside its buffer, and each CTA's shared memory must fit in 227 KB.
+stay inside its buffer, and each CTA's shared memory must fit in 227 KB.  The
+bulk-copy staging of the FP32 Z kernel is checked against the alignment and
+size rules of the copies it issues.
 
 The tile shapes below restate passes.cuh (Tile), common.cuh (Split) and
 passes_impl.cuh (ZPipe, YPipe, YInvPipe, XFwdPipe, XInvPipe, the launchers'
@@ -91,6 +93,40 @@ def test_zconv_pipe_indices(L, C, L1v):
     tid, k1 = grid(NT, L1)
     c, jl = tid % C, tid // C
     assert (c * PCI + jl * PKI + k1).max() < E                       # inverse exchange load
+
+
+TMA_YZ = [(L, C, L1v) for L, C, L1v in YZ if C == 16 and L <= 1024]
+
+
+@pytest.mark.parametrize("L,C,L1v", TMA_YZ)
+def test_zconv_bulk_copy_staging(L, C, L1v):
+    """The bulk-copy (TMA) staging of the FP32 Z kernel with 16-column tiles:
+    every copy starts and ends on the boundaries the hardware requires, the
+    boxes of input rows end inside the staging buffer for every n <= L/2, and
+    the bytes a barrier phase expects stay below the transaction-count limit."""
+    t = tile(L, C, L1v)
+    E, S, TW = t["SE"], (L // 2 + 1) * C, L
+    assert (E * CB) % 128 == 0                                        # S 128-byte aligned after E
+    assert ((E + S + TW) * CB) % 8 == 0                              # the mbarrier after TW
+    assert (E + S + TW) * CB + 128 + 16 <= SMEM_MAX                  # + alignment slack and barrier
+    zbox = min(L // 2, 256)
+    assert zbox <= 256 and C <= 256 and (C * CB) % 16 == 0           # box limits; inner extent
+    H = L // 2 + 1
+    for n in range(1, L // 2 + 1):
+        nbox = -(-n // zbox)
+        assert nbox * zbox <= L // 2 + 1                              # zero-filled rows stay in S
+        assert nbox * zbox * C * CB < 1 << 20                         # expect_tx limit
+        for q in range(nbox):
+            assert (q * zbox * C * CB) % 128 == 0                     # destination of box q
+        strides = [L * CB, L * L * CB, n * L * L * CB]                # tensor map strides
+        assert all(st % 16 == 0 and st < 1 << 40 for st in strides)
+    cb = np.arange(L // C)
+    assert np.all((cb * C * CB) % 16 == 0)                            # x coordinate x element size
+    ghat_bytes = (L // 2 + 1) * C * CB
+    assert ghat_bytes % 16 == 0 and ghat_bytes < 1 << 20
+    my = np.arange(H)[:, None]
+    off = ((my * (L // 16) + cb[None, :]) * (L // 2 + 1) * 16 * CB)
+    assert np.all(off % 16 == 0) and (H * H * L * CB) % 16 == 0        # spectrum source, per wave number
 
 
 @pytest.mark.parametrize("L,C,L1v", YZ)
@@ -205,7 +241,15 @@ def _read(name):
                          "B[c2 * PCI + j * PKI + k1] = b[it][j];",
                          "r[k1] = B[c * PCI + ja * PKI + k1];",
                          "b[it][k2] = okl ? B[c2 * L + k1 + L1 * k2] : czero<T>();",
-                         "E[c * PC + k1 * PK + j2] = r[k1];"]),
+                         "E[c * PC + k1 * PK + j2] = r[k1];",
+                         "static constexpr bool TMA = GZ && C == kZGroup;",
+                         "static constexpr size_t TMA_BYTES = TMA ? 128 + 16 : 0;",
+                         "for (int q = 0; q < nbox; ++q) tma_load_4d(S + q * a.zbox * C, &a.zrows, cb * C, ky, q * a.zbox, rhs, bar);",
+                         "constexpr unsigned bytes = unsigned(L / 2 + 1) * C * unsigned(sizeof(cpx<float>));",
+                         "if constexpr (ZP::TMA) base += (128u - (smem_addr(smraw) & 127u)) & 127u;"]),
+    ("ori_api.cu", ["const int zbox = std::min(L / 2, 256);",
+                    "const cuuint32_t box[4] = {cuuint32_t(kZGroup), 1, cuuint32_t(zbox), 1};",
+                    "if (enc != nullptr && L >= 64 && L <= 1024 && (reinterpret_cast<uintptr_t>(p->T2f) & 15u) == 0) {"]),
 ])
 def test_sources_still_define_the_restated_shapes(name, lines):
     src = _read(name)
