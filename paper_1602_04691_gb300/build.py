@@ -1,7 +1,10 @@
 """Build the CUDA library libori.so in-tree for sm_103a.
 
-The three translation units are compiled in parallel with nvcc and linked
-against the shared CUDA runtime (the same libcudart PyTorch loads).  A stamp
+The translation units are compiled in parallel with nvcc and linked against
+the shared CUDA runtime (the same libcudart PyTorch loads).  The FFT passes are
+compiled as twelve units, one per arithmetic and part (passes_inst.cu with
+ORI_PASS_T / ORI_PASS_PART), since their template instances dominate the
+build time.  A stamp
 of the sources and flags skips the build when nothing changed.
 """
 
@@ -20,7 +23,11 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libori.so")
 
-SOURCES = ["ori_api.cu", "ori_noalloc.cu", "passes_f32.cu", "passes_f64.cu", "passes_df.cu"]
+SOURCES = ["ori_api.cu", "ori_noalloc.cu", "passes_inst.cu"]
+# (object name, source, extra flags): passes_inst.cu once per arithmetic T and part
+UNITS = [("ori_api", "ori_api.cu", []), ("ori_noalloc", "ori_noalloc.cu", [])] + [
+    (f"passes_{tn}_{pn}", "passes_inst.cu", [f"-DORI_PASS_T={ti}", f"-DORI_PASS_PART={pi}"])
+    for ti, tn in ((1, "f32"), (2, "f64"), (3, "df")) for pi, pn in ((1, "x"), (2, "yfwd"), (3, "yinv"), (4, "z"))]
 # Every header next to the sources is part of the stamp, so an edit to any of them rebuilds.
 HEADERS = sorted(os.path.basename(f) for f in glob.glob(os.path.join(CSRC, "*.cuh")))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,6 +51,7 @@ def _stamp() -> str:
         with open(path, "rb") as fh:
             h.update(os.path.basename(path).encode() + fh.read())
     h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(repr(UNITS).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -58,18 +66,19 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 return LIB
     nvcc = _nvcc()
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit) -> str:
+        name, src, extra = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{res.stdout}\n{res.stderr}")
+            raise RuntimeError(f"nvcc failed for {name}:\n{res.stdout}\n{res.stderr}")
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(max_workers=min(len(UNITS), max(2, os.cpu_count() or 2))) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     res = subprocess.run(cmd, capture_output=True, text=True)

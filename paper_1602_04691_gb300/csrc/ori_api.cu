@@ -22,12 +22,6 @@
 #include "scalars.cuh"
 #include "vector_kernels.cuh"
 
-namespace ori {
-template <class T> cudaError_t run_xfwd(int, bool, const XArgs&, cudaStream_t, bool);
-template <class T> cudaError_t run_xinv(int, const XArgs&, Scalars*, int, cudaStream_t, bool, unsigned*);
-template <class T> cudaError_t run_strided(int, int, bool, const SArgs&, cudaStream_t, bool);
-}  // namespace ori
-
 using namespace ori;
 
 // NVTX range for profilers (nsys, ncu --nvtx): pushed on construction, popped

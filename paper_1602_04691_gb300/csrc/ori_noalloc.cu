@@ -20,9 +20,6 @@
 
 namespace ori {
 void set_last_error(const std::string& msg);   // ori_api.cu: the ori_last_error() message
-template <class T> cudaError_t run_xfwd(int, bool, const XArgs&, cudaStream_t, bool);
-template <class T> cudaError_t run_xinv(int, const XArgs&, Scalars*, int, cudaStream_t, bool, unsigned*);
-template <class T> cudaError_t run_strided(int, int, bool, const SArgs&, cudaStream_t, bool);
 }  // namespace ori
 
 using namespace ori;

@@ -258,4 +258,26 @@ __device__ __forceinline__ void block_partial_lane0(double2 v, double2* red, dou
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pass launchers.  Each arithmetic T (float, double, dfl) and each part (the
+// X passes, the strided forward and inverse passes, the Z pass) is explicitly
+// instantiated in a translation unit of its own (passes_inst.cu compiled once
+// per pair), so that the library builds in parallel.
+// ---------------------------------------------------------------------------
+struct Scalars;
+template <class T> cudaError_t run_xfwd(int L, bool half, const XArgs& a, cudaStream_t s, bool setup);
+template <class T> cudaError_t run_xinv(int L, const XArgs& a, Scalars* sc, int fin, cudaStream_t s, bool setup,
+                                        unsigned* nblocks);
+template <class T> cudaError_t run_strided_fwd(int L, bool half, const SArgs& a, cudaStream_t s, bool setup);
+template <class T> cudaError_t run_strided_inv(int L, const SArgs& a, cudaStream_t s, bool setup);
+template <class T> cudaError_t run_zconv(int L, const SArgs& a, cudaStream_t s, bool setup);
+
+// One strided pass (SMODE_FWD, SMODE_INV or SMODE_ZCONV) at padded length L.
+template <class T>
+inline cudaError_t run_strided(int L, int smode, bool half, const SArgs& a, cudaStream_t s, bool setup) {
+  if (smode == SMODE_FWD) return run_strided_fwd<T>(L, half, a, s, setup);
+  if (smode == SMODE_INV) return run_strided_inv<T>(L, a, s, setup);
+  return run_zconv<T>(L, a, s, setup);
+}
+
 }  // namespace ori

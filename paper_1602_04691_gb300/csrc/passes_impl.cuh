@@ -1997,14 +1997,31 @@ cudaError_t run_xinv(int L, const XArgs& a, Scalars* sc, int fin, cudaStream_t s
 }
 
 template <class T>
-cudaError_t run_strided(int L, int smode, bool half, const SArgs& a, cudaStream_t s, bool setup) {
+cudaError_t run_strided_fwd(int L, bool half, const SArgs& a, cudaStream_t s, bool setup) {
   switch (L) {
-#define ORI_CASE(LL)                                                                        \
-    case LL:                                                                                \
-      if (smode == SMODE_FWD) return half ? launch_strided_L<T, LL, SMODE_FWD, true>(a, s, setup) \
-                                          : launch_strided_L<T, LL, SMODE_FWD, false>(a, s, setup); \
-      if (smode == SMODE_INV) return launch_strided_L<T, LL, SMODE_INV, false>(a, s, setup); \
-      return launch_zconv_L<T, LL>(a, s, setup);
+#define ORI_CASE(LL) \
+    case LL: return half ? launch_strided_L<T, LL, SMODE_FWD, true>(a, s, setup) \
+                         : launch_strided_L<T, LL, SMODE_FWD, false>(a, s, setup);
+    ORI_FOR_EACH_L(ORI_CASE)
+#undef ORI_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T>
+cudaError_t run_strided_inv(int L, const SArgs& a, cudaStream_t s, bool setup) {
+  switch (L) {
+#define ORI_CASE(LL) case LL: return launch_strided_L<T, LL, SMODE_INV, false>(a, s, setup);
+    ORI_FOR_EACH_L(ORI_CASE)
+#undef ORI_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class T>
+cudaError_t run_zconv(int L, const SArgs& a, cudaStream_t s, bool setup) {
+  switch (L) {
+#define ORI_CASE(LL) case LL: return launch_zconv_L<T, LL>(a, s, setup);
     ORI_FOR_EACH_L(ORI_CASE)
 #undef ORI_CASE
     default: return cudaErrorInvalidValue;
