@@ -10,7 +10,9 @@
 //   inverse: decimation in time, digit-reversed in, natural order out
 //
 // so a forward transform, a pointwise product (indexed through the digit
-// reversal) and an inverse need no reordering pass.
+// reversal) and an inverse need no reordering pass.  The X inverse pass,
+// whose input comes in natural order from global memory, runs the DIF
+// stages with the inverse sign instead and gathers its outputs.
 #pragma once
 
 #include "dfloat.cuh"
@@ -115,20 +117,20 @@ __device__ __forceinline__ void dit_stage(cpx<T>* X, int M, const cpx<T>* tw, in
   }
 }
 
-// Forward DIF stages after the first one (which the callers fuse with their
-// loads): block sizes L/8, L/64, ...
-template <int L, int C, class T>
+// DIF stages after the first one (which the callers fuse with their loads):
+// block sizes L/8, L/64, ...  SIGN -1: forward transform; +1: inverse.
+template <int L, int C, int SIGN = -1, class T>
 __device__ __forceinline__ void dif_rest(cpx<T>* X, const cpx<T>* tw, int tid, int nt) {
   using DR = DRad<L>;
   int M = L / 8;
 #pragma unroll 1
   for (int st = 1; st < DR::NST8; ++st) {
-    dif_stage<8, -1, L, C>(X, M, tw, tid, nt);
+    dif_stage<8, SIGN, L, C>(X, M, tw, tid, nt);
     __syncthreads();
     M /= 8;
   }
   if constexpr (DR::RL > 1) {
-    dif_stage<DR::RL, -1, L, C>(X, M, tw, tid, nt);
+    dif_stage<DR::RL, SIGN, L, C>(X, M, tw, tid, nt);
     __syncthreads();
   }
 }

@@ -97,6 +97,14 @@ struct ori_plan_s {
   unsigned long long* d_count = nullptr;
   int* d_fault = nullptr;          // set by a kernel whose bounded wait on a bulk copy gave up
   int* h_fault = nullptr;          // pinned mirror
+  unsigned long long* h_count = nullptr;   // pinned mirror of d_count
+  // device addresses of the pinned mirrors (mapped host memory): the control
+  // copies between them and device memory run as kernels (k_small_copy)
+  void* h_fault_d = nullptr;
+  void* h_count_d = nullptr;
+  void* h_sc_d = nullptr;
+  void* h_small_d = nullptr;
+  void* h_skip_d = nullptr;
   // tensor map of the FP32 Z pass's input rows (bulk-copy staging), for T2f
   // and a batch of zmap_R right-hand sides
   CUtensorMap zmap{};
@@ -281,6 +289,7 @@ static void free_capacity(ori_plan_s* p) {
   p->h_sc = nullptr;
   p->h_small = nullptr;
   p->h_skip = nullptr;
+  p->h_sc_d = p->h_small_d = p->h_skip_d = nullptr;
   p->cap = 0;
   drop_graphs(p);
 }
@@ -315,6 +324,10 @@ static ori_status ensure_capacity(ori_plan_s* p, int nrhs) {
       cudaMallocHost(&p->h_small, 7 * c * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&p->h_skip, c * sizeof(int)) != cudaSuccess)
     return fail(ORI_ERR_OOM, "cudaMallocHost failed");
+  if (cudaHostGetDevicePointer(&p->h_sc_d, p->h_sc, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&p->h_small_d, p->h_small, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer(&p->h_skip_d, p->h_skip, 0) != cudaSuccess)
+    return fail(ORI_ERR_CUDA, "cudaHostGetDevicePointer failed (pinned memory not mapped)");
   std::memset(p->h_sc, 0, c * sizeof(Scalars));
   p->cap = nrhs;
   return ORI_OK;
@@ -333,6 +346,7 @@ static void plan_free(ori_plan_s* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_fault) cudaFreeHost(p->h_fault);
+  if (p->h_count) cudaFreeHost(p->h_count);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   if (p->evj) cudaEventDestroy(p->evj);
@@ -532,6 +546,40 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
 // Blocks per right-hand side of the vector kernels.
 static int vgrid(const ori_plan_s* p, int nrhs) { return std::max(16, p->vec_grid / std::max(1, nrhs)); }
 
+// Control copy on the plan's stream by k_small_copy (rows of `bytes` at the
+// given pitches); dst and src are device addresses (device memory or the
+// mapped address of a pinned mirror).
+static ori_status small_copy(ori_plan_s* p, void* dst, const void* src, size_t bytes, int rows = 1,
+                             size_t dpitch = 0, size_t spitch = 0) {
+  k_small_copy<<<1, 256, 0, p->ps>>>(static_cast<const unsigned char*>(src), static_cast<unsigned char*>(dst),
+                                     (long long)bytes, (long long)(spitch ? spitch : bytes),
+                                     (long long)(dpitch ? dpitch : bytes), rows);
+  ORI_CUDA(cudaGetLastError());
+  launched(p);
+  return ORI_OK;
+}
+
+// Device-to-device copy by k_copy16 (16-byte words) and k_small_copy (the
+// tail); buffers not 16-byte aligned (a caller's offset view) take
+// cudaMemcpyAsync.
+static ori_status dev_copy(ori_plan_s* p, void* dst, const void* src, size_t bytes) {
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) != 0) {
+    ORI_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, p->ps));
+    return ORI_OK;
+  }
+  const size_t n16 = bytes / 16;
+  if (n16 > 0) {
+    k_copy16<<<p->vec_grid, 256, 0, p->ps>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst),
+                                             (long long)n16);
+    ORI_CUDA(cudaGetLastError());
+    launched(p);
+  }
+  if (bytes % 16)
+    ORI_TRY(small_copy(p, static_cast<unsigned char*>(dst) + 16 * n16, static_cast<const unsigned char*>(src) + 16 * n16,
+                       bytes % 16));
+  return ORI_OK;
+}
+
 template <class T>
 static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n, int sm_count) {
   XArgs a{};
@@ -551,18 +599,19 @@ static ori_status setup_kernels(int L, unsigned* xinv_blocks, int n, int sm_coun
 static ori_status set_medium(ori_plan_s* p, const double* h_dev, const double* N_dev) {
   const size_t n3 = size_t(p->n3);
   const cpx<double>* h = reinterpret_cast<const cpx<double>*>(h_dev);
-  const double* N = N_dev;
-  if (!p->lean) {   // a lean plan keeps no copy of h and N (no adjoint, no field)
-    ORI_CUDA(cudaMemcpyAsync(p->h, h_dev, n3 * sizeof(cpx<double>), cudaMemcpyDeviceToDevice, p->ps));
-    ORI_CUDA(cudaMemcpyAsync(p->N, N_dev, n3 * sizeof(double), cudaMemcpyDeviceToDevice, p->ps));
-    h = p->h;
-    N = p->N;
-  }
+  // the plan's copies of h and N (a lean plan keeps none: no adjoint, no field)
+  // are written by the same pass; h_dev may alias them (set_medium(p->h, p->N))
+  const bool copy = !p->lean && h != p->h;
+  if (!p->lean && !copy && N_dev != p->N)
+    ORI_TRY(dev_copy(p, p->N, N_dev, n3 * sizeof(double)));
   ORI_CUDA(cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), p->ps));
-  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(h, N, p->w64, p->S64, p->w32, p->S32,
+  ORI_VEC(p, ORI_PASS_VECTOR, (k_medium<<<p->vec_grid, 256, 0, p->ps>>>(h, N_dev, copy ? p->h : nullptr,
+                                                                        copy && N_dev != p->N ? p->N : nullptr,
+                                                                        p->w64, p->S64, p->w32, p->S32,
                                                                         p->Sinv, p->wdf, p->Sdf, p->n3, p->d_count)));
-  ORI_CUDA(cudaMemcpyAsync(&p->zero_S, p->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p->ps));
+  ORI_TRY(small_copy(p, p->h_count_d, p->d_count, sizeof(unsigned long long)));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
+  p->zero_S = *p->h_count;
   if (p->lean && p->zero_S != 0)
     return fail(ORI_ERR_UNSUPPORTED, "a lean plan needs h N != 0 in every cell (no FP64 recovery of S = 0 cells)");
   return ORI_OK;
@@ -847,11 +896,15 @@ static ori_status plan_create(int64_t n, double k, const ori_domain* dom, const 
         (st = alloc_n(p, &p->twdf, size_t(p->L))) || (st = alloc_n(p, &p->d_count, 1)) ||
         (st = alloc_n(p, &p->d_fault, 1)))
       break;
-    if (cudaMemset(p->d_fault, 0, sizeof(int)) != cudaSuccess || cudaMallocHost(&p->h_fault, sizeof(int)) != cudaSuccess) {
+    if (cudaMemset(p->d_fault, 0, sizeof(int)) != cudaSuccess || cudaMallocHost(&p->h_fault, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&p->h_count, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaHostGetDevicePointer(&p->h_fault_d, p->h_fault, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(&p->h_count_d, p->h_count, 0) != cudaSuccess) {
       st = fail(ORI_ERR_CUDA, "fault flag");
       break;
     }
     *p->h_fault = 0;
+    *p->h_count = 0;
     unsigned bx32 = 0, bx64 = 0, bxdf = 0;
     if ((st = setup_kernels<float>(p->L, &bx32, p->n, p->sm_count)) ||
         (st = setup_kernels<double>(p->L, &bx64, p->n, p->sm_count)) ||
@@ -996,7 +1049,7 @@ ori_status ori_plan_set_timing(ori_plan_t p, int on) {
 
 ori_status ori_plan_get_stats(ori_plan_t p, ori_plan_stats* out) {
   if (!p || !out) return fail(ORI_ERR_INVALID_ARG, "NULL argument");
-  ORI_CUDA(cudaMemcpyAsync(p->h_fault, p->d_fault, sizeof(int), cudaMemcpyDeviceToHost, p->ps));
+  ORI_TRY(small_copy(p, p->h_fault_d, p->d_fault, sizeof(int)));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   if (p->timing) t_harvest(p);
   *out = p->stats;
@@ -1121,9 +1174,8 @@ struct InnerResult {
 
 // Copy the scalar heads of all right-hand sides to the pinned mirror.
 static ori_status read_heads(ori_plan_s* p, int nrhs) {
-  ORI_CUDA(cudaMemcpy2DAsync(p->h_sc, sizeof(Scalars), p->sc, sizeof(Scalars), offsetof(Scalars, hist),
-                             size_t(nrhs), cudaMemcpyDeviceToHost, p->ps));
-  ORI_CUDA(cudaMemcpyAsync(p->h_fault, p->d_fault, sizeof(int), cudaMemcpyDeviceToHost, p->ps));
+  ORI_TRY(small_copy(p, p->h_sc_d, p->sc, offsetof(Scalars, hist), nrhs, sizeof(Scalars), sizeof(Scalars)));
+  ORI_TRY(small_copy(p, p->h_fault_d, p->d_fault, sizeof(int)));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   if (p->timing) t_harvest(p);
   return check_fault(p);
@@ -1150,7 +1202,7 @@ static ori_status cocg_inner(ori_plan_s* p, int nrhs, int rhs_per_k, cpx<T>* x, 
   NvtxRange nvtx(sizeof(T) == 4 ? "ori cocg fp32" : "ori cocg fp64");
   double* h_tols = p->h_small;
   for (int i = 0; i < nrhs; ++i) h_tols[i] = tols_host[i];
-  ORI_CUDA(cudaMemcpyAsync(p->d_tols, h_tols, nrhs * sizeof(double), cudaMemcpyHostToDevice, p->ps));
+  ORI_TRY(small_copy(p, p->d_tols, p->h_small_d, nrhs * sizeof(double)));   // h_tols is h_small
   const int vg = vgrid(p, nrhs);
   ORI_VEC(p, ORI_PASS_VECTOR + (sizeof(T) == 4 ? 0 : ORI_PASS_FP64),
           (k_cocg_init<T><<<dim3(vg, nrhs), 256, 0, p->ps>>>(r, x, p->n3, p->sc, p->partials, p->d_tols, maxit,
@@ -1291,13 +1343,13 @@ static ori_status status_of(int done) {
 }
 
 static ori_status push_skip(ori_plan_s* p, int nrhs) {
-  ORI_CUDA(cudaMemcpyAsync(p->d_skip, p->h_skip, nrhs * sizeof(int), cudaMemcpyHostToDevice, p->ps));
+  ORI_TRY(small_copy(p, p->d_skip, p->h_skip_d, nrhs * sizeof(int)));
   return ORI_OK;
 }
 static ori_status push_doubles(ori_plan_s* p, double* dst, const double* src, int count) {
   double* stage = p->h_small + 3 * p->cap;   // pinned staging beyond the tolerance slots
   for (int i = 0; i < count; ++i) stage[i] = src[i];
-  ORI_CUDA(cudaMemcpyAsync(dst, stage, count * sizeof(double), cudaMemcpyHostToDevice, p->ps));
+  ORI_TRY(small_copy(p, dst, static_cast<double*>(p->h_small_d) + 3 * p->cap, count * sizeof(double)));
   ORI_CUDA(cudaStreamSynchronize(p->ps));
   return ORI_OK;
 }
@@ -1346,7 +1398,7 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
   if (o.precision == ORI_FP64) {
     if (!warm) {
       ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
-      ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+      ORI_TRY(dev_copy(p, p->r64, p->b64, bytes64));
     }
     // COCG from w (0, or the warm start) to ||r|| <= tol ||b||.  The recursive
     // residual can drift from the true one b - B w; when the true residual
@@ -1404,7 +1456,7 @@ static ori_status solve_B(ori_plan_s* p, int nrhs, int rhs_per_k, const double* 
   // mixed: FP32 COCG on the normalised residual, FP64-class refinement
   if (!warm) {
     ORI_CUDA(cudaMemsetAsync(p->w, 0, bytes64, p->ps));
-    ORI_CUDA(cudaMemcpyAsync(p->r64, p->b64, bytes64, cudaMemcpyDeviceToDevice, p->ps));
+    ORI_TRY(dev_copy(p, p->r64, p->b64, bytes64));
   }
   std::vector<double> rn(rn0), err(nrhs, 0.0), recur(nrhs, 0.0);
   if (warm)

@@ -881,6 +881,12 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xf
   }
 }
 
+// The inverse X transform runs by decimation in frequency with the inverse
+// sign: its first radix-8 stage takes each line's L points in natural order
+// straight from global memory (eight independent coalesced loads per thread,
+// no scattered shared-memory stores), the remaining stages run in shared
+// memory, and the epilogue gathers the n kept points x < n from their
+// digit-reversed positions, so its own global reads and writes are coalesced.
 template <class T, int L, int C>
 __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xinv_smem(XArgs a0, Scalars* sc0, int fin) {
   const XArgs a = x_for_rhs(a0, blockIdx.y);
@@ -897,31 +903,27 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_xi
   const cpx<T>* in = reinterpret_cast<const cpx<T>*>(a.in);
   const int tid = threadIdx.x;
   for (int i = tid; i < L; i += NT) TW[i] = twg[i];
-  for (int e = tid; e < C * L; e += NT) {
-    const int k = e % L, c = e / L;
-    const long long line = (long long)blockIdx.x * C + c;
-    st_stage(X + sidx<C>(inv_digit_rev<L>(k), c), line < a.nlines ? in[line * a.line_len_in + k] : czero<T>());
-  }
   __syncthreads();
-  dit_head<L, C>(X, TW, tid, NT);
-  double2 acc = make_double2(0.0, 0.0);
-  cpx<T> accT = czero<T>();
   for (int g = tid; g < C * S8; g += NT) {
     const int j = g % S8, c = g / S8;
     const long long line = (long long)blockIdx.x * C + c;
     cpx<T> v[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = ld_stage(X + sidx<C>(j + t * S8, c));
+    for (int t = 0; t < 8; ++t) v[t] = line < a.nlines ? in[line * a.line_len_in + j + t * S8] : czero<T>();
+    dft<8, +1, false>(v);
 #pragma unroll
     for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
-    dft<8, +1, false>(v);
-    if (line < a.nlines) {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int x = j + t * S8;
-        if (x < a.n) x_epilogue<T>(a, line * a.n + x, v[t], accT, acc);
-      }
-    }
+    for (int t = 0; t < 8; ++t) st_stage(X + sidx<C>(j + t * S8, c), settle(v[t]));
+  }
+  __syncthreads();
+  dif_rest<L, C, +1>(X, TW, tid, NT);
+  double2 acc = make_double2(0.0, 0.0);
+  cpx<T> accT = czero<T>();
+  for (int e = tid; e < C * a.n; e += NT) {
+    const int x = e % a.n, c = e / a.n;
+    const long long line = (long long)blockIdx.x * C + c;
+    if (line < a.nlines) x_epilogue<T>(a, line * a.n + x, ld_stage(X + sidx<C>(inv_digit_rev<L>(x), c)), accT, acc);
   }
   const cpx<double> accD = c_to_c64(accT);
   acc.x += accD.x;

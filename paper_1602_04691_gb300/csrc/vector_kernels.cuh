@@ -11,23 +11,37 @@
 
 namespace ori {
 
-// Principal square root of a + ib (Re >= 0), from |z| by the half-angle formulas.
-__device__ __forceinline__ cpx<double> csqrt_principal(cpx<double> z) {
-  if (z.x == 0.0 && z.y == 0.0) return {0.0, 0.0};
-  const double m = hypot(z.x, z.y);
-  const double t = sqrt(0.5 * (m + fabs(z.x)));
-  if (z.x >= 0.0) return {t, z.y / (2.0 * t)};
-  return {fabs(z.y) / (2.0 * t), copysign(t, z.y)};
-}
-
 __device__ __forceinline__ cpx<double> cdivd(cpx<double> a, cpx<double> b) {
   const double den = b.x * b.x + b.y * b.y;
   return {(a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den};
 }
 
-// w = h N (A form scale), S = sqrt(h N) (B form scale), both precisions;
-// counts cells with S == 0 and cells with h == 0 or N == 0.
+// Principal square root s of w = a + ib (Re s >= 0, the branch of the
+// symmetrisation S = sqrt(h N)) by the half-angle formulas, with m = |w|:
+//   v = (m + |a|) / 2,  t = sqrt(v),  s = (t, b / 2t) if a >= 0, else (|b| / 2t, sign(b) t).
+// GB300's FP64 pipe issues a small fraction of the FP32 rate, so the square
+// root and the quotient come from one reciprocal square root r = 1/sqrt(v):
+// t = v r and b / 2t = b r / 2.  Also returns m, since |s|^2 = m and hence
+// 1 / s = conj(s) / m.
+__device__ __forceinline__ cpx<double> csqrt_principal(cpx<double> w, double& m) {
+  m = hypot(w.x, w.y);
+  if (m == 0.0) return {0.0, 0.0};
+  const double v = 0.5 * (m + fabs(w.x));
+  const double r = rsqrt(v);
+  const double t = v * r;
+  const double q = 0.5 * r * w.y;
+  if (w.x >= 0.0) return {t, q};
+  return {fabs(q), copysign(t, w.y)};
+}
+
+// The medium arrays of a plan from h and N (one pass over the cells):
+//   w = h N (scale of the A form), S = sqrt(h N) (scale of the B form), 1/S,
+// in FP64, FP32 and paired FP32 (the FP32 value is the pair's high part);
+// h and N are also copied into the plan (hcopy, Ncopy) when those are given.
+// The A-form arrays, 1/S and the copies are optional (nullptr).  Counts the
+// cells with S == 0.
 __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __restrict__ N,
+                         cpx<double>* hcopy, double* Ncopy,
                          cpx<double>* w64, cpx<double>* S64, cpx<float>* w32, cpx<float>* S32,
                          cpx<double>* Sinv, cpx<dfl>* wdf, cpx<dfl>* Sdf, long long n3,
                          unsigned long long* zero_count) {
@@ -36,19 +50,63 @@ __global__ void k_medium(const cpx<double>* __restrict__ h, const double* __rest
        i += (long long)gridDim.x * blockDim.x) {
     const cpx<double> hv = h[i];
     const double nv = N[i];
+    if (hcopy) hcopy[i] = hv;
+    if (Ncopy) Ncopy[i] = nv;
     const cpx<double> w = {hv.x * nv, hv.y * nv};
-    const cpx<double> s = csqrt_principal(w);
+    double m;
+    const cpx<double> s = csqrt_principal(w, m);
     S64[i] = s;
-    S32[i] = ccast<float>(s);
-    Sdf[i] = c_from_c64<dfl>(s);
-    if (w64) w64[i] = w;                 // the A-form arrays and 1/S are optional
-    if (w32) w32[i] = ccast<float>(w);
-    if (wdf) wdf[i] = c_from_c64<dfl>(w);
-    const bool zero = w.x == 0.0 && w.y == 0.0;
+    const cpx<dfl> sd = c_from_c64<dfl>(s);
+    Sdf[i] = sd;
+    S32[i] = {sd.x.hi, sd.y.hi};
+    if (w64) w64[i] = w;
+    if (wdf) {
+      const cpx<dfl> wd = c_from_c64<dfl>(w);
+      wdf[i] = wd;
+      if (w32) w32[i] = {wd.x.hi, wd.y.hi};
+    } else if (w32) {
+      w32[i] = ccast<float>(w);
+    }
+    const bool zero = m == 0.0;
     if (zero) ++zs;
-    if (Sinv) Sinv[i] = zero ? cpx<double>{0.0, 0.0} : cdivd(cpx<double>{1.0, 0.0}, s);
+    if (Sinv) {
+      const double im = zero ? 0.0 : 1.0 / m;
+      Sinv[i] = {s.x * im, -s.y * im};
+    }
   }
   if (zs) atomicAdd(zero_count, zs);
+}
+
+// Copies of the solver's small control data (scalar heads, tolerances, skip
+// flags, fault and count words) between device memory and mapped pinned host
+// memory, made by one CTA instead of a copy engine.  The solver reads and
+// writes these on the host between launches; a copy engine busy with a
+// caller's large transfer on another stream would hold them back for the
+// whole transfer.  rows blocks of `bytes` bytes at the given pitches, in
+// 8-byte words when every address, size and pitch allows.
+__global__ void k_small_copy(const unsigned char* src, unsigned char* dst, long long bytes, long long spitch,
+                             long long dpitch, int rows) {
+  const bool words = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) |
+                       uintptr_t(bytes) | uintptr_t(spitch) | uintptr_t(dpitch)) & 7u) == 0;
+  for (int r = 0; r < rows; ++r) {
+    const unsigned char* sr = src + r * spitch;
+    unsigned char* dr = dst + r * dpitch;
+    if (words) {
+      const unsigned long long* s8 = reinterpret_cast<const unsigned long long*>(sr);
+      unsigned long long* d8 = reinterpret_cast<unsigned long long*>(dr);
+      for (long long i = threadIdx.x; i < bytes / 8; i += blockDim.x) d8[i] = s8[i];
+    } else {
+      for (long long i = threadIdx.x; i < bytes; i += blockDim.x) dr[i] = sr[i];
+    }
+  }
+}
+
+// dst = src for n16 16-byte words of device memory (an SM copy, for the same
+// reason as k_small_copy).
+__global__ void k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, long long n16) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 // Spectrum of the kernel cube: keep the (L/2+1)^3 distinct entries of the

@@ -290,6 +290,75 @@ class Plan:
             d["history"] = self.residual_history(0)
         return u, d
 
+    def solve_media(self, hs, Ns, us, raise_on_failure: bool = True, **kw):
+        """Solve for a sequence of media held in host memory: for each i, set
+        the medium (hs[i], Ns[i]), solve, and copy the solution into us[i].
+
+        hs[i] (complex128), Ns[i] (float64) and us[i] (complex128) are CPU
+        tensors of n^3 values; pinned ones (``pin_memory()``) let the copies
+        run on the copy engines while the GPU solves: the inputs of medium
+        i + 1 travel to the device and the solution of medium i - 1 to the
+        host during the solve of medium i, through two device buffers of each.
+        An entry of us may repeat (the copies into it follow one another).
+        ``kw`` are the options of ``solve``.  Returns the info dicts."""
+        count = len(hs)
+        if len(Ns) != count or len(us) != count:
+            raise ValueError("hs, Ns and us must have the same length")
+        m = self.n ** 3
+        for name, seq, dt in (("hs", hs, torch.complex128), ("Ns", Ns, torch.float64), ("us", us, torch.complex128)):
+            for t in seq:
+                if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dt or t.numel() != m \
+                        or not t.is_contiguous():
+                    raise TypeError(f"every entry of {name} must be a contiguous CPU {dt} tensor of {m} values")
+        dev = self.device
+        main = torch.cuda.current_stream(dev)
+        cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        nb = min(2, count)
+        hb = [torch.empty(m, dtype=torch.complex128, device=dev) for _ in range(nb)]
+        Nb = [torch.empty(m, dtype=torch.float64, device=dev) for _ in range(nb)]
+        ub = [torch.empty(m, dtype=torch.complex128, device=dev) for _ in range(nb)]
+        # an event that was never recorded is complete for a waiting stream
+        uploaded = [torch.cuda.Event() for _ in range(nb)]
+        consumed = [torch.cuda.Event() for _ in range(nb)]
+        solved = [torch.cuda.Event() for _ in range(nb)]
+        downloaded = [torch.cuda.Event() for _ in range(nb)]
+
+        def upload(i):
+            b = i % nb
+            cin.wait_event(consumed[b])          # set_medium of medium i - 2 has read the buffers
+            with torch.cuda.stream(cin):
+                hb[b].copy_(hs[i], non_blocking=True)
+                Nb[b].copy_(Ns[i], non_blocking=True)
+            uploaded[b].record(cin)
+
+        def download(i):
+            b = i % nb
+            cout.wait_event(solved[b])
+            with torch.cuda.stream(cout):
+                us[i].copy_(ub[b], non_blocking=True)
+            downloaded[b].record(cout)
+
+        infos = []
+        if count:
+            upload(0)
+        for i in range(count):
+            b = i % nb
+            main.wait_event(uploaded[b])
+            self.set_medium(hb[b], Nb[b], stream=main)
+            consumed[b].record(main)
+            if i + 1 < count:
+                upload(i + 1)
+            main.wait_event(downloaded[b])       # the solution of medium i - 2 has left ub[b]
+            _, info = self.solve(out=ub[b], raise_on_failure=raise_on_failure, stream=main, **kw)
+            solved[b].record(main)
+            download(i)
+            infos.append(info)
+        cout.synchronize()
+        # the caller's stream is ordered after the copies into us
+        for b in range(nb):
+            main.wait_event(downloaded[b])
+        return infos
+
     def solve_batch(self, alphas=None, rhs: torch.Tensor | None = None, out: torch.Tensor | None = None,
                     raise_on_failure: bool = True, stream=None, **kw):
         """Solve for every wave number of the plan and every incidence direction at once.

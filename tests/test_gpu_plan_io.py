@@ -9,12 +9,16 @@
   recursive residual after every iteration: it falls to the tolerance, its
   last value matches the info of an FP64 solve, and a mixed solve records
   every FP32 iteration of its refinement steps.
+* Plan.solve_media (media and solutions in host memory, the copies
+  overlapping the solves) gives each medium's solution as set_medium and
+  solve one by one do, and matches the oracle's LU solution (Eq. 2.19).
 """
 
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_1602_04691_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -101,3 +105,48 @@ def test_residual_history_records_every_iteration(precision, tol):
         assert hist[-1] <= 10 * tol                  # the recursive estimate of the last FP32 step
     _, info2 = plan.solve(tol=tol, precision=precision)   # history off: the last recorded stays readable
     assert plan.residual_history(0) == hist
+
+
+@pytest.mark.parametrize("precision,tol,bound", [("mixed", 1e-6, 2e-5), ("fp64", 1e-11, 1e-9)])
+def test_solve_media_matches_one_by_one_and_oracle(precision, tol, bound):
+    """Three media through solve_media with an output buffer used twice (it
+    ends with the third solution) against set_medium + solve per medium, and
+    each solution against dense LU of the oracle."""
+    from paper_1602_04691_gb300 import Plan
+    n, k = 10, 2.5
+    media = [inputs.random_h_N(n, 700 + i) for i in range(3)]
+    hs = [torch.from_numpy(h).pin_memory() for h, _ in media]
+    Ns = [torch.from_numpy(N).pin_memory() for _, N in media]
+    a = torch.empty(n ** 3, dtype=torch.complex128).pin_memory()
+    b = torch.empty(n ** 3, dtype=torch.complex128).pin_memory()
+    plan = Plan(n, k, to_dev(media[0][0]), to_dev(media[0][1]))
+    infos = plan.solve_media(hs, Ns, [a, b, a], tol=tol, precision=precision)
+    got = [a.numpy().copy(), b.numpy().copy()]
+    want = []
+    for h, N in media:
+        plan.set_medium(to_dev(h), to_dev(N))
+        u, _ = plan.solve(tol=tol, precision=precision)
+        want.append(u.cpu().numpy())
+    plan.close()
+    assert all(i["returned"] == 0 for i in infos)
+    for g, w in ((got[0], want[2]), (got[1], want[1])):
+        assert np.linalg.norm(g - w) / np.linalg.norm(w) <= 1e-13
+    u0 = O.plane_wave(O.cell_centres(n), k)
+    for i, (h, N) in enumerate(media):
+        ref = O.solve_dense(O.red_matrix(n, k, h, N), u0)
+        assert np.linalg.norm(want[i] - ref) / np.linalg.norm(ref) <= bound, i
+
+
+def test_solve_media_rejects_device_or_mistyped_entries():
+    from paper_1602_04691_gb300 import Plan
+    n = 4
+    h, N = inputs.random_h_N(n, 9)
+    plan = Plan(n, 1.0, to_dev(h), to_dev(N))
+    u = torch.empty(n ** 3, dtype=torch.complex128)
+    with pytest.raises(TypeError):
+        plan.solve_media([to_dev(h)], [torch.from_numpy(N)], [u])
+    with pytest.raises(TypeError):
+        plan.solve_media([torch.from_numpy(h)], [torch.from_numpy(N).float()], [u])
+    with pytest.raises(ValueError):
+        plan.solve_media([torch.from_numpy(h)], [], [u])
+    plan.close()
