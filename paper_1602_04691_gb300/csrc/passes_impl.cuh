@@ -817,26 +817,30 @@ __global__ void __launch_bounds__(LSmem<L, C, T>::NT, LSmem<L, C, T>::MINB) k_st
       if (c < colmax && k < a.n_out) out[(long long)k * a.out_pt + c] = ld_stage(X + sidx<C>(p, c));
     }
   } else {
-    for (int e = tid; e < C * L; e += NT) {
-      const int c = e % C, p = e / C;
-      const int k = digit_rev<L>(p);
-      st_stage(X + sidx<C>(p, c), c < colmax ? in[(long long)k * a.in_pt + c] : czero<T>());
-    }
+    // the inverse by decimation in frequency with the inverse sign: the first
+    // radix-8 stage reads the L input rows in natural order from global
+    // memory, the others run in shared memory, and the n_out kept rows are
+    // gathered from their digit-reversed positions
     __syncthreads();
-    dit_head<L, C>(X, TW, tid, NT);
     for (int g = tid; g < C * S8; g += NT) {
       const int c = g % C, j = g / C;
       cpx<T> v[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = ld_stage(X + sidx<C>(j + t * S8, c));
-#pragma unroll
-      for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
+      for (int t = 0; t < 8; ++t) {
+        const int jj = j + t * S8;
+        v[t] = (c < colmax && jj < a.n_in) ? in[(long long)jj * a.in_pt + c] : czero<T>();
+      }
       dft<8, +1, false>(v);
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int z = j + t * S8;
-        if (c < colmax && z < a.n_out) out[(long long)z * a.out_pt + c] = settle(v[t]);
-      }
+      for (int t = 1; t < 8; ++t) v[t] = twL_mul<+1>(v[t], TW, (j * t) & (L - 1));
+#pragma unroll
+      for (int t = 0; t < 8; ++t) st_stage(X + sidx<C>(j + t * S8, c), settle(v[t]));
+    }
+    __syncthreads();
+    dif_rest<L, C, +1>(X, TW, tid, NT);
+    for (int e = tid; e < C * a.n_out; e += NT) {
+      const int c = e % C, z = e / C;
+      if (c < colmax) out[(long long)z * a.out_pt + c] = ld_stage(X + sidx<C>(inv_digit_rev<L>(z), c));
     }
   }
 }
