@@ -518,6 +518,7 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YINV + K, e0, e1); e0 = e1;
 
   epi.n = n; epi.nlines = n * n; epi.line_len_in = L; epi.line_len_out = n;
+  epi.err = p->d_fault;
   epi.in = T1; epi.twL = tw; epi.done = mask.flags; epi.done_stride = mask.stride;
   epi.partials = p->partials; epi.nrhs = nrhs; epi.bs_fft = bsT1; epi.sm_count = p->sm_count;
   ORI_CUDA(run_xinv<T>(L, epi, p->sc, fin, s, false, nullptr));

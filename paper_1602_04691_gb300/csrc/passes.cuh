@@ -92,6 +92,7 @@ struct XArgs {
   const double* coefs;  // EPI_RUPDATE: per-RHS coefficient (overrides coef when set)
   int nrhs;             // right-hand sides in the batch (gridDim.y)
   int sm_count;         // persistent kernels: SMs of the device
+  int* err;             // set to 1 by a kernel whose bounded wait on a bulk copy gave up
 };
 
 struct SArgs {

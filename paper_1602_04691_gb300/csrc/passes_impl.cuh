@@ -533,6 +533,7 @@ __device__ __forceinline__ void xinv_prefetch(const XArgs& a, int tile, cpx<floa
 template <int L, int C>
 __global__ void __launch_bounds__(XInvPipe<L, C>::NT, L > 1024 ? 1 : 3) k_xinv_pipe(XArgs a0, Scalars* sc0, int fin) {
   using T = float;
+  using XP = XInvPipe<L, C>;
   const XArgs a = x_for_rhs(a0, blockIdx.y);
   Scalars* sc = sc0 == nullptr ? nullptr : sc0 + blockIdx.y;
   using TL = Tile<L, C, T>;
@@ -540,29 +541,93 @@ __global__ void __launch_bounds__(XInvPipe<L, C>::NT, L > 1024 ? 1 : 3) k_xinv_p
   constexpr int PKI = TL::PKI, PCI = TL::PCI;
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* B = reinterpret_cast<cpx<T>*>(smraw);
-  cpx<T>* XI = B + XInvPipe<L, C>::BUF;
-  cpx<T>* GI = XI + XInvPipe<L, C>::EPI / 2;
+  cpx<T>* XI = B + XP::BUF;
+  cpx<T>* GI = XI + XP::EPI / 2;
   __shared__ double2 red[32];
   __shared__ int s_last;
+  __shared__ __align__(8) unsigned long long bars[2];   // bulk copies: [0] the T1 tile, [1] the epilogue inputs
   if (a.done != nullptr && *a.done != 0) return;
   const cpx<T>* tw = reinterpret_cast<const cpx<T>*>(a.twL);
   const int tid = threadIdx.x;
   const int ntiles = int((a.nlines + C - 1) / C);
   const bool staged = xinv_stage_epi(a.mode) && (a.n % 2 == 0);
+  // Bulk copies (TMA, one thread issues them): a tile's C lines of T1 are one
+  // contiguous block and its epilogue inputs two more (n even keeps every
+  // offset and size a multiple of 16 bytes; the shared-memory regions start
+  // on 16-byte boundaries when their element counts are even).
+  constexpr bool kBulkFits = XP::BUF % 2 == 0 && (XP::EPI / 2) % 2 == 0;
+  const bool bulk = kBulkFits && staged &&
+                    ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.xin) |
+                      reinterpret_cast<uintptr_t>(a.scale)) & 15u) == 0;
+  unsigned ph_t = 0, ph_e = 0;      // barrier phases awaited next
+  bool pend_t = false, pend_e = false, failed = false;
+  if (bulk) {
+    if (tid == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  auto lines_of = [&](int t) {
+    const long long left = a.nlines - (long long)t * C;
+    return left < C ? int(left) : C;
+  };
+  auto bulk_tile = [&](int t) {
+    if (tid == 0) {
+      const unsigned bytes = unsigned(lines_of(t)) * unsigned(L) * unsigned(sizeof(cpx<T>));
+      fence_proxy_async();
+      mbar_expect_tx(&bars[0], bytes);
+      bulk_load(B, reinterpret_cast<const cpx<T>*>(a.in) + (long long)t * C * L, bytes, &bars[0]);
+    }
+    pend_t = true;
+  };
+  auto bulk_epi = [&](int t) {
+    if (tid == 0) {
+      const unsigned bytes = unsigned(lines_of(t)) * unsigned(a.n) * unsigned(sizeof(cpx<T>));
+      const long long off = (long long)t * C * a.n;
+      fence_proxy_async();
+      mbar_expect_tx(&bars[1], 2 * bytes);
+      bulk_load(XI, reinterpret_cast<const cpx<T>*>(a.xin) + off, bytes, &bars[1]);
+      bulk_load(GI, reinterpret_cast<const cpx<T>*>(a.scale) + off, bytes, &bars[1]);
+    }
+    pend_e = true;
+  };
+  // Bounded wait for a bulk copy (all threads).  A copy that has not landed
+  // after kMbarWaitNs sets *a.err; the CTA then stops working on tiles.
+  auto bulk_wait = [&](unsigned long long* bar, unsigned& ph, bool& pend) -> bool {
+    const bool ok = mbar_wait(bar, ph);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0 && a.err != nullptr) atomicExch(a.err, 1);
+      return false;
+    }
+    ph ^= 1u;
+    pend = false;
+    return true;
+  };
   int c, ja;
   map_t<LAYOUT_CONTIG, C, L2>(tid, c, ja);
   double2 acc = make_double2(0.0, 0.0);
   cpx<T> accT = czero<T>();
   int tile = blockIdx.x;
-  // groups in flight, oldest first: [T1 of this tile] [epilogue inputs of this tile] [T1 of the next]
+  // cp.async groups in flight, oldest first: [T1 of this tile] [epilogue inputs of this tile] [T1 of the next]
   if (tile < ntiles) {
-    xinv_prefetch<L, C>(a, tile, B);
-    if (staged) xinv_prefetch_epi<L, C>(a, tile, XI, GI);
-    else cp_async_commit();
+    if (bulk) {
+      bulk_tile(tile);
+      bulk_epi(tile);
+    } else {
+      xinv_prefetch<L, C>(a, tile, B);
+      if (staged) xinv_prefetch_epi<L, C>(a, tile, XI, GI);
+      else cp_async_commit();
+    }
   }
   for (; tile < ntiles; tile += gridDim.x) {
-    cp_async_wait_1();   // this tile's T1 block has landed
-    __syncthreads();
+    if (bulk) {
+      if (!bulk_wait(&bars[0], ph_t, pend_t)) { failed = true; break; }
+    } else {
+      cp_async_wait_1();   // this tile's T1 block has landed
+      __syncthreads();
+    }
     // stage A: DFT over k2 of X[k1 + L1 k2], twiddle
     cpx<T> b[NI][L2];
 #pragma unroll
@@ -590,11 +655,20 @@ __global__ void __launch_bounds__(XInvPipe<L, C>::NT, L > 1024 ? 1 : 3) k_xinv_p
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) r[k1] = B[c * PCI + ja * PKI + k1];
     __syncthreads();   // exchange consumed: the buffer takes the next tile
-    if (tile + (int)gridDim.x < ntiles) xinv_prefetch<L, C>(a, tile + gridDim.x, B);
-    else cp_async_commit();
+    if (bulk) {
+      if (tile + (int)gridDim.x < ntiles) bulk_tile(tile + gridDim.x);
+    } else if (tile + (int)gridDim.x < ntiles) {
+      xinv_prefetch<L, C>(a, tile + gridDim.x, B);
+    } else {
+      cp_async_commit();
+    }
     dft<L1, +1, false>(r);
-    cp_async_wait_1();   // this tile's epilogue inputs have landed
-    __syncthreads();
+    if (bulk) {
+      if (!bulk_wait(&bars[1], ph_e, pend_e)) { failed = true; break; }
+    } else {
+      cp_async_wait_1();   // this tile's epilogue inputs have landed
+      __syncthreads();
+    }
     const long long line = (long long)tile * C + c;
     if (line < a.nlines) {
       if (staged) {
@@ -619,9 +693,14 @@ __global__ void __launch_bounds__(XInvPipe<L, C>::NT, L > 1024 ? 1 : 3) k_xinv_p
     }
     __syncthreads();   // epilogue inputs consumed
     if (tile + (int)gridDim.x < ntiles) {
-      if (staged) xinv_prefetch_epi<L, C>(a, tile + gridDim.x, XI, GI);
+      if (bulk) bulk_epi(tile + gridDim.x);
+      else if (staged) xinv_prefetch_epi<L, C>(a, tile + gridDim.x, XI, GI);
       else cp_async_commit();
     }
+  }
+  if (failed) {   // leave no bulk copy writing into shared memory behind (bounded waits)
+    if (pend_t) mbar_wait(&bars[0], ph_t);
+    if (pend_e) mbar_wait(&bars[1], ph_e);
   }
   cp_async_wait_all();
   if (fin == FIN_NONE) return;
