@@ -110,6 +110,11 @@ struct ori_plan_s {
   CUtensorMap zmap{};
   const void* zmap_ptr = nullptr;
   int zmap_R = 0, zmap_ok = 0, zbox = 0;
+  // tensor maps of the FP32 Y passes' input rows: T1f rows (Y forward) and
+  // T2f rows (Y inverse), 16 columns by ybox rows a box
+  CUtensorMap ymap_f{}, ymap_i{};
+  const void* ymap_ptr = nullptr;
+  int ymap_R = 0, ymap_ok = 0, ybox_f = 0, ybox_i = 0;
   // batch capacity: pass scratch and solver state for cap right-hand sides
   int cap = 0;
   cpx<float>* T1f = nullptr;
@@ -456,6 +461,53 @@ static void z_tensor_map(ori_plan_s* p, SArgs& z, int nrhs) {
   z.err = p->d_fault;
 }
 
+// Tensor maps of the rows the pipelined FP32 Y passes stage per tile (16
+// FP32 columns = 128 bytes a row): the Y-forward input T1f, dims (kx, y, z,
+// right-hand side) and box (16, ybox_f, 1, 1), ybox_f = min(L/2, 256) (a
+// power of two dividing L/2: the zero-filled rows past n stay within the L/2
+// staged rows); the Y-inverse input T2f, dims (kx, ky, z, right-hand side)
+// and box (16, ybox_i, 1, 1), ybox_i = min(L, 256).
+static void y_tensor_maps(ori_plan_s* p, SArgs& y, SArgs& yi, int nrhs) {
+  const int R = std::max(1, nrhs);
+  if (p->ymap_ptr != p->T1f || p->ymap_R != R) {
+    p->ymap_ok = 0;
+    p->ymap_ptr = p->T1f;
+    p->ymap_R = R;
+    const int L = p->L, n = p->n;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (enc != nullptr && L >= 64 && L <= 1024 && ((reinterpret_cast<uintptr_t>(p->T1f) |
+                                                    reinterpret_cast<uintptr_t>(p->T2f)) & 15u) == 0) {
+      const cuuint64_t es = sizeof(cpx<float>);
+      const int bf = std::min(L / 2, 256), bi = std::min(L, 256);
+      const cuuint32_t estr[4] = {1, 1, 1, 1};
+      const cuuint64_t dims_f[4] = {cuuint64_t(L), cuuint64_t(n), cuuint64_t(n), cuuint64_t(R)};
+      const cuuint64_t str_f[3] = {cuuint64_t(L) * es, cuuint64_t(n) * L * es, cuuint64_t(t1_elems(p)) * es};
+      const cuuint32_t box_f[4] = {cuuint32_t(kZGroup), cuuint32_t(bf), 1, 1};
+      const cuuint64_t dims_i[4] = {cuuint64_t(L), cuuint64_t(L), cuuint64_t(n), cuuint64_t(R)};
+      const cuuint64_t str_i[3] = {cuuint64_t(L) * es, cuuint64_t(L) * L * es, cuuint64_t(t2_elems(p)) * es};
+      const cuuint32_t box_i[4] = {cuuint32_t(kZGroup), cuuint32_t(bi), 1, 1};
+      if (enc(&p->ymap_f, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, p->T1f, dims_f, str_f, box_f, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+          enc(&p->ymap_i, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, p->T2f, dims_i, str_i, box_i, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+        p->ymap_ok = 1;
+        p->ybox_f = bf;
+        p->ybox_i = bi;
+      }
+    }
+  }
+  y.zrows = p->ymap_f;
+  y.zrows_ok = p->ymap_ok;
+  y.zbox = p->ybox_f;
+  y.err = p->d_fault;
+  yi.zrows = p->ymap_i;
+  yi.zrows_ok = p->ymap_ok;
+  yi.zbox = p->ybox_i;
+  yi.err = p->d_fault;
+}
+
 template <class T>
 static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStream_t s, Mask mask,
                            int nrhs = 1, int rhs_per_k = 1) {
@@ -485,6 +537,8 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   y.twL = tw; y.done = mask.flags; y.done_stride = mask.stride; y.sm_count = p->sm_count;
   y.nrhs = nrhs; y.bs_in = bsT1; y.bs_out = bsT2;
   y.sched = p->sched_y; y.cta_cap = p->cta_cap; y.variant = p->var_y;
+  SArgs yi{};
+  if (f32) y_tensor_maps(p, y, yi, nrhs);
   ORI_CUDA(run_strided<T>(L, SMODE_FWD, true, y, s, false));
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_YFWD + K, e0, e1); e0 = e1;
@@ -506,7 +560,6 @@ static ori_status run_conv(ori_plan_s* p, XArgs pro, XArgs epi, int fin, cudaStr
   launched(p);
   e1 = t_rec(p, s); t_pair(p, ORI_PASS_ZCONV + K, e0, e1); e0 = e1;
 
-  SArgs yi{};
   yi.in = T2; yi.out = T1;
   yi.in_outer = (long long)L * L; yi.out_outer = (long long)n * L;
   yi.in_pt = L; yi.out_pt = L; yi.ncols = L; yi.n_in = L; yi.n_out = n; yi.nouter = n;

@@ -1623,10 +1623,29 @@ template <int L, int C, class T, int L1X = Split<L>::L1>
 struct YPipe {
   using TL = Tile<L, C, T, L1X>;
   static constexpr int NT = TL::NT;
+  // 128-byte rows (16 FP32 columns): the input rows arrive by TMA when the
+  // host supplied the tensor map (a.zrows); 128 bytes of slack align the
+  // tile to 128 bytes, then the mbarrier
+  static constexpr bool TMA = sizeof(T) == 4 && C == kZGroup;
   static constexpr size_t E_ELEMS = size_t(TL::SMEM_ELEMS);
   static constexpr size_t S_ELEMS = size_t(L / 2) * C;
-  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>);
+  static constexpr size_t TMA_BYTES = TMA ? 128 + 16 : 0;
+  static constexpr size_t SMEM_BYTES = (E_ELEMS + S_ELEMS + size_t(L)) * sizeof(cpx<T>) + TMA_BYTES;
 };
+
+// Bulk-copy staging of the rows [0, rows) of a pipelined FP32 Y tile (C ==
+// kZGroup columns at x = cb * C of plane `outer`, right-hand side rhs)
+// through the tensor map a.zrows (box: C columns x a.zbox rows); rows past
+// the map's extent are zero-filled and must fit the staging buffer.  Thread 0
+// issues the copies.
+template <int C>
+__device__ __forceinline__ void ypipe_tma_rows(const SArgs& a, int rhs, int outer, int cb, int rows, cpx<float>* S,
+                                               unsigned long long* bar) {
+  const int nbox = (rows + a.zbox - 1) / a.zbox;
+  fence_proxy_async();
+  mbar_expect_tx(bar, unsigned(nbox * a.zbox * C * int(sizeof(cpx<float>))));
+  for (int q = 0; q < nbox; ++q) tma_load_4d(S + q * a.zbox * C, &a.zrows, cb * C, q * a.zbox, outer, rhs, bar);
+}
 
 template <class T, int L, int C, int L1X>
 __device__ __forceinline__ void ypipe_prefetch(const SArgs& a, int tile, int per_rhs, cpx<T>* S) {
@@ -1649,15 +1668,18 @@ template <class T, int L, int C, int L1X = Split<L>::L1>
 __global__ void __launch_bounds__(YPipe<L, C, T, L1X>::NT,
                                   (L > 1024 || L1X >= 64 || YPipe<L, C, T, L1X>::NT >= 512)
                                       ? 1 : (YPipe<L, C, T, L1X>::NT >= 256 ? 2 : 512 / YPipe<L, C, T, L1X>::NT))
-k_yfwd_pipe(SArgs a) {
+k_yfwd_pipe(const __grid_constant__ SArgs a) {
   using TL = Tile<L, C, T, L1X>;
   using YP = YPipe<L, C, T, L1X>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PK = TL::PK, PC = TL::PC;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* E = reinterpret_cast<cpx<T>*>(smraw);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* base = smraw;
+  if constexpr (YP::TMA) base += (128u - (smem_addr(smraw) & 127u)) & 127u;   // E, S: 128-byte aligned
+  cpx<T>* E = reinterpret_cast<cpx<T>*>(base);
   cpx<T>* S = E + YP::E_ELEMS;
   cpx<T>* TW = S + YP::S_ELEMS;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(TW + L);
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
   fill_tw2<L, L2>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
   const int per_rhs = a.nouter * a.col_blocks;
@@ -1665,15 +1687,47 @@ k_yfwd_pipe(SArgs a) {
   const int step = gridDim.x;
   const int tid = threadIdx.x;
   const int c = tid % C, jl = tid / C;
+  const bool tma = YP::TMA && a.zrows_ok != 0;   // uniform over the grid
+  unsigned phase = 0;
+  if (tma) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  auto stage = [&](int t) {
+    if constexpr (YP::TMA) {
+      if (tma) {
+        if (tid == 0) {
+          const int rt = t / per_rhs, tt = t - rt * per_rhs;
+          const int o = tt / a.col_blocks;
+          ypipe_tma_rows<C>(a, rt, o, tt - o * a.col_blocks, a.n_in, reinterpret_cast<cpx<float>*>(S), bar);
+        }
+        return;
+      }
+    }
+    ypipe_prefetch<T, L, C, L1X>(a, t, per_rhs, S);
+  };
   int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
-  if (tile < ntiles) ypipe_prefetch<T, L, C, L1X>(a, tile, per_rhs, S);
+  if (tile < ntiles) stage(tile);
   while (tile < ntiles) {
     const int rhs = tile / per_rhs;
     const int tl = tile - rhs * per_rhs;
     const int outer = tl / a.col_blocks, cb = tl - outer * a.col_blocks;
     const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
-    cp_async_wait_all();
-    __syncthreads();
+    if (tma) {
+      const bool ok = mbar_wait(bar, phase);
+      if (__syncthreads_or(!ok)) {   // rows that have not landed: flag it, wait once more (bounded), leave
+        if (tid == 0 && a.err != nullptr) atomicExch(a.err, 1);
+        if (!ok) mbar_wait(bar, phase);
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     cpx<T> r[L1];
 #pragma unroll
     for (int j1 = 0; j1 < L1; ++j1) {
@@ -1684,7 +1738,7 @@ k_yfwd_pipe(SArgs a) {
       }
     }
     __syncthreads();
-    if (next < ntiles) ypipe_prefetch<T, L, C, L1X>(a, next, per_rhs, S);
+    if (next < ntiles) stage(next);
     dft<L1, -1, true>(r);
     const cpx<T>* t2 = TW + jl;
 #pragma unroll
@@ -1724,7 +1778,10 @@ struct YInvPipe {
   using TL = Tile<L, C, float, L1X>;
   static constexpr int NT = TL::NT;
   static constexpr int BUF = (C * L > TL::SMEM_ELEMS) ? C * L : TL::SMEM_ELEMS;
-  static constexpr size_t SMEM_BYTES = size_t(BUF + L) * sizeof(cpx<float>);
+  // 128-byte rows: TMA staging as in YPipe (slack to align the tile, the mbarrier)
+  static constexpr bool TMA = C == kZGroup;
+  static constexpr size_t TMA_BYTES = TMA ? 128 + 16 : 0;
+  static constexpr size_t SMEM_BYTES = size_t(BUF + L) * sizeof(cpx<float>) + TMA_BYTES;
 };
 
 template <int L, int C, int L1X>
@@ -1747,15 +1804,18 @@ template <int L, int C, int L1X = Split<L>::L1>
 __global__ void __launch_bounds__(YInvPipe<L, C, L1X>::NT,
                                   (L > 1024 || L1X >= 64 || YInvPipe<L, C, L1X>::NT >= 512)
                                       ? 1 : (YInvPipe<L, C, L1X>::NT >= 256 ? 2 : 512 / YInvPipe<L, C, L1X>::NT))
-k_yinv_pipe(SArgs a) {
+k_yinv_pipe(const __grid_constant__ SArgs a) {
   using T = float;
   using TL = Tile<L, C, T, L1X>;
   using YP = YInvPipe<L, C, L1X>;
   constexpr int L1 = TL::L1, L2 = TL::L2, NT = TL::NT, NI = L1 / L2;
   constexpr int PKI = TL::PKI, PCI = TL::PCI;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T>* B = reinterpret_cast<cpx<T>*>(smraw);
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* base = smraw;
+  if constexpr (YP::TMA) base += (128u - (smem_addr(smraw) & 127u)) & 127u;   // B: 128-byte aligned
+  cpx<T>* B = reinterpret_cast<cpx<T>*>(base);
   cpx<T>* TW = B + YP::BUF;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(TW + L);
   const cpx<T>* twg = reinterpret_cast<const cpx<T>*>(a.twL);
   fill_tw2<L, L2>(TW, twg, threadIdx.x, NT);   // [k1][j] layout
   const int per_rhs = a.nouter * a.col_blocks;
@@ -1764,15 +1824,47 @@ k_yinv_pipe(SArgs a) {
   const int tid = threadIdx.x;
   int c, ja;
   map_t<LAYOUT_STRIDED, C, L2>(tid, c, ja);
+  const bool tma = YP::TMA && a.zrows_ok != 0;   // uniform over the grid
+  unsigned phase = 0;
+  if (tma) {
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  auto stage = [&](int t) {
+    if constexpr (YP::TMA) {
+      if (tma) {
+        if (tid == 0) {
+          const int rt = t / per_rhs, tt = t - rt * per_rhs;
+          const int o = tt / a.col_blocks;
+          ypipe_tma_rows<C>(a, rt, o, tt - o * a.col_blocks, L, B, bar);
+        }
+        return;
+      }
+    }
+    yinv_prefetch<L, C, L1X>(a, t, per_rhs, B);
+  };
   int tile = next_live_tile(a, blockIdx.x, step, per_rhs, ntiles);
-  if (tile < ntiles) yinv_prefetch<L, C, L1X>(a, tile, per_rhs, B);
+  if (tile < ntiles) stage(tile);
   while (tile < ntiles) {
     const int rhs = tile / per_rhs;
     const int tl = tile - rhs * per_rhs;
     const int outer = tl / a.col_blocks, cb = tl - outer * a.col_blocks;
     const int next = next_live_tile(a, tile + step, step, per_rhs, ntiles);
-    cp_async_wait_all();
-    __syncthreads();
+    if (tma) {
+      const bool ok = mbar_wait(bar, phase);
+      if (__syncthreads_or(!ok)) {   // rows that have not landed: flag it, wait once more (bounded), leave
+        if (tid == 0 && a.err != nullptr) atomicExch(a.err, 1);
+        if (!ok) mbar_wait(bar, phase);
+        return;
+      }
+      phase ^= 1u;
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     // stage A: DFT over k2 of rows k1 + L1 k2, twiddle
     cpx<T> b[NI][L2];
 #pragma unroll
@@ -1799,7 +1891,7 @@ k_yinv_pipe(SArgs a) {
 #pragma unroll
     for (int k1 = 0; k1 < L1; ++k1) r[k1] = B[c * PCI + ja * PKI + k1];
     __syncthreads();   // exchange consumed: the buffer takes the next tile
-    if (next < ntiles) yinv_prefetch<L, C, L1X>(a, next, per_rhs, B);
+    if (next < ntiles) stage(next);
     dft<L1, +1, false>(r);
     cpx<T>* out = reinterpret_cast<cpx<T>*>(bmove(a.out, a.bs_out * rhs)) + outer * a.out_outer + (long long)cb * C;
 #pragma unroll
