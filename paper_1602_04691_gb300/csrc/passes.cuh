@@ -119,15 +119,17 @@ struct SArgs {
   int mirror_in;                   // forward transform of an even sequence stored up to L/2:
                                    // input row j > L/2 is read from row L - j
   // launch schedule of the FP32 Y-forward and Z passes (chosen by the plan's
-  // autotuner): SCHED_PERSISTENT = the cp.async-pipelined persistent kernel
+  // autotuner): SCHED_PERSISTENT = the pipelined persistent kernel
   // with at most cta_cap resident CTAs per SM (0 = as many as fit);
   // SCHED_TILES = one CTA per tile of columns
   int sched;
   int cta_cap;
   int variant;                     // pipelined FP32 kernels: launch variant (has_pipe_variants)
-  // FP32 Z pass with 16-column tiles: the input rows of a tile arrive by TMA
-  // (cp.async.bulk.tensor) through this map of the input cube, dims (kx, ky,
-  // z, right-hand side), box (16, 1, zbox, 1); zrows_ok = 0 keeps cp.async
+  // FP32 Z and Y passes with 16-column tiles: the input rows of a tile
+  // arrive by TMA (cp.async.bulk.tensor) through this map of the input cube,
+  // dims (kx, ky, z, right-hand side) and box (16, 1, zbox, 1) for the Z
+  // pass, (kx, y, z, right-hand side) and box (16, zbox, 1, 1) for the Y
+  // passes; zrows_ok = 0 keeps cp.async
   CUtensorMap zrows;
   int zrows_ok;
   int zbox;

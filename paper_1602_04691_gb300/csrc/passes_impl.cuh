@@ -477,10 +477,11 @@ __global__ void __launch_bounds__(Tile<L, C, T>::NT, Tile<L, C, T>::MINB) k_xinv
 // ---------------------------------------------------------------------------
 // X inverse pass, persistent and pipelined (FP32).  A CTA loops over tiles
 // of C consecutive lines; a tile's L points per line (one contiguous block
-// of C L complex values) are staged in shared memory with cp.async, the
-// exchange between the two DFT stages reuses that buffer in place, and as
-// soon as the second stage has read the exchange the next tile starts
-// streaming in, overlapping the inverse DFT and the epilogue.
+// of C L complex values) are staged in shared memory by one bulk copy (or
+// cp.async when an address is not 16-byte aligned), the exchange between the
+// two DFT stages reuses that buffer in place, and as soon as the second stage
+// has read the exchange the next tile starts streaming in, overlapping the
+// inverse DFT and the epilogue.
 // ---------------------------------------------------------------------------
 template <int L, int C>
 struct XInvPipe {
@@ -1616,8 +1617,9 @@ cudaError_t launch_zconv_smem_L(SArgs a, cudaStream_t s, bool setup, int sm_coun
 // ---------------------------------------------------------------------------
 // Y forward pass, persistent and software-pipelined like the Z pass: each CTA
 // loops over tiles (outer index z, C columns); the next tile's n input rows
-// stream into shared memory with cp.async while the current one is
-// transformed.
+// stream into shared memory while the current one is transformed, by TMA
+// through a tensor map of T1 for 16-column tiles (boxes of up to 256 rows)
+// and by cp.async otherwise.
 // ---------------------------------------------------------------------------
 template <int L, int C, class T, int L1X = Split<L>::L1>
 struct YPipe {
@@ -1769,9 +1771,10 @@ k_yfwd_pipe(const __grid_constant__ SArgs a) {
 // ---------------------------------------------------------------------------
 // Y inverse pass, persistent and pipelined (FP32): tiles (outer index z, C
 // columns) of every right-hand side numbered together.  A tile's L input
-// rows stream into shared memory with cp.async; the exchange between the
-// two DFT stages reuses that buffer in place, and the next tile is requested
-// as soon as the second stage has read the exchange.
+// rows stream into shared memory (TMA through a tensor map of T2 for
+// 16-column tiles, cp.async otherwise); the exchange between the two DFT
+// stages reuses that buffer in place, and the next tile is requested as soon
+// as the second stage has read the exchange.
 // ---------------------------------------------------------------------------
 template <int L, int C, int L1X = Split<L>::L1>
 struct YInvPipe {
