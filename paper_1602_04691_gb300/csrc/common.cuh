@@ -190,29 +190,105 @@ constexpr int bitrev(int i, int R) {
   return r;
 }
 
+// z * (SIGN i): a quarter turn, no arithmetic.
+template <int SIGN, class T>
+__device__ __forceinline__ cpx<T> mul_i(cpx<T> z) {
+  return SIGN > 0 ? cpx<T>{-z.y, z.x} : cpx<T>{z.y, -z.x};
+}
+
 // In-register DFT of size R (power of two, R <= 64):
 //   a[k] <- sum_j a[j] exp(SIGN 2 pi i j k / R).
-// Radix-2 decimation in frequency, then the bit-reversal permutation (free:
-// all indices are compile-time constants).  HALF: a[j] = 0 for j >= R/2 on
-// input (the zero padding of Section 3), which removes the first stage's adds.
+// Decimation in frequency, then the bit-reversal permutation (free: all
+// indices are compile-time constants).  The stages go two at a time as
+// radix-4 butterflies, a final radix-2 stage when log2 R is odd.  A radix-4
+// butterfly leaves the array exactly as the two radix-2 stages it replaces
+// (spans s and s/2 of a block of M = 2s points, w = exp(SIGN 2 pi i / M)):
+// for x0..x3 = a[j], a[j + s/2], a[j + s], a[j + 3s/2] and
+// t0 = x0 + x2, t1 = x0 - x2, t2 = x1 + x3, t3 = SIGN i (x1 - x3),
+//   a[j] = t0 + t2,           a[j + s/2] = (t0 - t2) w^2j,
+//   a[j + s] = (t1 + t3) w^j, a[j + 3s/2] = (t1 - t3) w^3j,
+// since w^(s/2) = SIGN i; it needs three twiddle products where the two
+// radix-2 stages need four (34 -> 28 nontrivial products at R = 32, measured:
+// the FP32 Z pass 3.43 -> 3.36 ms at n = 512).  HALF: a[j] = 0 for j >= R/2
+// on input (the zero padding of Section 3), so the first butterflies have
+// x2 = x3 = 0.
+// Radix-2 form of the same transform (every stage span s = R/2, R/4, ..., 1;
+// the outputs multiplied by w^j of their block): the small transforms (R <= 8,
+// the radix-8 stages of the paired-FP32 passes), where the radix-4 form
+// saves no twiddle product.
+template <int R, int SIGN, bool HALF, class T>
+__device__ __forceinline__ void dft_radix2(cpx<T> (&a)[R]) {
+#pragma unroll
+  for (int s = R / 2; s >= 1; s >>= 1) {
+#pragma unroll
+    for (int b = 0; b < R; b += 2 * s) {
+#pragma unroll
+      for (int j = 0; j < s; ++j) {
+        const int idx = j * (64 / (2 * s));
+        const cpx<T> u = a[b + j];
+        if (HALF && s == R / 2) {
+          a[b + j + s] = tw64_mul<SIGN>(u, idx);
+        } else {
+          const cpx<T> v = a[b + j + s];
+          a[b + j] = u + v;
+          a[b + j + s] = tw64_mul<SIGN>(u - v, idx);
+        }
+      }
+    }
+  }
+  cpx<T> t[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) t[i] = a[bitrev(i, R)];
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = t[i];
+}
+
 template <int R, int SIGN, bool HALF, class T>
 __device__ __forceinline__ void dft(cpx<T> (&a)[R]) {
-  if constexpr (R > 1) {
+  if constexpr (R > 1 && R <= 8) {
+    dft_radix2<R, SIGN, HALF>(a);
+  } else if constexpr (R > 1) {
+    bool first = true;
+    int s = R / 2;
 #pragma unroll
-    for (int s = R / 2; s >= 1; s >>= 1) {
+    for (; s >= 2; s /= 4) {
 #pragma unroll
       for (int b = 0; b < R; b += 2 * s) {
 #pragma unroll
-        for (int j = 0; j < s; ++j) {
-          const int idx = j * (64 / (2 * s));
-          const cpx<T> u = a[b + j];
-          if (HALF && s == R / 2) {
-            a[b + j + s] = tw64_mul<SIGN>(u, idx);
+        for (int j = 0; j < s / 2; ++j) {
+          const int idx = j * (64 / (2 * s));   // w^j in 64ths of a turn
+          const int h = s / 2;
+          cpx<T> t0, t1, t2, t3;
+          if (HALF && first) {
+            t0 = a[b + j];
+            t1 = a[b + j];
+            t2 = a[b + j + h];
+            t3 = mul_i<SIGN>(a[b + j + h]);
           } else {
-            const cpx<T> v = a[b + j + s];
-            a[b + j] = u + v;
-            a[b + j + s] = tw64_mul<SIGN>(u - v, idx);
+            const cpx<T> x0 = a[b + j], x1 = a[b + j + h], x2 = a[b + j + s], x3 = a[b + j + 3 * h];
+            t0 = x0 + x2;
+            t1 = x0 - x2;
+            t2 = x1 + x3;
+            t3 = mul_i<SIGN>(x1 - x3);
           }
+          a[b + j] = t0 + t2;
+          a[b + j + h] = tw64_mul<SIGN>(t0 - t2, 2 * idx);
+          a[b + j + s] = tw64_mul<SIGN>(t1 + t3, idx);
+          a[b + j + 3 * h] = tw64_mul<SIGN>(t1 - t3, 3 * idx);
+        }
+      }
+      first = false;
+    }
+    if (s == 1) {   // the last radix-2 stage (span 1: no twiddles)
+#pragma unroll
+      for (int b = 0; b < R; b += 2) {
+        const cpx<T> u = a[b];
+        if (HALF && first) {
+          a[b + 1] = u;
+        } else {
+          const cpx<T> v = a[b + 1];
+          a[b] = u + v;
+          a[b + 1] = u - v;
         }
       }
     }
