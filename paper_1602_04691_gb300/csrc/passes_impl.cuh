@@ -1,5 +1,5 @@
 // passes_impl.cuh - kernels of the five FFT passes and their launchers.
-// Included by one translation unit per precision (passes_f32.cu, passes_f64.cu).
+// Included by passes_inst.cu, compiled once per arithmetic and part of the passes.
 #pragma once
 
 #include "dfloat.cuh"
