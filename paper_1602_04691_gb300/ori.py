@@ -296,9 +296,10 @@ class Plan:
 
         hs[i] (complex128), Ns[i] (float64) and us[i] (complex128) are CPU
         tensors of n^3 values; pinned ones (``pin_memory()``) let the copies
-        run on the copy engines while the GPU solves: the inputs of medium
-        i + 1 travel to the device and the solution of medium i - 1 to the
-        host during the solve of medium i, through two device buffers of each.
+        run on the copy engines while the GPU solves: the inputs of the next
+        media travel to the device and the solutions of the previous ones to
+        the host during the solve of medium i, through three device buffers
+        of each.
         An entry of us may repeat (the copies into it follow one another).
         ``kw`` are the options of ``solve``.  Returns the info dicts."""
         count = len(hs)
@@ -313,7 +314,12 @@ class Plan:
         dev = self.device
         main = torch.cuda.current_stream(dev)
         cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        nb = min(2, count)
+        # three device buffers of each: the inputs of two media ahead are on
+        # their way while one is solved, and a solution has two solves' time
+        # to reach the host before its buffer is reused (host-link copy rates
+        # vary from run to run; the slack absorbs slow copies)
+        nb = min(3, count)
+        ahead = max(1, nb - 1)
         hb = [torch.empty(m, dtype=torch.complex128, device=dev) for _ in range(nb)]
         Nb = [torch.empty(m, dtype=torch.float64, device=dev) for _ in range(nb)]
         ub = [torch.empty(m, dtype=torch.complex128, device=dev) for _ in range(nb)]
@@ -325,7 +331,7 @@ class Plan:
 
         def upload(i):
             b = i % nb
-            cin.wait_event(consumed[b])          # set_medium of medium i - 2 has read the buffers
+            cin.wait_event(consumed[b])          # set_medium of medium i - nb has read the buffers
             with torch.cuda.stream(cin):
                 hb[b].copy_(hs[i], non_blocking=True)
                 Nb[b].copy_(Ns[i], non_blocking=True)
@@ -339,16 +345,16 @@ class Plan:
             downloaded[b].record(cout)
 
         infos = []
-        if count:
-            upload(0)
+        for i in range(min(ahead, count)):
+            upload(i)
         for i in range(count):
             b = i % nb
             main.wait_event(uploaded[b])
             self.set_medium(hb[b], Nb[b], stream=main)
             consumed[b].record(main)
-            if i + 1 < count:
-                upload(i + 1)
-            main.wait_event(downloaded[b])       # the solution of medium i - 2 has left ub[b]
+            if i + ahead < count:
+                upload(i + ahead)
+            main.wait_event(downloaded[b])       # the solution of medium i - nb has left ub[b]
             _, info = self.solve(out=ub[b], raise_on_failure=raise_on_failure, stream=main, **kw)
             solved[b].record(main)
             download(i)
